@@ -1,0 +1,213 @@
+/*
+ * gpga.h -- C ABI of libgpga.so, the GB300 (sm_103a) hot path of the
+ * master-slave parallel genetic algorithm for unsupervised market clustering of
+ * Hendricks, Gebbie & Wilcox (arXiv:1403.4099).
+ *
+ * The path: Pearson correlation C of a T x N returns matrix (Eq. 7), scoring of
+ * a population of cluster-label vectors with the Giada-Marsili log-likelihood
+ * L_c (Eq. 5, 6, 8), and the device-resident GA generation of Algorithm 1
+ * (isolate fittest, elitism, scaling, SUS selection, crossover, mutation,
+ * replacement) driven by a counter-based Philox4x32-10 stream.
+ *
+ * Conventions for every call:
+ *   - Status: 0 = GPGA_OK, negative = error (GPGA_ERR_*). No C++ exception
+ *     crosses the ABI. gpga_last_error() returns a description of the last
+ *     error of the calling thread (static storage, valid until the next call).
+ *   - Pointers are plain addresses. "device" pointers must be readable by the
+ *     current CUDA device (cudaMalloc / torch CUDA storage / managed memory);
+ *     "host or device" pointers are classified with cudaPointerGetAttributes.
+ *     Caller buffers are borrowed for the duration of the call only (or, for
+ *     asynchronous calls, until the stream reaches the call), never retained.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Layouts are row-major. Labels are int32 in [0, N) (0-based form of the
+ *     paper's 1..K labels, Eq. 9, with K = N).
+ *   - The library allocates device memory only in ga_init (owned by the handle,
+ *     released by ga_free) and, for cluster_corr and ga_score, stream-ordered
+ *     scratch (cudaMallocAsync / cudaFreeAsync) inside the call.
+ */
+#ifndef GPGA_H
+#define GPGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GPGA_API __attribute__((visibility("default")))
+#else
+#define GPGA_API
+#endif
+
+/* status codes */
+#define GPGA_OK 0
+#define GPGA_ERR_ARG (-1)        /* bad argument: size, pointer, label range */
+#define GPGA_ERR_CUDA (-2)       /* a CUDA runtime call failed */
+#define GPGA_ERR_OOM (-3)        /* device allocation failed */
+#define GPGA_ERR_DEGENERATE (-4) /* non-finite input or zero-variance column */
+#define GPGA_ERR_TIMEOUT (-5)    /* a bounded device wait gave up */
+#define GPGA_ERR_STATE (-6)      /* call not valid in the handle's state */
+
+/* scoring forms (both end in the same FP64 log-term assembly) */
+#define GPGA_FORM_PLAIN 0  /* FP32 CUDA-core pair accumulation */
+#define GPGA_FORM_TENSOR 1 /* tcgen05 one-hot contraction, D split BF16 hi+lo */
+
+/* fitness scaling before selection ("apply scaling", Algorithm 1) */
+#define GPGA_SCALING_RANK 0 /* w(r) = floor(2^32 / sqrt(r + 1)), r = 0-based rank */
+#define GPGA_SCALING_PROP 1 /* w = floor(max(L, 0) / L_max * 2^32) */
+
+/* initial population ("create initial population", Algorithm 1) */
+#define GPGA_INIT_UNIFORM 0   /* labels uniform in [0, init_labels) */
+#define GPGA_INIT_THRESHOLD 1 /* components of {C_ij > tau_p}, tau_p ~ U[tau_lo, tau_hi) */
+
+/* Limits of this build. */
+#define GPGA_MAX_N 4096       /* stocks (genes per individual) */
+#define GPGA_MAX_P 16384      /* population size */
+
+/*
+ * GA parameters; gpga_default_params() fills Table 3 of the paper (population
+ * 1000, 400 generations, P_c 0.9, error tolerance 1e-5, stall 50, elite 10,
+ * knowledge-based crossover share 0.9) with P_m read per gene as 0.01.
+ */
+typedef struct gpga_params {
+    int32_t P;           /* population size, 2..GPGA_MAX_P */
+    int32_t elite;       /* E fittest copied unchanged, 0..P-1 */
+    int32_t max_gens;    /* G_max: stop after scoring generation G_max */
+    int32_t stall_gens;  /* G_stall (<= 0: no stall rule) */
+    double tol;          /* stall when best_g - best_{g-G_stall} <= tol*max(1,|best_g|); < 0 off */
+    double pc;           /* crossover probability */
+    double pkb;          /* share of crossovers that are knowledge-based (else one-point) */
+    double pm;           /* mutation probability per gene (random replacement in [0, N)) */
+    int32_t scaling;     /* GPGA_SCALING_* */
+    int32_t form;        /* GPGA_FORM_* */
+    int32_t init;        /* GPGA_INIT_* */
+    int32_t init_labels; /* uniform init range K0 (0 = N) */
+    double tau_lo;       /* threshold init: tau range */
+    double tau_hi;
+    int32_t record;      /* keep per-generation best L, best labels and device timestamps */
+    int32_t reserved[3];
+} gpga_params;
+
+/* Opaque GA run: population (two device buffers), fitness, derived forms of C,
+ * generation counter, termination state, Philox seed. */
+typedef struct gpga_ga gpga_ga;
+
+/* Fill *p with the defaults above (P = 1000). */
+GPGA_API int gpga_default_params(gpga_params *p);
+
+/* Description of the last error on this thread ("" when none). */
+GPGA_API const char *gpga_last_error(void);
+
+/*
+ * cluster_corr -- Pearson correlation matrix, Eq. 7 (Sec. 2.1; data normalised
+ * to zero mean and unit variance below Eq. 2):
+ *   C_ij = sum_t z_ti z_tj / sqrt(sum_t z_ti^2 sum_t z_tj^2),  z = R - column mean.
+ * R: device, T x N FP64, row-major, leading dimension ld >= N. C: device, N x N
+ * FP64 (written; diagonal exactly 1, symmetric, clamped to [-1, 1]).
+ * Column statistics are FP64; the T-contraction runs in FP32 on normalised
+ * columns with FP64 combination of short partial sums (|error| ~1e-7).
+ * Errors: GPGA_ERR_ARG if T < 2, N < 2, N > GPGA_MAX_N or ld < N;
+ * GPGA_ERR_DEGENERATE if a column holds a non-finite value or has zero variance
+ * (C is then left unspecified). Blocks the host until the stream reaches the
+ * end of the call (the degeneracy check is data-dependent).
+ */
+GPGA_API int cluster_corr(const double *R, int T, int N, int ld, double *C, void *stream);
+
+/*
+ * ga_score -- L_c of P configurations, Eq. 8 with n_s (Eq. 5) and c_s (Eq. 6):
+ *   L_c(S) = 1/2 sum_{s: n_s>1} [ log(n_s/c_s) + (n_s-1) log((n_s^2-n_s)/(n_s^2-c_s)) ].
+ * n_s^2 - c_s is accumulated directly as d_s = sum_{i,j in s} (1 - C_ij) (no
+ * cancellation for tight clusters); c_s = n_s^2 - d_s. Domain edge (degenerate
+ * data only): c_s floored at n_s 2^-40 and d_s at n_s(n_s-1) 2^-40.
+ * labels: device, P x N int32 in [0, N), leading dimension ld >= N.
+ * C: device, N x N FP64 (read; asymmetric input is used through (C + C^T)/2,
+ * which leaves Eq. 6 unchanged). L: device, P FP64 (written).
+ * form: GPGA_FORM_PLAIN or GPGA_FORM_TENSOR.
+ * Errors: GPGA_ERR_ARG for sizes out of range or any label outside [0, N)
+ * (found on the device; the matching L entries are NaN). Blocks the host until
+ * the stream reaches the end of the call.
+ */
+GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double *C, double *L,
+                      int form, void *stream);
+
+/*
+ * ga_evolve -- one stateless GA generation after scoring (Algorithm 1: isolate
+ * fittest, elitism, scaling, selection, crossover, mutation, replacement) from
+ * population `pop` (device, P x N int32, row stride N) with fitness `L`
+ * (device, P FP64) into `next` (device, P x N int32). Draws come from
+ * Philox4x32-10 keyed by `seed` with counters (generation, index, block,
+ * stream): SUS (g,0,0,1) word 0; child k (g,k,0,2) words crossover?,
+ * knowledge-based?, anchor/cut; gene j (g,k,j/2,3) words (0,1) or (2,3).
+ * Ranking: L descending, ties to the lower index; NaN ranks as -inf.
+ * Knowledge-based crossover (reading of Sec. 3.1): the child is parent a with
+ * parent b's cluster of anchor gene q merged into a's cluster of q.
+ * perm (device, P int32, optional) receives the rank order; parents (device,
+ * P - elite int32, optional) the selected parent of each child.
+ * Uses p->P, elite, pc, pkb, pm, scaling; N is the gene count.
+ * Asynchronous on `stream`.
+ */
+GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_params *p,
+                       uint64_t seed, int generation, int32_t *next, int32_t *perm,
+                       int32_t *parents, void *stream);
+
+/*
+ * ga_init -- create a GA run on correlation matrix C (device, N x N FP64; copied
+ * and derived from, so the caller may free it on return): allocates the
+ * population buffers, the FP32 and BF16 hi/lo forms of D = 1 - C and the
+ * per-generation records, creates the initial population and scores it
+ * (generation 0). Asynchronous on `stream`, which the handle keeps for all
+ * later calls. Errors: GPGA_ERR_ARG (N < 2, N > GPGA_MAX_N, bad params),
+ * GPGA_ERR_OOM. *out is NULL on error.
+ */
+GPGA_API int ga_init(const double *C, int N, const gpga_params *p, uint64_t seed, void *stream,
+                     gpga_ga **out);
+
+/*
+ * ga_reset -- restart handle h on a new correlation matrix C (device, same N)
+ * and seed without reallocating; generation 0 is created and scored.
+ * Asynchronous.
+ */
+GPGA_API int ga_reset(gpga_ga *h, const double *C, uint64_t seed);
+
+/*
+ * ga_step -- run up to `generations` generations (evolve, score, rank, test
+ * termination), all on the device with no host round trip; generations after
+ * termination are no-ops. Asynchronous when done == NULL; otherwise waits for
+ * the stream and writes 1 to *done if the run has terminated, else 0.
+ */
+GPGA_API int ga_step(gpga_ga *h, int generations, int *done);
+
+/*
+ * ga_best -- the fittest configuration of the current generation, canonically
+ * relabelled by first occurrence (0, 1, 2, ...), with L re-scored in FP64
+ * directly from the FP64 C (the final re-score). labels: host or device, N
+ * int32 (optional); L: host or device, 1 FP64 (optional); generation: host
+ * (optional). Waits for the handle's stream.
+ */
+GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation);
+
+/*
+ * ga_history -- per-generation records kept when params.record != 0: best L
+ * (FP64), best labels (int32, as stored), and the device clock (ns, %globaltimer)
+ * at the end of each generation, for generations 0..count-1, count <= cap.
+ * Host pointers (each optional). t_ns[0] is taken at the start of ga_init /
+ * ga_reset, t_ns[1 + g] at the end of generation g. Waits for the stream.
+ */
+GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns, int cap,
+                        int *count);
+
+/*
+ * ga_population -- copy the current population (P x N int32) and its fitness
+ * (P FP64) to host or device buffers (each optional). Waits for the stream.
+ */
+GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
+
+/* ga_free -- release the handle and all its device memory (NULL is a no-op). */
+GPGA_API int ga_free(gpga_ga *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPGA_H */

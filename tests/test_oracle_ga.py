@@ -1,0 +1,183 @@
+"""Pins of the oracle's GA operators (Sec. 3.1, Algorithm 1, Table 3) by
+properties that hold whatever the random draws: sorting against numpy, exact
+integer weights, the defining property of stochastic universal sampling, the
+structure of each crossover child, mutation rate, elitism, termination."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1403_4099_gb300 import synth
+
+
+def test_init_range_and_determinism(orc):
+    a = orc.ga_init(64, 16, seed=123)
+    b = orc.ga_init(64, 16, seed=123)
+    c = orc.ga_init(64, 16, seed=124)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.min() >= 0 and a.max() < 16
+    k = orc.ga_init(400, 50, seed=5, K0=7)
+    assert k.min() == 0 and k.max() == 6
+    counts = np.bincount(k.ravel(), minlength=7)
+    expect = k.size / 7
+    assert np.all(np.abs(counts - expect) < 6 * math.sqrt(expect))
+
+
+def test_rank_matches_lexsort(orc):
+    rng = np.random.default_rng(0)
+    L = np.round(rng.standard_normal(1000), 1)  # many ties
+    L[5] = -np.inf
+    L[9] = np.nan  # ranks as -inf
+    perm = orc.ga_rank(L)
+    key = np.where(np.isnan(L), -np.inf, L)
+    ref = np.lexsort((np.arange(1000), -key))
+    assert np.array_equal(perm, ref)
+
+
+def test_rank_weights_exact(orc):
+    P = 5000
+    w = orc.ga_weights(np.zeros(P), np.arange(P, dtype=np.int32), orc.SCALING_RANK)
+    exact = np.array([math.isqrt((1 << 64) // (r + 1)) for r in range(P)], dtype=np.uint64)
+    # floor(2^32 / sqrt(r)) computed exactly with integers; FP64 may round across by 1
+    diff = w.astype(np.int64) - exact.astype(np.int64)
+    assert np.abs(diff).max() <= 1
+    assert (diff == 0).mean() > 0.99
+    assert w[0] == 1 << 32 and np.all(np.diff(w.astype(np.int64)) <= 0)
+
+
+def test_prop_weights(orc):
+    rng = np.random.default_rng(1)
+    L = rng.uniform(-1, 10, 300)
+    perm = orc.ga_rank(L)
+    w = orc.ga_weights(L, perm, orc.SCALING_PROP)
+    assert w[0] == 1 << 32 and np.all(np.diff(w.astype(np.int64)) <= 0)
+    for r in range(300):
+        x = max(L[perm[r]], 0.0)
+        exact = Fraction(x) / Fraction(L[perm[0]]) * (1 << 32)
+        assert abs(int(w[r]) - math.floor(exact)) <= 1
+    assert np.all(orc.ga_weights(-np.abs(L), orc.ga_rank(-np.abs(L)), orc.SCALING_PROP) == 1)
+
+
+@pytest.mark.parametrize("P,M", [(64, 62), (1000, 990), (37, 37), (4096, 4094), (10, 3)])
+def test_sus_counts_are_floor_or_ceil_of_expectation(orc, P, M):
+    rng = np.random.default_rng(P + M)
+    w = orc.ga_weights(np.zeros(P), np.arange(P, dtype=np.int32), orc.SCALING_RANK)
+    w = (w * rng.integers(1, 4, P).astype(np.uint64)).astype(np.uint64)
+    W = int(w.astype(object).sum())
+    for u in [0, 1, 2**31, 2**32 - 1, int(rng.integers(0, 2**32))]:
+        sel = orc.ga_sus(w, M, u)
+        assert np.all(np.diff(sel) >= 0) and sel.min() >= 0 and sel.max() < P
+        counts = np.bincount(sel, minlength=P)
+        for r in range(P):
+            e = Fraction(M * int(w[r]), W)
+            assert math.floor(e) <= counts[r] <= math.ceil(e)
+
+
+def _classify_child(child, a, b):
+    """Which crossover shapes explain child (no mutation)."""
+    N = a.shape[0]
+    kinds = set()
+    if np.array_equal(child, a):
+        kinds.add("copy")
+    for cut in range(1, N):
+        if np.array_equal(child[:cut], a[:cut]) and np.array_equal(child[cut:], b[cut:]):
+            kinds.add("onepoint")
+            break
+    # merge: some cluster Q of b, all of whose genes now carry the a-label of one
+    # of its members, everything else as in a
+    for lab in np.unique(b):
+        Q = b == lab
+        if not np.array_equal(child[~Q], a[~Q]):
+            continue
+        v = child[Q]
+        if np.all(v == v[0]) and v[0] in set(a[Q].tolist()):
+            kinds.add("merge")
+    return kinds
+
+
+@pytest.mark.parametrize("pc,pkb,kind", [(0.0, 0.0, "copy"), (1.0, 0.0, "onepoint"),
+                                          (1.0, 1.0, "merge")])
+def test_crossover_structure(orc, pc, pkb, kind):
+    rng = np.random.default_rng(11)
+    P, N = 40, 12
+    pop = rng.integers(0, 5, (P, N)).astype(np.int32)
+    L = rng.standard_normal(P)
+    prm = orc.params(P, N, elite=3, pc=pc, pkb=pkb, pm=0.0)
+    nxt, perm, par = orc.ga_evolve(pop, L, prm, seed=99, g=4)
+    M = P - 3
+    assert np.array_equal(nxt[:3], pop[perm[:3]])
+    for k in range(M):
+        a, b = pop[par[k]], pop[par[(k + M // 2) % M]]
+        assert kind in _classify_child(nxt[3 + k], a, b), k
+
+
+def test_mixed_crossover_rates(orc):
+    rng = np.random.default_rng(12)
+    P, N = 2000, 20
+    pop = rng.integers(0, 20, (P, N)).astype(np.int32)
+    L = rng.standard_normal(P)
+    prm = orc.params(P, N, elite=0, pc=0.9, pkb=0.0, pm=0.0)
+    nxt, perm, par = orc.ga_evolve(pop, L, prm, seed=3, g=0)
+    copies = sum(np.array_equal(nxt[k], pop[par[k]]) for k in range(P))
+    # 10% no-crossover plus the rare one-point cut that reproduces a
+    assert 0.07 * P < copies < 0.14 * P
+    prm = orc.params(P, N, elite=0, pc=1.0, pkb=0.5, pm=0.0)
+    nxt, perm, par = orc.ga_evolve(pop, L, prm, seed=4, g=0)
+    M = P
+    kinds = [_classify_child(nxt[k], pop[par[k]], pop[par[(k + M // 2) % M]]) for k in range(P)]
+    merges = sum("merge" in k and "onepoint" not in k for k in kinds)
+    onepoints = sum("onepoint" in k and "merge" not in k for k in kinds)
+    assert abs(merges - onepoints) < 0.15 * P
+
+
+def test_mutation_rate_and_elites_untouched(orc):
+    rng = np.random.default_rng(13)
+    P, N, E = 500, 100, 5
+    pop = rng.integers(0, N, (P, N)).astype(np.int32)
+    L = rng.standard_normal(P)
+    pm = 0.02
+    prm = orc.params(P, N, elite=E, pc=0.0, pm=pm)
+    nxt, perm, par = orc.ga_evolve(pop, L, prm, seed=7, g=2)
+    assert np.array_equal(nxt[:E], pop[perm[:E]])
+    changed = (nxt[E:] != pop[par]).sum()
+    n = (P - E) * N
+    p = pm * (1 - 1 / N)
+    assert abs(changed - n * p) < 6 * math.sqrt(n * p * (1 - p))
+    assert nxt.min() >= 0 and nxt.max() < N
+
+
+def test_selection_follows_rank(orc):
+    rng = np.random.default_rng(14)
+    P, N = 256, 8
+    pop = rng.integers(0, N, (P, N)).astype(np.int32)
+    L = rng.standard_normal(P)
+    prm = orc.params(P, N, elite=2, pc=0.0, pm=0.0)
+    _, perm, par = orc.ga_evolve(pop, L, prm, seed=1, g=0)
+    rank_of = np.empty(P, np.int64)
+    rank_of[perm] = np.arange(P)
+    r = rank_of[par]
+    assert np.all(np.diff(r) >= 0)  # pointers walk the line in rank order
+    assert (r < P // 4).mean() > 0.4  # 1/sqrt(rank) favours the fittest
+
+
+def test_termination_rule(orc):
+    prm = orc.params(10, 5, max_gens=30, stall_gens=5, tol=1e-5)
+    h = np.concatenate([np.linspace(1, 2, 10), np.full(21, 2.0)])
+    done = [g for g in range(31) if orc.ga_terminated(h, g, prm)]
+    assert done[0] == 14  # best_14 - best_9 = 0
+    h2 = np.linspace(1, 100, 31)
+    assert [g for g in range(31) if orc.ga_terminated(h2, g, prm)] == [30]
+    prm_off = orc.params(10, 5, max_gens=30, stall_gens=5, tol=-1.0)
+    assert [g for g in range(31) if orc.ga_terminated(h, g, prm_off)] == [30]
+
+
+def test_run_elitism_monotone_and_recovers_small16(orc):
+    p = synth.small16()
+    C = orc.pearson(p.R)
+    prm = orc.params(64, 16, elite=2, max_gens=200, stall_gens=50, tol=1e-5, pm=0.01)
+    out = orc.ga_run(C, prm, seed=synth.seed_for(1), ring=True)
+    assert np.all(np.diff(out["hist"]) >= 0)
+    assert orc.ari(out["best"], p.truth) >= 0.99
+    assert out["L"] == orc.loglik(out["best"], C)
+    assert np.array_equal(out["ring"][-1], out["best"])
