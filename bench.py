@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the PGA hot path on the N=500, T=5000, P=4096 planted-cluster
+workload (20 clusters, market mode 0.3, 10% noise series).
+
+A step is one whole PGA job on one window: Pearson prelude (cluster_corr) from
+device-resident returns, initial population + scoring (ga_reset), and G
+generations of score / rank / select / crossover / mutate (ga_step), all on the
+device. Metric: fitness evaluations per second, P (G + 1) per step. Also
+reported: generations/s, ms to recover the planted clusters (ARI >= 0.99),
+per-stage kernel times (CUDA events on the launching stream, live in the timed
+region), the roofline of the dominant kernel, the end-to-end number through host
+buffers, and the FP64 CPU oracle timed on the host cores.
+
+Multi-GPU (torchrun): every rank runs its own independent jobs (replicas, weak
+scaling); only a barrier and max-over-ranks timing cross ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, T, P = 500, 5000, 4096
+ELITE = 10
+WORKLOAD = "planted_n500_t5000_p4096"
+METRIC = "fitness evals/s (N=500, P=4096; step = Pearson prelude + init + G generations)"
+SMS = 152
+ALU_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpga", choices=["gpga", "reference"])
+    ap.add_argument("--form", default="plain", choices=["plain", "tensor"])
+    ap.add_argument("--gens", type=int, default=100, help="generations per step")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recover", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1403_4099_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(R, gens: int):
+    """Time the FP64 oracle on one window: Pearson + initial population + `gens`
+    generations (score + operators), on all host threads. Returns
+    (seconds, evaluations, seconds_pearson, seconds_ga)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    C = oracle.pearson(R)
+    t1 = time.perf_counter()
+    prm = oracle.params(P, N, elite=ELITE, max_gens=gens, stall_gens=50, tol=-1.0, pm=0.01)
+    oracle.ga_run(C, prm, seed=12345, nthreads=0)
+    t2 = time.perf_counter()
+    return t2 - t0, P * (gens + 1), t1 - t0, t2 - t1
+
+
+def run_reference(args, ranks):
+    from paper_1403_4099_gb300 import synth
+    import oracle
+    if ranks.rank != 0:
+        return
+    planted = synth.n500()
+    gens = 2
+    for _ in range(args.warmup):
+        oracle_sample(planted.R, gens)
+    secs, evals = 0.0, 0
+    for _ in range(args.steps):
+        s, e, _, _ = oracle_sample(planted.R, gens)
+        secs += s
+        evals += e
+    value = evals / secs
+    cores = oracle.max_threads()
+    sample = (f"per step: FP64 oracle Pearson (T={T}, N={N}) + initial population + {gens} "
+              f"generations at P={P}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "T": T, "P": P, "generations_per_step": gens},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def launches_per_step(form: str, gens: int) -> int:
+    corr = 7                      # colsum x2, colfinal x2, normalise, gram, gram_final
+    score = 2 if form == "plain" else 4
+    start = 4 + score + 1         # state, prep_d, rank table, init, score, select
+    return corr + start + gens * (2 + score)
+
+
+def run_gpu(args, ranks):
+    import torch
+
+    from paper_1403_4099_gb300 import gpga, metrics, runtime, synth
+
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    runtime.init_dist(ranks, "nccl")
+    form = gpga.FORM_PLAIN if args.form == "plain" else gpga.FORM_TENSOR
+    G = args.gens
+    planted = synth.n500(replicate=ranks.rank)
+    R_host = torch.from_numpy(planted.R).pin_memory()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    with torch.cuda.stream(stream):
+        R = R_host.to(dev, non_blocking=True)
+        C = torch.empty((N, N), dtype=torch.float64, device=dev)
+        gpga.cluster_corr(R, C, stream)
+        prm = gpga.default_params(P=P, elite=ELITE, max_gens=G, stall_gens=50, tol=-1.0,
+                                  pm=0.01, form=form, record=1, profile=1)
+        ga = gpga.GA(C, prm, seed=1, stream=stream)
+
+        def one_step(k):
+            gpga.cluster_corr(R, C, stream)
+            ga.reset(C, 1000 + k)
+            ga.step(G)
+
+        for k in range(args.warmup):
+            one_step(k)
+        stream.synchronize()
+        runtime.barrier(ranks)
+
+        gpu = None
+        try:
+            props = torch.cuda.get_device_properties(dev)
+            gpu = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(ranks.local)
+        except Exception:
+            gpu = str(ranks.local)
+        sampler = runtime.ClockSampler(gpu)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stage = []
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            one_step(args.warmup + k)
+            ev1[k].record(stream)
+            stage.append(ga.kernel_times())
+        stream.synchronize()
+        wall = time.perf_counter() - wall0
+        clocks = sampler.stop(busy_mhz_floor=600.0)
+        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        hist = ga.history()
+    runtime.barrier(ranks)
+
+    secs = sum(step_ms) / 1e3
+    evals = P * (G + 1) * args.steps
+    max_secs, total_evals = runtime.aggregate(ranks, secs, evals, device=dev)
+    value = total_evals / max_secs
+    gens_per_s = value / P
+
+    stage = np.concatenate(stage)  # rows: generations; cols: evolve, pair, assemble, select
+    stage_mean = stage.mean(axis=0)
+    names = ["evolve", "pair_plain" if form == gpga.FORM_PLAIN else "tc_contract", "assemble",
+             "select"]
+    kernel_ms = {n: float(v) for n, v in zip(names, stage_mean)}
+    dominant = names[int(np.argmax(stage_mean))]
+
+    pk, pk_kind = peaks()
+    if form == gpga.FORM_PLAIN:
+        # compare + predicated add per unordered gene pair (i < j) per individual
+        ops = float(P) * N * (N - 1)
+        t = kernel_ms["pair_plain"] / 1e3
+        peak = SMS * ALU_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        traffic = profiled_traffic("pair_plain_n500_p4096", source_hash("score.cu"))
+        roof = {"bound": "alu", "kernel": "pair_plain", "achieved": ops / t / 1e12, "peak": peak,
+                "unit": "Tops/s", "frac": (ops / t / 1e12) / peak, "traffic": traffic,
+                "peak_source": f"{SMS} SMs x {ALU_LANES} FP32/INT32 lanes x "
+                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
+                "algorithmic_ops_per_launch": ops, "launch_ms": kernel_ms["pair_plain"]}
+    else:
+        roof = None  # filled by the tensor form
+
+    # recovery: first generation whose best individual has ARI >= 0.99 vs the planted labels
+    ari = [metrics.ari(l, planted.truth) for l in hist["labels"]]
+    rec = next((g for g, a in enumerate(ari) if a >= 0.99), None)
+    ms_rec = {"uniform_init": None if rec is None else
+              float(hist["t_ns"][1 + rec] - hist["t_ns"][0]) / 1e6,
+              "uniform_init_best_ari": float(max(ari))}
+
+    out = {}
+    if ranks.rank == 0:
+        out = dict(e2e=run_e2e(args, ranks, R_host, dev, form, G),
+                   recover=None if args.no_recover else run_recover(args, ranks, planted, dev, form))
+        if out["recover"]:
+            ms_rec.update(out["recover"])
+
+    cpu = None
+    if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        g_cpu = 3
+        s, e, sp, sg = oracle_sample(planted.R, g_cpu)
+        # extrapolate the GA part linearly to G generations
+        s_full = sp + sg * (G + 1) / (g_cpu + 1)
+        cpu = {"value": P * (G + 1) / s_full, "unit": "evals/s", "cores": oracle.max_threads(),
+               "kind": "oracle",
+               "sample": (f"FP64 oracle on this workload: Pearson once ({sp:.2f} s, 1 thread) + "
+                          f"initial population + {g_cpu} generations ({sg:.2f} s, all threads), "
+                          f"GA time extrapolated linearly to {G} generations")}
+
+    if ranks.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ranks.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "dtype_detail": "FP32 pair accumulation, FP64 column statistics and log terms, "
+                            "integer GA operators",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "T": T, "P": P, "elite": ELITE,
+                       "generations_per_step": G, "form": args.form, "init": "uniform",
+                       "l2": "flushed between steps (256 MB memset outside the step events)"},
+            "generations_per_s": gens_per_s,
+            "ms_to_recover": ms_rec,
+            "kernel_ms": kernel_ms, "dominant_kernel": dominant,
+            "roofline": roof,
+            "e2e": out.get("e2e"),
+            "cpu_baseline": cpu,
+            "gpu_launches": launches_per_step(args.form, G) * args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    runtime.barrier(ranks)
+
+
+def run_e2e(args, ranks, R_host, dev, form, G):
+    """The same metric through the public API from pinned host returns to the
+    host-side best configuration: H2D of R, prelude, init, G generations,
+    FP64 re-score, D2H of the labels and L, every step."""
+    import torch
+
+    from paper_1403_4099_gb300 import gpga
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        R = torch.empty(R_host.shape, dtype=torch.float64, device=dev)
+        C = torch.empty((N, N), dtype=torch.float64, device=dev)
+        R.copy_(R_host, non_blocking=True)
+        gpga.cluster_corr(R, C, stream)
+        prm = gpga.default_params(P=P, elite=ELITE, max_gens=G, tol=-1.0, pm=0.01, form=form)
+        ga = gpga.GA(C, prm, seed=7, stream=stream)
+        lab = np.zeros(N, np.int32)
+        Lb = np.zeros(1, np.float64)
+        times = []
+        for k in range(args.e2e_steps + 1):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            R.copy_(R_host, non_blocking=True)
+            gpga.cluster_corr(R, C, stream)
+            ga.reset(C, 50 + k)
+            ga.step(G)
+            ga.best(lab, Lb)
+            times.append(time.perf_counter() - t0)
+        ga.close()
+    t = float(np.mean(times[1:]))
+    return {"value": P * (G + 1) / t, "unit": "evals/s", "ms_per_step": 1e3 * t,
+            "h2d_bytes_per_step": int(R_host.numel() * 8), "d2h_bytes_per_step": int(N * 4 + 8)}
+
+
+def run_recover(args, ranks, planted, dev, form):
+    """Device time from the start of ga_reset to the first generation whose best
+    individual has ARI >= 0.99, with the correlation-threshold initial
+    population; plus the prelude's own time."""
+    import torch
+
+    from paper_1403_4099_gb300 import gpga, metrics
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        R = torch.from_numpy(planted.R).to(dev)
+        C = torch.empty((N, N), dtype=torch.float64, device=dev)
+        gpga.cluster_corr(R, C, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gpga.cluster_corr(R, C, stream)
+        e1.record(stream)
+        stream.synchronize()
+        corr_ms = e0.elapsed_time(e1)
+        prm = gpga.default_params(P=P, elite=ELITE, max_gens=200, tol=-1.0, pm=0.01, form=form,
+                                  init=gpga.INIT_THRESHOLD, record=1)
+        ga = gpga.GA(C, prm, seed=3, stream=stream)
+        ga.step(50)
+        ga.reset(C, 4)
+        ga.step(50)
+        h = ga.history()
+        ga.close()
+    ari = [metrics.ari(l, planted.truth) for l in h["labels"]]
+    rec = next((g for g, a in enumerate(ari) if a >= 0.99), None)
+    ms = None if rec is None else float(h["t_ns"][1 + rec] - h["t_ns"][0]) / 1e6
+    return {"threshold_init": ms, "threshold_init_generation": rec,
+            "threshold_init_best_ari": float(max(ari)), "prelude_ms": corr_ms,
+            "threshold_init_with_prelude": None if ms is None else ms + corr_ms}
+
+
+def main():
+    args = parse()
+    from paper_1403_4099_gb300 import runtime
+    ranks = runtime.ranks_from_env()
+    if args.impl == "reference":
+        run_reference(args, ranks)
+        return
+    run_gpu(args, ranks)
+
+
+if __name__ == "__main__":
+    main()

@@ -86,7 +86,8 @@ typedef struct gpga_params {
     double tau_lo;       /* threshold init: tau range */
     double tau_hi;
     int32_t record;      /* keep per-generation best L, best labels and device timestamps */
-    int32_t reserved[3];
+    int32_t profile;     /* record CUDA events around every stage of every generation */
+    int32_t reserved[2];
 } gpga_params;
 
 /* Opaque GA run: population (two device buffers), fitness, derived forms of C,
@@ -196,6 +197,15 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation);
  */
 GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns, int cap,
                         int *count);
+
+/*
+ * ga_kernel_times -- stage durations (ms, CUDA events on the handle's stream) of
+ * the generations run by the most recent graph launch of ga_step, available
+ * when params.profile != 0. Row g of ms (count x 4, count <= cap) holds
+ * [evolve, pair accumulation (plain) or contraction (tensor), assembly,
+ * selection]. Waits for the stream. GPGA_ERR_STATE without profile.
+ */
+GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count);
 
 /*
  * ga_population -- copy the current population (P x N int32) and its fitness

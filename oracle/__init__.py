@@ -96,6 +96,9 @@ def _load():
             "orc_canonicalize": (ct.c_int, [i32p, ct.c_int, i32p]),
             "orc_ga_init": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ct.c_uint64, i32p]),
             "orc_ga_rank": (ct.c_int, [f64p, ct.c_int, i32p]),
+            "orc_prim_order": (ct.c_int, [f64p, ct.c_int, i32p]),
+            "orc_ga_init_threshold": (ct.c_int, [f64p, ct.c_int, ct.c_int, ct.c_double,
+                                                 ct.c_double, ct.c_uint64, i32p]),
             "orc_ga_weights": (ct.c_int, [f64p, i32p, ct.c_int, ct.c_int, u64p]),
             "orc_ga_sus": (ct.c_int, [u64p, ct.c_int, ct.c_int, ct.c_uint32, i32p]),
             "orc_ga_evolve": (ct.c_int, [i32p, f64p, ct.POINTER(GaParams), ct.c_uint64,
@@ -199,6 +202,23 @@ def canonicalize(s) -> np.ndarray:
 def ga_init(P, N, seed, K0=None) -> np.ndarray:
     pop = np.zeros((P, N), np.int32)
     _check(_load().orc_ga_init(P, N, N if K0 is None else K0, seed, pop), "ga_init")
+    return pop
+
+
+def prim_order(C) -> np.ndarray:
+    C = _f64(C)
+    order = np.zeros(C.shape[0], np.int32)
+    _check(_load().orc_prim_order(C, C.shape[0], order), "prim_order")
+    return order
+
+
+def ga_init_threshold(C, P, seed, tau_lo=0.05, tau_hi=0.6) -> np.ndarray:
+    """Correlation-threshold initial population (components of C > tau_p)."""
+    C = _f64(C)
+    N = C.shape[0]
+    pop = np.zeros((P, N), np.int32)
+    _check(_load().orc_ga_init_threshold(C, P, N, float(tau_lo), float(tau_hi), seed, pop),
+           "ga_init_threshold")
     return pop
 
 

@@ -369,6 +369,87 @@ int orc_ga_init(int P, int N, int K0, uint64_t seed, int32_t *pop)
     return ORC_OK;
 }
 
+/* Reading of "create initial population" with domain knowledge (optional): the
+ * connected components of {(i, j) : C_ij > tau_p} for a per-individual level
+ * tau_p = tau_lo + (tau_hi - tau_lo) * (u / 2^32), u = word 0 of Philox
+ * (0, p, 0, TAU=4). Built here by brute force: union of every pair above the
+ * level (union-find), each component labelled with its member that joins the
+ * maximum spanning tree first under Prim's rule (start at 0; next = largest key,
+ * ties to the lower index; keys improve only on a strictly larger C). */
+#define ORC_STREAM_TAU 4u
+
+int orc_prim_order(const double *C, int N, int32_t *order)
+{
+    if (N < 1 || !C || !order) return ORC_ERR_ARG;
+    double *key = (double *)malloc((size_t)N * sizeof(double));
+    unsigned char *in = (unsigned char *)calloc((size_t)N, 1);
+    if (!key || !in) {
+        free(key);
+        free(in);
+        return ORC_ERR_OOM;
+    }
+    in[0] = 1;
+    order[0] = 0;
+    for (int j = 0; j < N; ++j) key[j] = C[j];
+    for (int step = 1; step < N; ++step) {
+        int best = -1;
+        for (int j = 0; j < N; ++j)
+            if (!in[j] && (best < 0 || key[j] > key[best])) best = j;
+        in[best] = 1;
+        order[step] = best;
+        for (int j = 0; j < N; ++j)
+            if (!in[j] && C[(size_t)best * N + j] > key[j]) key[j] = C[(size_t)best * N + j];
+    }
+    free(key);
+    free(in);
+    return ORC_OK;
+}
+
+static int uf_find(int32_t *par, int x)
+{
+    while (par[x] != x) x = par[x] = par[par[x]];
+    return x;
+}
+
+int orc_ga_init_threshold(const double *C, int P, int N, double tau_lo, double tau_hi,
+                          uint64_t seed, int32_t *pop)
+{
+    if (P < 1 || N < 1 || !C || !pop || !(tau_hi >= tau_lo)) return ORC_ERR_ARG;
+    int32_t *order = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int32_t *pos = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int32_t *par = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int32_t *rep = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int rc = (order && pos && par && rep) ? orc_prim_order(C, N, order) : ORC_ERR_OOM;
+    if (rc == ORC_OK) {
+        for (int k = 0; k < N; ++k) pos[order[k]] = k;
+        const double span = tau_hi - tau_lo;
+        for (int p = 0; p < P; ++p) {
+            uint32_t w[4];
+            philox_draw(seed, 0u, (uint32_t)p, 0u, ORC_STREAM_TAU, w);
+            const double tau = tau_lo + span * ((double)w[0] * 2.3283064365386963e-10);
+            for (int i = 0; i < N; ++i) par[i] = i;
+            for (int i = 0; i < N; ++i)
+                for (int j = i + 1; j < N; ++j)
+                    if (C[(size_t)i * N + j] > tau) {
+                        int a = uf_find(par, i), b = uf_find(par, j);
+                        if (a != b) par[a] = b;
+                    }
+            /* label: the member of the component that comes first in Prim order */
+            for (int i = 0; i < N; ++i) rep[i] = -1;
+            for (int i = 0; i < N; ++i) {
+                int r = uf_find(par, i);
+                if (rep[r] < 0 || pos[i] < pos[rep[r]]) rep[r] = i;
+            }
+            for (int i = 0; i < N; ++i) pop[(size_t)p * N + i] = rep[uf_find(par, i)];
+        }
+    }
+    free(order);
+    free(pos);
+    free(par);
+    free(rep);
+    return rc;
+}
+
 /* "Isolate fittest individuals": perm[r] is the individual of rank r, ranked by
  * L descending, ties by lower index first (a stable merge sort of 0..P-1); a NaN
  * fitness ranks as -inf. */

@@ -1,0 +1,181 @@
+// init.cu -- correlation-threshold initial population (reading of "create
+// initial population", Algorithm 1, which the paper leaves to a thesis).
+//
+// Individual p starts as the connected components of the graph
+// {(i, j) : C_ij > tau_p}, tau_p = tau_lo + (tau_hi - tau_lo) u_p / 2^32 with u_p
+// word 0 of Philox(0, p, 0, TAU): single-linkage cuts of C at a spread of levels,
+// which the GA then refines. Components of {C > tau} equal those of the maximum
+// spanning tree's edges above tau, so the tree is built once (Prim, one CTA) and
+// each individual needs one O(N) pass:
+//   vertices in Prim order v_0 = 0, v_1, ...; vertex v_k joined the tree through
+//   edge (from_k, v_k) of weight w_k; label(v_0) = v_0 and
+//   label(v_k) = w_k > tau ? label(from_k) : v_k.
+// Prim's rule: the next vertex has the largest key (ties to the lower index);
+// a key improves only on a strictly larger C. All comparisons are exact FP64.
+#include <math.h>
+
+#include "gpga_internal.cuh"
+
+namespace gpga {
+
+static constexpr uint32_t STREAM_TAU = 4u;
+
+__global__ void __launch_bounds__(1024)
+    mst_kernel(const double *__restrict__ C, int N, int32_t *__restrict__ order,
+               int32_t *__restrict__ from, double *__restrict__ w_out)
+{
+    extern __shared__ double sm[];
+    double *key = sm;                                        // N
+    int *src = reinterpret_cast<int *>(key + N);             // N
+    int *in = src + N;                                       // N
+    __shared__ double s_bk[32];
+    __shared__ int s_bi[32];
+    __shared__ int s_pick;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = tid; j < N; j += nt) {
+        key[j] = C[j]; // row 0
+        src[j] = 0;
+        in[j] = j == 0;
+    }
+    if (tid == 0) {
+        order[0] = 0;
+        from[0] = 0;
+        w_out[0] = INFINITY;
+    }
+    __syncthreads();
+    for (int step = 1; step < N; ++step) {
+        // argmax of key over vertices not in the tree, ties to the lower index
+        double bk = -INFINITY;
+        int bi = 0x7fffffff;
+        for (int j = tid; j < N; j += nt) {
+            if (in[j]) continue;
+            const double k = key[j];
+            if (k > bk || (k == bk && j < bi)) {
+                bk = k;
+                bi = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ok > bk || (ok == bk && oi < bi)) {
+                bk = ok;
+                bi = oi;
+            }
+        }
+        if ((tid & 31) == 0) {
+            s_bk[tid >> 5] = bk;
+            s_bi[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const int nw = nt >> 5;
+            bk = tid < nw ? s_bk[tid] : -INFINITY;
+            bi = tid < nw ? s_bi[tid] : 0x7fffffff;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ok > bk || (ok == bk && oi < bi)) {
+                    bk = ok;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                s_pick = bi;
+                order[step] = bi;
+                from[step] = src[bi];
+                w_out[step] = key[bi];
+                in[bi] = 1;
+            }
+        }
+        __syncthreads();
+        const int v = s_pick;
+        const double *row = C + (size_t)v * N;
+        for (int j = tid; j < N; j += nt) {
+            if (in[j]) continue;
+            const double c = row[j];
+            if (c > key[j]) {
+                key[j] = c;
+                src[j] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int launch_mst(const double *C, int N, int32_t *order, int32_t *from, double *w,
+               cudaStream_t s)
+{
+    const size_t smem = (size_t)N * (sizeof(double) + 2 * sizeof(int));
+    mst_kernel<<<1, 1024, smem, s>>>(C, N, order, from, w);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+// one warp per individual; the Prim-order pass is made parallel by pointer
+// jumping: up(v_k) = w_k > tau ? from_k : v_k, then label = up^(log N)(v).
+template <typename LabT>
+__global__ void __launch_bounds__(256)
+    init_threshold_kernel(LabT *__restrict__ pop, int ldp, int P, int N,
+                          const int32_t *__restrict__ order, const int32_t *__restrict__ from,
+                          const double *__restrict__ w, double tau_lo, double tau_span,
+                          uint32_t k0, uint32_t k1)
+{
+    extern __shared__ int sm_up[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *up = sm_up + warp * N;
+    for (int p = blockIdx.x * 8 + warp; p < P; p += gridDim.x * 8) {
+        const U4 r = philox(0u, (uint32_t)p, 0u, STREAM_TAU, k0, k1);
+        const double frac = (double)r.x * 2.3283064365386963e-10; // u / 2^32, exact
+        const double tau = __dadd_rn(tau_lo, __dmul_rn(tau_span, frac));
+        for (int k = lane; k < N; k += 32) {
+            const int v = order[k];
+            up[v] = (k > 0 && w[k] > tau) ? from[k] : v;
+        }
+        __syncwarp();
+        // pointer jumping to the component root (the earliest vertex in Prim order);
+        // every value ever stored in up[v] is an ancestor of v, so updating in
+        // place only moves pointers further up, and ceil(log2 N) rounds suffice
+        for (int round = 0; (1 << round) < N; ++round) {
+            for (int v = lane; v < N; v += 32) up[v] = up[up[v]];
+            __syncwarp();
+        }
+        LabT *dst = pop + (size_t)p * ldp;
+        for (int j = lane; j < ldp; j += 32) dst[j] = (LabT)(j < N ? up[j] : 0);
+        __syncwarp();
+    }
+}
+
+template <typename LabT>
+int launch_init_threshold(LabT *pop, int ldp, int P, int N, const int32_t *order,
+                          const int32_t *from, const double *w, double tau_lo, double tau_hi,
+                          uint32_t k0, uint32_t k1, cudaStream_t s)
+{
+    const size_t smem = (size_t)8 * N * sizeof(int);
+    const int grid = (P + 7) / 8;
+    init_threshold_kernel<LabT><<<grid, 256, smem, s>>>(pop, ldp, P, N, order, from, w, tau_lo, tau_hi - tau_lo, k0, k1);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+template int launch_init_threshold<uint16_t>(uint16_t *, int, int, int, const int32_t *,
+                                             const int32_t *, const double *, double, double,
+                                             uint32_t, uint32_t, cudaStream_t);
+template int launch_init_threshold<int32_t>(int32_t *, int, int, int, const int32_t *,
+                                            const int32_t *, const double *, double, double,
+                                            uint32_t, uint32_t, cudaStream_t);
+
+int prepare_init_kernels(int maxsmem)
+{
+    GPGA_CUDA(cudaFuncSetAttribute(mst_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(init_threshold_kernel<uint16_t>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(init_threshold_kernel<int32_t>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    return GPGA_OK;
+}
+
+} // namespace gpga

@@ -1,0 +1,407 @@
+// score.cu -- Giada-Marsili log-likelihood L_c of a population (Eq. 5, 6, 8),
+// plain form on CUDA cores, plus the FP64 assembly shared with the tensor form
+// and the FP64 final re-score of one configuration.
+//
+// Split of the work (D = 1 - C, symmetric, zero diagonal for a Pearson C):
+//   d_s = sum_{i,j in s} D_ij = sum_{i in s} (2 u_i + D_ii),
+//   u_i = sum_{j > i, s_j = s_i} D_ij        (pair kernel, FP32, upper triangle)
+//   n_s, d_s per cluster -> c_s = n_s^2 - d_s -> Eq. 8 terms in FP64 (assembly)
+// Accumulating 1 - C_ij directly keeps n_s^2 - c_s free of cancellation.
+#include <math.h>
+
+#include "gpga_internal.cuh"
+
+namespace gpga {
+
+int fix_bits_for(int N)
+{
+    // 2 N^2 2^bits < 2^62 with margin
+    double need = log2(2.0 * (double)N * (double)N + 1.0);
+    int bits = 61 - (int)ceil(need);
+    if (bits > 40) bits = 40;
+    if (bits < 20) bits = 20;
+    return bits;
+}
+
+// ---------------------------------------------------------------------------
+// D forms: D32 = fp32(1 - (C + C^T)/2), Dhi = bf16(D), Dlo = bf16(D - Dhi),
+// all Np x Np, zero outside N x N; logtab[k] = log(k) for k = 1..N.
+// ---------------------------------------------------------------------------
+__global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int Np,
+                              float *__restrict__ D32, __nv_bfloat16 *__restrict__ Dhi,
+                              __nv_bfloat16 *__restrict__ Dlo, double *__restrict__ logtab)
+{
+    const size_t total = (size_t)Np * Np;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / Np), j = (int)(idx - (size_t)i * Np);
+        double d = 0.0;
+        if (i < N && j < N) {
+            const double cij = C[(size_t)i * ldc + j], cji = C[(size_t)j * ldc + i];
+            d = 1.0 - 0.5 * (cij + cji);
+        }
+        const float df = (float)d;
+        D32[idx] = df;
+        if (Dhi) {
+            const __nv_bfloat16 hi = __double2bfloat16(d);
+            const double rem = d - (double)__bfloat162float(hi);
+            Dhi[idx] = hi;
+            Dlo[idx] = __double2bfloat16(rem);
+        }
+    }
+    if (logtab) {
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= N; k += gridDim.x * blockDim.x)
+            logtab[k] = k > 0 ? log((double)k) : 0.0;
+    }
+}
+
+int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,
+                  __nv_bfloat16 *Dlo, double *logtab, cudaStream_t s)
+{
+    const size_t total = (size_t)Np * Np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, logtab);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pair kernel (plain form, row u_i of the upper triangle).
+//
+// A CTA of 8 warps owns IPC individuals per group and G groups (G > 1 only for
+// small N). Rows are cut into 32-row blocks I (NB = Np/32); row block I needs
+// the tiles (I, J >= I): NB - I of them. Block I is paired with block NB-1-I so
+// that every warp item costs NB + 1 tiles. Lane l of a warp owns row
+// i = 32 I + l of all IPC individuals: per column j it loads D_ij once (a
+// coalesced 128-byte row of the symmetric D from L2) and compares s_j with s_i
+// for the IPC individuals (labels transposed in shared memory, one broadcast
+// 16-byte load per 4 individuals). The only per-pair work is compare + add.
+// ---------------------------------------------------------------------------
+template <typename LabT, int IPC>
+__global__ void __launch_bounds__(256, 2)
+    pair_plain_kernel(const float *__restrict__ D, int Np, const LabT *lab0, const LabT *lab1,
+                      int ldl, int sel_off, int P, int N, float *__restrict__ acc_out,
+                      const DevState *__restrict__ st)
+{
+    const LabT *__restrict__ lab = lab0;
+    if (st) {
+        if (st->done) return;
+        lab = ((st->gen + sel_off) & 1) ? lab1 : lab0;
+    }
+    extern __shared__ int4 smem_i4[];
+    int *lab_s = reinterpret_cast<int *>(smem_i4);
+    const int NB = Np >> 5;
+    const int npairs = (NB + 1) >> 1;
+    const int G = npairs >= 8 ? 1 : (8 / npairs);
+    const int p_base = blockIdx.x * G * IPC;
+
+    // labels, transposed: lab_s[(g * Np + j) * IPC + q]
+    for (int idx = threadIdx.x; idx < G * IPC * Np; idx += blockDim.x) {
+        const int gq = idx / Np, j = idx - gq * Np;
+        const int p = p_base + gq;
+        int v = 0x7fffffff; // padding genes: D is zero there anyway
+        if (p < P && j < N) v = (int)lab[(size_t)p * ldl + j];
+        const int g = gq / IPC, q = gq - g * IPC;
+        lab_s[(g * Np + j) * IPC + q] = v;
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int items = G * npairs;
+    for (int it = warp; it < items; it += 8) {
+        const int g = it / npairs, t = it - g * npairs;
+        const int *ls = lab_s + (size_t)g * Np * IPC;
+        const int pg = p_base + g * IPC;
+        for (int half = 0; half < 2; ++half) {
+            const int I = half ? (NB - 1 - t) : t;
+            if (half && I == t) break;
+            const int i = (I << 5) + lane;
+            int my[IPC];
+            float acc[IPC];
+#pragma unroll
+            for (int q4 = 0; q4 < IPC / 4; ++q4) {
+                const int4 v = *reinterpret_cast<const int4 *>(ls + i * IPC + 4 * q4);
+                my[4 * q4 + 0] = v.x;
+                my[4 * q4 + 1] = v.y;
+                my[4 * q4 + 2] = v.z;
+                my[4 * q4 + 3] = v.w;
+            }
+#pragma unroll
+            for (int q = 0; q < IPC; ++q) acc[q] = 0.f;
+
+            for (int J = I; J < NB; ++J) {
+                float dv[32];
+                const float *Dp = D + (size_t)(J << 5) * Np + i;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) dv[jj] = __ldg(Dp + (size_t)jj * Np);
+                if (J == I) {
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj)
+                        if (jj <= lane) dv[jj] = 0.f;
+                }
+                const int *lj = ls + (J << 5) * IPC;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+#pragma unroll
+                    for (int q4 = 0; q4 < IPC / 4; ++q4) {
+                        const int4 v = *reinterpret_cast<const int4 *>(lj + jj * IPC + 4 * q4);
+                        if (v.x == my[4 * q4 + 0]) acc[4 * q4 + 0] += dv[jj];
+                        if (v.y == my[4 * q4 + 1]) acc[4 * q4 + 1] += dv[jj];
+                        if (v.z == my[4 * q4 + 2]) acc[4 * q4 + 2] += dv[jj];
+                        if (v.w == my[4 * q4 + 3]) acc[4 * q4 + 3] += dv[jj];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < IPC; ++q)
+                if (pg + q < P) acc_out[(size_t)(pg + q) * Np + i] = acc[q];
+        }
+    }
+}
+
+template <typename LabT>
+int launch_pair_plain(const float *D32, int Np, const LabT *const *lab2, int ldl, int sel_off,
+                      int P, int N, float *acc, const DevState *st, cudaStream_t s)
+{
+    const int NB = Np >> 5;
+    const int npairs = (NB + 1) >> 1;
+    const int G = npairs >= 8 ? 1 : (8 / npairs);
+    if (Np <= 2048) {
+        constexpr int IPC = 16;
+        const size_t smem = (size_t)G * Np * IPC * sizeof(int);
+        const int per_cta = G * IPC;
+        const int grid = (P + per_cta - 1) / per_cta;
+        pair_plain_kernel<LabT, IPC><<<grid, 256, smem, s>>>(D32, Np, lab2[0], lab2[1], ldl,
+                                                             sel_off, P, N, acc, st);
+    } else {
+        constexpr int IPC = 8;
+        const size_t smem = (size_t)G * Np * IPC * sizeof(int);
+        const int per_cta = G * IPC;
+        const int grid = (P + per_cta - 1) / per_cta;
+        pair_plain_kernel<LabT, IPC><<<grid, 256, smem, s>>>(D32, Np, lab2[0], lab2[1], ldl,
+                                                             sel_off, P, N, acc, st);
+    }
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Assembly (Eq. 5 and Eq. 8): one warp per individual. Row sums are turned into
+// fixed point and added into per-label bins with integer shared-memory atomics,
+// so d_s is independent of the order of the additions (the score is
+// deterministic). Then, per label with n_s > 1,
+//   t_s = 1/2 [ log n_s - log c_s + (n_s - 1)(log n_s + log(n_s - 1) - log d_s) ]
+// in FP64 (log of the integers from a table), summed per lane in ascending s and
+// across lanes by a fixed butterfly.
+//   full_rows = 0: row value = 2 u_i + D_ii (upper-triangle sums of the plain form)
+//   full_rows = 1: row value = y_i = sum_j D_ij [s_j = s_i] (tensor form)
+// ---------------------------------------------------------------------------
+template <typename LabT>
+__global__ void __launch_bounds__(256)
+    assemble_kernel(const LabT *lab0, const LabT *lab1, int ldl, int sel_off,
+                    const float *__restrict__ acc, int Np, const float *__restrict__ D32,
+                    int full_rows, int P, int N, const double *__restrict__ logtab, int fix_bits,
+                    double *__restrict__ L, int *__restrict__ err, const DevState *__restrict__ st)
+{
+    const LabT *__restrict__ lab = lab0;
+    if (st) {
+        if (st->done) return;
+        lab = ((st->gen + sel_off) & 1) ? lab1 : lab0;
+    }
+    extern __shared__ unsigned long long smem_u64[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    unsigned long long *dfx = smem_u64 + (size_t)warp * Np;
+    int *cnt = reinterpret_cast<int *>(smem_u64 + (size_t)nw * Np) + warp * Np;
+    const float fscale = exp2f((float)fix_bits);
+    const double inv = exp2(-(double)fix_bits);
+    const double cl_eps = 9.094947017729282e-13; // 2^-40
+
+    for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
+        for (int s = lane; s < N; s += 32) {
+            cnt[s] = 0;
+            dfx[s] = 0ull;
+        }
+        __syncwarp();
+        bool bad = false;
+        const LabT *lp = lab + (size_t)p * ldl;
+        const float *ap = acc + (size_t)p * Np;
+        for (int i = lane; i < N; i += 32) {
+            const int s = (int)lp[i];
+            if (s < 0 || s >= N) {
+                bad = true;
+                continue;
+            }
+            const float y = ap[i];
+            long long f;
+            if (full_rows) {
+                f = __float2ll_rn(y * fscale);
+            } else {
+                f = __float2ll_rn((2.f * y) * fscale) +
+                    __float2ll_rn(D32[(size_t)i * Np + i] * fscale);
+            }
+            atomicAdd(&cnt[s], 1);
+            atomicAdd(&dfx[s], (unsigned long long)f);
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        __syncwarp();
+        double part = 0.0;
+        for (int s = lane; s < N; s += 32) {
+            const int n = cnt[s];
+            if (n >= 2) {
+                const double dn = (double)n;
+                double d = (double)(long long)dfx[s] * inv;
+                double c = dn * dn - d;
+                const double cmin = dn * cl_eps, dmin = dn * (dn - 1.0) * cl_eps;
+                if (!(c >= cmin)) c = cmin;
+                if (!(d >= dmin)) d = dmin;
+                const double ln = logtab[n], ln1 = logtab[n - 1];
+                part += 0.5 * ((ln - log(c)) + (dn - 1.0) * ((ln + ln1) - log(d)));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) {
+            L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : part;
+            if (bad && err) atomicOr(err, 1);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename LabT>
+int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *acc, int Np,
+                    const float *D32, int full_rows, int P, int N, const double *logtab,
+                    double *L, int *err, const DevState *st, cudaStream_t s)
+{
+    // 8 warps (one individual each) unless the per-warp bins of a large N need
+    // fewer to fit the 227 KB of shared memory
+    const size_t per_warp = (size_t)Np * (sizeof(unsigned long long) + sizeof(int));
+    int nw = 8;
+    while (nw > 1 && nw * per_warp > (size_t)200 * 1024) nw >>= 1;
+    const size_t smem = nw * per_warp;
+    const int grid = (P + nw - 1) / nw;
+    assemble_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, acc, Np, D32,
+                                                  full_rows, P, N, logtab, fix_bits_for(N), L,
+                                                  err, st);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+template int launch_pair_plain<uint16_t>(const float *, int, const uint16_t *const *, int, int,
+                                         int, int, float *, const DevState *, cudaStream_t);
+template int launch_pair_plain<int32_t>(const float *, int, const int32_t *const *, int, int,
+                                        int, int, float *, const DevState *, cudaStream_t);
+template int launch_assemble<uint16_t>(const uint16_t *const *, int, int, const float *, int,
+                                       const float *, int, int, int, const double *, double *,
+                                       int *, const DevState *, cudaStream_t);
+template int launch_assemble<int32_t>(const int32_t *const *, int, int, const float *, int,
+                                      const float *, int, int, int, const double *, double *,
+                                      int *, const DevState *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Final re-score of one configuration in FP64 straight from C (Eq. 5, 6, 8),
+// plus its canonical relabelling (first occurrence -> 0, 1, 2, ...). One CTA.
+// Row sums are sequential in j; cluster sums run over members in ascending i;
+// terms are added in first-occurrence order with compensation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void neu_add(double &s, double &c, double x)
+{
+    const double t = s + x;
+    if (fabs(s) >= fabs(x))
+        c += (s - t) + x;
+    else
+        c += (x - t) + s;
+    s = t;
+}
+
+__global__ void __launch_bounds__(1024)
+    rescore_kernel(const uint16_t *pop0, const uint16_t *pop1, int ldp,
+                   const DevState *__restrict__ st, const double *__restrict__ C, int N,
+                   int32_t *__restrict__ canon, double *__restrict__ L_out)
+{
+    const uint16_t *lab = ((st->gen & 1) ? pop1 : pop0) + (size_t)st->best_idx * ldp;
+    extern __shared__ double sm_d[];
+    double *rc = sm_d;          // N row sums of C over same-cluster columns
+    double *rd = sm_d + N;      // N row sums of (1 - C)
+    int *li = reinterpret_cast<int *>(sm_d + 2 * N); // labels
+    int *map = li + N;          // label -> canonical id
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        li[i] = lab[i];
+        map[i] = -1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double sc = 0.0, cc = 0.0, sd = 0.0, cd = 0.0;
+        const int si = li[i];
+        for (int j = 0; j < N; ++j) {
+            if (li[j] != si) continue;
+            const double v = C[(size_t)i * N + j];
+            neu_add(sc, cc, v);
+            neu_add(sd, cd, 1.0 - v);
+        }
+        rc[i] = sc + cc;
+        rd[i] = sd + cd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int next = 0;
+        double acc = 0.0, comp = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const int s = li[i];
+            if (map[s] >= 0) continue;
+            map[s] = next++;
+            // members of s are i and later indices with the same label
+            int n = 0;
+            double c = 0.0, cc = 0.0, d = 0.0, dc = 0.0;
+            for (int j = i; j < N; ++j) {
+                if (li[j] != s) continue;
+                ++n;
+                neu_add(c, cc, rc[j]);
+                neu_add(d, dc, rd[j]);
+            }
+            if (n >= 2) {
+                const double dn = (double)n;
+                double cs = c + cc, ds = d + dc;
+                const double eps = 9.094947017729282e-13;
+                if (!(cs >= dn * eps)) cs = dn * eps;
+                if (!(ds >= dn * (dn - 1.0) * eps)) ds = dn * (dn - 1.0) * eps;
+                const double term = 0.5 * (log(dn / cs) + (dn - 1.0) * log((dn * dn - dn) / ds));
+                neu_add(acc, comp, term);
+            }
+        }
+        *L_out = acc + comp;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) canon[i] = map[li[i]];
+}
+
+int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
+                        const double *C, int N, int32_t *canon_out, double *L_out, cudaStream_t s)
+{
+    const size_t smem = (size_t)N * (2 * sizeof(double) + 2 * sizeof(int));
+    rescore_kernel<<<1, 1024, smem, s>>>(pop0, pop1, ldp, st, C, N, canon_out, L_out);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+int prepare_score_kernels(int maxsmem)
+{
+    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<uint16_t, 16>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<uint16_t, 8>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<int32_t, 16>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<int32_t, 8>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(assemble_kernel<uint16_t>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(assemble_kernel<int32_t>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    GPGA_CUDA(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   maxsmem));
+    return GPGA_OK;
+}
+
+} // namespace gpga

@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libgpga.so (include/gpga.h): argument marshalling only.
+
+Every computation runs in the library's sm_103a kernels. PyTorch supplies device
+memory and streams. There is no CPU fallback: if the library is missing or fails
+to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgpga.so")
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6
+FORM_PLAIN, FORM_TENSOR = 0, 1
+SCALING_RANK, SCALING_PROP = 0, 1
+INIT_UNIFORM, INIT_THRESHOLD = 0, 1
+MAX_N, MAX_P = 4096, 16384
+
+EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score", "ga_evolve",
+           "ga_init", "ga_reset", "ga_step", "ga_best", "ga_history", "ga_kernel_times",
+           "ga_population", "ga_free"]
+
+
+class GpgaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gpga status {code}: {msg}")
+        self.code = code
+
+
+class Params(ct.Structure):
+    """Mirror of struct gpga_params."""
+
+    _fields_ = [
+        ("P", ct.c_int32),
+        ("elite", ct.c_int32),
+        ("max_gens", ct.c_int32),
+        ("stall_gens", ct.c_int32),
+        ("tol", ct.c_double),
+        ("pc", ct.c_double),
+        ("pkb", ct.c_double),
+        ("pm", ct.c_double),
+        ("scaling", ct.c_int32),
+        ("form", ct.c_int32),
+        ("init", ct.c_int32),
+        ("init_labels", ct.c_int32),
+        ("tau_lo", ct.c_double),
+        ("tau_hi", ct.c_double),
+        ("record", ct.c_int32),
+        ("profile", ct.c_int32),
+        ("reserved", ct.c_int32 * 2),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ct.CDLL:
+    """Load libgpga.so (build it first with paper_1403_4099_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first "
+                               "(there is no fallback implementation)")
+        L = ct.CDLL(LIB_PATH)
+        vp, i32, f64 = ct.c_void_p, ct.c_int, ct.c_double
+        sigs = {
+            "gpga_default_params": (i32, [ct.POINTER(Params)]),
+            "gpga_last_error": (ct.c_char_p, []),
+            "cluster_corr": (i32, [vp, i32, i32, i32, vp, vp]),
+            "ga_score": (i32, [vp, i32, i32, i32, vp, vp, i32, vp]),
+            "ga_evolve": (i32, [vp, vp, i32, ct.POINTER(Params), ct.c_uint64, i32, vp, vp, vp, vp]),
+            "ga_init": (i32, [vp, i32, ct.POINTER(Params), ct.c_uint64, vp, ct.POINTER(vp)]),
+            "ga_reset": (i32, [vp, vp, ct.c_uint64]),
+            "ga_step": (i32, [vp, i32, ct.POINTER(i32)]),
+            "ga_best": (i32, [vp, vp, vp, ct.POINTER(i32)]),
+            "ga_history": (i32, [vp, vp, vp, vp, i32, ct.POINTER(i32)]),
+            "ga_kernel_times": (i32, [vp, vp, i32, ct.POINTER(i32)]),
+            "ga_population": (i32, [vp, vp, vp]),
+            "ga_free": (i32, [vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise GpgaError(rc, lib().gpga_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype_name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ct.c_void_p(t.data_ptr())
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(lib().gpga_default_params(ct.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def cluster_corr(R, C=None, stream=None):
+    """Pearson C (N x N FP64, device) of returns R (T x N FP64, device)."""
+    import torch
+    T, N = R.shape
+    if C is None:
+        C = torch.empty((N, N), dtype=torch.float64, device=R.device)
+    _check(lib().cluster_corr(_dev(R, "float64"), T, N, N, _dev(C, "float64"),
+                              _stream_ptr(stream)))
+    return C
+
+
+def ga_score(labels, C, form: int = FORM_PLAIN, L=None, stream=None):
+    """L_c (P FP64, device) of labels (P x N int32, device) against C (device)."""
+    import torch
+    P, N = labels.shape
+    if L is None:
+        L = torch.empty(P, dtype=torch.float64, device=labels.device)
+    _check(lib().ga_score(_dev(labels, "int32"), P, N, N, _dev(C, "float64"), _dev(L, "float64"),
+                          int(form), _stream_ptr(stream)))
+    return L
+
+
+def ga_evolve(pop, L, params: Params, seed: int, generation: int, stream=None):
+    """One stateless generation; returns (next, perm, parents) device tensors."""
+    import torch
+    P, N = pop.shape
+    if P != params.P:
+        raise ValueError("pop rows must equal params.P")
+    nxt = torch.empty_like(pop)
+    perm = torch.empty(P, dtype=torch.int32, device=pop.device)
+    par = torch.empty(P - params.elite, dtype=torch.int32, device=pop.device)
+    _check(lib().ga_evolve(_dev(pop, "int32"), _dev(L, "float64"), N, ct.byref(params),
+                           ct.c_uint64(seed), int(generation), _dev(nxt, "int32"),
+                           _dev(perm, "int32"), _dev(par, "int32") if par.numel() else None,
+                           _stream_ptr(stream)))
+    return nxt, perm, par
+
+
+class GA:
+    """A device-resident GA run (ga_init / ga_step / ga_best / ga_free)."""
+
+    def __init__(self, C, params: Params, seed: int, stream=None):
+        self.N = C.shape[0]
+        self.params = params
+        self._stream = stream
+        h = ct.c_void_p()
+        _check(lib().ga_init(_dev(C, "float64"), self.N, ct.byref(params), ct.c_uint64(seed),
+                             _stream_ptr(stream), ct.byref(h)))
+        self._h = h
+
+    def reset(self, C, seed: int):
+        _check(lib().ga_reset(self._h, _dev(C, "float64"), ct.c_uint64(seed)))
+
+    def step(self, generations: int, wait: bool = False):
+        if wait:
+            d = ct.c_int()
+            _check(lib().ga_step(self._h, int(generations), ct.byref(d)))
+            return bool(d.value)
+        _check(lib().ga_step(self._h, int(generations), None))
+        return None
+
+    def best(self, labels_out=None, L_out=None):
+        """(canonical labels, FP64 re-scored L, generation). Outputs may be given
+        as host numpy arrays or device tensors; by default host numpy."""
+        g = ct.c_int()
+        if labels_out is None and L_out is None:
+            lab = np.zeros(self.N, np.int32)
+            Lb = np.zeros(1, np.float64)
+            _check(lib().ga_best(self._h, lab.ctypes.data, Lb.ctypes.data, ct.byref(g)))
+            return lab, float(Lb[0]), g.value
+        lp = _ptr(labels_out)
+        Lp = _ptr(L_out)
+        _check(lib().ga_best(self._h, lp, Lp, ct.byref(g)))
+        return labels_out, L_out, g.value
+
+    def history(self):
+        cap = self.params.max_gens + 1
+        bl = np.zeros(cap, np.float64)
+        n = ct.c_int()
+        if self.params.record:
+            lab = np.zeros((cap, self.N), np.int32)
+            ts = np.zeros(cap + 1, np.int64)
+            _check(lib().ga_history(self._h, bl.ctypes.data, lab.ctypes.data, ts.ctypes.data,
+                                    cap, ct.byref(n)))
+            k = n.value
+            return dict(best_L=bl[:k], labels=lab[:k], t_ns=ts[:k + 1])
+        _check(lib().ga_history(self._h, bl.ctypes.data, None, None, cap, ct.byref(n)))
+        return dict(best_L=bl[: n.value])
+
+    def kernel_times(self):
+        """(count x 4) ms of [evolve, pair/contraction, assembly, selection] for the
+        generations of the last graph launch (params.profile must be set)."""
+        ms = np.zeros((8, 4), np.float32)
+        n = ct.c_int()
+        _check(lib().ga_kernel_times(self._h, ms.ctypes.data, 8, ct.byref(n)))
+        return ms[: n.value]
+
+    def population(self):
+        pop = np.zeros((self.params.P, self.N), np.int32)
+        L = np.zeros(self.params.P, np.float64)
+        _check(lib().ga_population(self._h, pop.ctypes.data, L.ctypes.data))
+        return pop, L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ga_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ct.c_void_p(x.ctypes.data)
+    return ct.c_void_p(x.data_ptr())

@@ -1,0 +1,176 @@
+"""GPU GA generation against the oracle: bit-exact operators given the same
+fitness vector and Philox key, the stateful pipeline's wiring generation by
+generation, initial populations, termination, and end-to-end recovery."""
+import numpy as np
+import pytest
+
+from paper_1403_4099_gb300 import synth
+from gpu_util import assert_L_close, dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1403_4099_gb300 import build, gpga
+    build.build()
+    return gpga
+
+
+def _gparams(g, P, E=2, **kw):
+    return g.default_params(P=P, elite=E, **kw)
+
+
+def _oparams(orc, gp, N):
+    return orc.params(gp.P, N, elite=gp.elite, max_gens=gp.max_gens, stall_gens=gp.stall_gens,
+                      tol=gp.tol, pc=gp.pc, pkb=gp.pkb, pm=gp.pm, scaling=gp.scaling,
+                      init_labels=gp.init_labels)
+
+
+CASES = [
+    # P, N, E, pc, pkb, pm, scaling, generation
+    (64, 16, 2, 0.9, 0.9, 0.01, 0, 0),
+    (1000, 100, 10, 0.9, 0.9, 0.1, 0, 7),
+    (37, 5, 0, 1.0, 0.5, 0.2, 0, 3),
+    (4096, 500, 10, 0.9, 0.9, 0.01, 0, 12345),
+    (333, 65, 5, 0.7, 0.3, 0.05, 1, 2),
+    (2, 2, 1, 1.0, 1.0, 1.0, 0, 1),
+    (129, 31, 128, 0.9, 0.9, 0.5, 1, 9),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_evolve_bit_exact(g, orc, case):
+    import torch
+    P, N, E, pc, pkb, pm, scaling, gen = case
+    rng = np.random.default_rng(P + N)
+    pop = rng.integers(0, N, (P, N)).astype(np.int32)
+    L = np.round(rng.standard_normal(P) * 3, 2)  # ties
+    L[rng.integers(0, P, 3)] = -np.inf
+    L[rng.integers(0, P)] = np.nan
+    if scaling == 1:
+        L = np.abs(np.nan_to_num(L, nan=0.5, neginf=0.0))
+    seed = 0xDEADBEEF12345 + P
+    gp = _gparams(g, P, E, pc=pc, pkb=pkb, pm=pm, scaling=scaling)
+    nxt, perm, par = g.ga_evolve(dev(pop, torch.int32), dev(L), gp, seed, gen)
+    torch.cuda.synchronize()
+    onxt, operm, opar = orc.ga_evolve(pop, L, _oparams(orc, gp, N), seed, gen)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    if P - E:
+        assert np.array_equal(par.cpu().numpy(), opar)
+    assert np.array_equal(nxt.cpu().numpy(), onxt)
+
+
+def test_uniform_init_bit_exact(g, orc):
+    import torch
+    p = synth.n100()
+    C = orc.pearson(p.R)
+    for K0 in (0, 13):
+        gp = _gparams(g, 300, init_labels=K0)
+        ga = g.GA(dev(C), gp, seed=99)
+        pop, L = ga.population()
+        assert np.array_equal(pop, orc.ga_init(300, 100, 99, K0=K0 or None))
+        assert_L_close(L, orc.loglik_batch(pop, C), "gen0")
+        ga.close()
+
+
+def test_threshold_init_bit_exact(g, orc):
+    for which in ("n100", "small16"):
+        p = getattr(synth, which)()
+        C = orc.pearson(p.R)
+        gp = _gparams(g, 257, init=g.INIT_THRESHOLD, tau_lo=0.05, tau_hi=0.6)
+        ga = g.GA(dev(C), gp, seed=1234)
+        pop, _ = ga.population()
+        assert np.array_equal(pop, orc.ga_init_threshold(C, 257, 1234, 0.05, 0.6))
+        ga.close()
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_pipeline_generation_by_generation(g, orc, scaling):
+    """Each device generation equals the oracle's operators applied to the
+    device's own population and fitness (bit-exact), and the device fitness
+    matches the oracle's likelihood of that population."""
+    p = synth.n100()
+    C = orc.pearson(p.R)
+    gp = _gparams(g, 1024, E=10, scaling=scaling, max_gens=50, tol=-1.0, record=1)
+    seed = 4242
+    ga = g.GA(dev(C), gp, seed=seed)
+    op = _oparams(orc, gp, 100)
+    pop, L = ga.population()
+    for gen in range(8):
+        assert_L_close(L, orc.loglik_batch(pop, C), f"gen {gen}")
+        ref_next, _, _ = orc.ga_evolve(pop, L, op, seed, gen)
+        ga.step(1)
+        pop, L = ga.population()
+        assert np.array_equal(pop, ref_next), f"generation {gen + 1}"
+    h = ga.history()
+    assert len(h["best_L"]) == 9 and np.all(np.diff(h["best_L"]) >= 0)
+    assert np.all(np.diff(h["t_ns"]) >= 0)
+    lab, Lb, gen = ga.best()
+    assert gen == 8
+    assert np.array_equal(lab, orc.canonicalize(lab))
+    assert abs(Lb - orc.loglik(lab, C)) <= 1e-10 * max(1, abs(Lb))
+    assert abs(Lb - h["best_L"][-1]) <= 1e-4 + 1e-6 * abs(Lb)
+    ga.close()
+
+
+def test_termination_and_noop_after_done(g, orc):
+    p = synth.small16()
+    C = orc.pearson(p.R)
+    gp = _gparams(g, 64, max_gens=5, tol=-1.0)
+    ga = g.GA(dev(C), gp, seed=5)
+    assert ga.step(3, wait=True) is False
+    assert ga.step(2, wait=True) is True
+    pop5, L5 = ga.population()
+    ga.step(4, wait=True)
+    pop9, L9 = ga.population()
+    assert np.array_equal(pop5, pop9) and np.array_equal(L5, L9)
+    assert ga.best()[2] == 5
+    ga.close()
+    # stall rule: a huge tolerance stops at generation G_stall
+    gp = _gparams(g, 64, max_gens=100, stall_gens=4, tol=1e9)
+    ga = g.GA(dev(C), gp, seed=5)
+    assert ga.step(10, wait=True) is True
+    assert ga.best()[2] == 4
+    ga.close()
+
+
+def test_recovers_small16(g, orc):
+    p = synth.small16()
+    C = orc.pearson(p.R)
+    gp = _gparams(g, 64, max_gens=200, tol=-1.0)
+    ga = g.GA(dev(C), gp, seed=synth.seed_for(1))
+    ga.step(200)
+    lab, L, gen = ga.best()
+    assert gen == 200
+    assert orc.ari(lab, p.truth) >= 0.99
+    ga.close()
+
+
+def test_global_max_n10(g, orc):
+    """Small-workload parameters on N=10: the exhaustive maximum in >= 99 of
+    100 seeds."""
+    p = synth.small10()
+    C = orc.pearson(p.R)
+    _, Lmax, _ = orc.brute_force(C)
+    gp = _gparams(g, 64, max_gens=200, tol=-1.0)
+    ga = g.GA(dev(C), gp, seed=1)
+    hits = 0
+    for k in range(100):
+        ga.reset(dev(C), 1000 + k)
+        ga.step(200)
+        _, L, _ = ga.best()
+        hits += abs(L - Lmax) <= 1e-9 * abs(Lmax)
+    ga.close()
+    assert hits >= 99
+
+
+def test_bad_params_rejected(g, orc):
+    C = orc.pearson(synth.small16().R)
+    for kw in (dict(P=1), dict(elite=64), dict(pm=1.5), dict(scaling=7), dict(form=9)):
+        gp = _gparams(g, 64, **{k: v for k, v in kw.items() if k != "P"})
+        if "P" in kw:
+            gp.P = kw["P"]
+        with pytest.raises(g.GpgaError) as e:
+            g.GA(dev(C), gp, seed=1)
+        assert e.value.code == g.ERR_ARG

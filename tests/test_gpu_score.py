@@ -1,0 +1,111 @@
+"""GPU likelihood (plain FP32 form) against the FP64 oracle, element by element,
+through the C-ABI: |dL| <= 1e-4 + 1e-6 |L| per individual."""
+import numpy as np
+import pytest
+
+from paper_1403_4099_gb300 import synth
+from gpu_util import assert_L_close, dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    from paper_1403_4099_gb300 import build, gpga
+    build.build()
+    assert torch.cuda.is_available()
+    return gpga
+
+
+def _score(g, labels, C, form=0):
+    import torch
+    L = g.ga_score(dev(labels, torch.int32), dev(C), form=form)
+    torch.cuda.synchronize()
+    return L.cpu().numpy()
+
+
+def _cases(rng, truth, P):
+    N = truth.shape[0]
+    return {
+        "uniform": synth.random_labels(rng, P, N),
+        "few_labels": synth.random_labels(rng, P, N, K=max(2, N // 12)),
+        "converged": synth.perturbed_population(rng, truth, P, 0.05),
+    }
+
+
+@pytest.mark.parametrize("form", [0])
+def test_small16(g, orc, form):
+    p = synth.small16()
+    C = orc.pearson(p.R)
+    rng = np.random.default_rng(1)
+    pop = np.concatenate([synth.random_labels(rng, 60, 16),
+                          [p.truth, np.arange(16), np.zeros(16), np.full(16, 15)]]).astype(np.int32)
+    got = _score(g, pop, C, form)
+    ref = orc.loglik_batch(pop, C)
+    assert_L_close(got, ref, "small16")
+    assert got[61] == 0.0  # all singletons contribute nothing
+
+
+@pytest.mark.parametrize("form", [0])
+def test_n100_population(g, orc, form):
+    p = synth.n100()
+    C = orc.pearson(p.R)
+    rng = np.random.default_rng(2)
+    for name, pop in _cases(rng, p.truth, 1024).items():
+        got = _score(g, pop, C, form)
+        assert_L_close(got, orc.loglik_batch(pop, C), f"n100/{name}")
+
+
+@pytest.mark.parametrize("form", [0])
+@pytest.mark.parametrize("N", [2, 3, 31, 33, 63, 64, 65, 127, 129, 200, 1000, 2100])
+def test_ragged_sizes(g, orc, form, N):
+    rng = np.random.default_rng(N)
+    R = rng.standard_normal((3 * N + 5, N)) + rng.standard_normal((3 * N + 5, 1))
+    C = orc.pearson(R)
+    for P in (1, 7, 33):
+        pop = synth.random_labels(rng, P, N, K=max(1, N // 5))
+        got = _score(g, pop, C, form)
+        assert_L_close(got, orc.loglik_batch(pop, C), f"N={N} P={P}")
+
+
+@pytest.mark.parametrize("form", [0])
+def test_full_size_n500_p4096(g, orc, form):
+    """The benchmark's workload size, in the benchmark's launch shape: every
+    individual compared (the oracle needs seconds)."""
+    p = synth.n500()
+    C = orc.pearson(p.R)
+    rng = np.random.default_rng(3)
+    errs = {}
+    for name, pop in _cases(rng, p.truth, 4096).items():
+        got = _score(g, pop, C, form)
+        errs[name] = assert_L_close(got, orc.loglik_batch(pop, C), f"n500/{name}")
+    print("max |dL|", errs)
+
+
+def test_deterministic_and_relabel_invariant(g, orc):
+    p = synth.n100()
+    C = orc.pearson(p.R)
+    rng = np.random.default_rng(4)
+    pop = synth.perturbed_population(rng, p.truth, 256, 0.1)
+    a = _score(g, pop, C)
+    b = _score(g, pop, C)
+    assert np.array_equal(a, b)
+    pi = rng.permutation(100).astype(np.int32)
+    c = _score(g, pi[pop], C)
+    assert np.all(np.abs(c - a) <= 1e-12 * np.maximum(1, np.abs(a)))
+
+
+def test_invalid_label_is_reported(g, orc):
+    p = synth.small16()
+    C = orc.pearson(p.R)
+    pop = np.tile(p.truth, (4, 1)).astype(np.int32)
+    pop[2, 5] = 16
+    import torch
+    L = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(g.GpgaError) as e:
+        g.ga_score(dev(pop, torch.int32), dev(C), L=L)
+    assert e.value.code == g.ERR_ARG
+    torch.cuda.synchronize()
+    Lh = L.cpu().numpy()
+    assert np.isnan(Lh[2]) and np.all(np.isfinite(Lh[[0, 1, 3]]))

@@ -181,3 +181,44 @@ def test_run_elitism_monotone_and_recovers_small16(orc):
     assert orc.ari(out["best"], p.truth) >= 0.99
     assert out["L"] == orc.loglik(out["best"], C)
     assert np.array_equal(out["ring"][-1], out["best"])
+
+
+def test_threshold_init_matches_scipy_components(orc):
+    """Components of {C > tau} against scipy's connected_components (a library
+    routine), for the tau each individual draws."""
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    from scipy.sparse import csr_matrix
+    p = synth.n100()
+    C = orc.pearson(p.R)
+    pop = orc.ga_init_threshold(C, 40, seed=77, tau_lo=0.05, tau_hi=0.6)
+    seen_tau = []
+    for q in range(40):
+        w = orc.philox((0, q, 0, 4), (77, 0))
+        tau = 0.05 + (0.6 - 0.05) * (float(w[0]) * 2.0 ** -32)
+        seen_tau.append(tau)
+        A = csr_matrix(np.triu(C > tau, 1))
+        _, comp = sp.connected_components(A, directed=False)
+        assert orc.ari(pop[q], comp.astype(np.int32)) == 1.0
+        # label = the member joining Prim's tree first
+        order = orc.prim_order(C)
+        pos = np.empty(100, np.int64); pos[order] = np.arange(100)
+        for lab in np.unique(pop[q]):
+            members = np.flatnonzero(pop[q] == lab)
+            assert lab == members[np.argmin(pos[members])]
+    assert max(seen_tau) - min(seen_tau) > 0.3
+
+
+def test_prim_order_is_a_maximum_spanning_tree(orc):
+    """Total weight of the tree Prim's order implies equals scipy's minimum
+    spanning tree of -C (a library routine)."""
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    rng = np.random.default_rng(21)
+    C = orc.pearson(rng.standard_normal((60, 30)))
+    order = orc.prim_order(C)
+    assert sorted(order.tolist()) == list(range(30)) and order[0] == 0
+    # attach each vertex to its best earlier vertex: the Prim tree
+    tot = 0.0
+    for k in range(1, 30):
+        tot += max(C[order[k], order[:k]])
+    mst = sp.minimum_spanning_tree(-(C - np.eye(30)) + 10.0)  # shift keeps weights positive
+    assert abs((-(mst.sum() - 10.0 * 29)) - tot) < 1e-9
