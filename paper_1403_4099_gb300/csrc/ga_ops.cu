@@ -444,10 +444,8 @@ template int launch_evolve<int32_t>(const int32_t *const *, int32_t *const *, co
 
 int prepare_ga_kernels(int maxsmem)
 {
-    GPGA_CUDA(cudaFuncSetAttribute(select_kernel<uint16_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(select_kernel<int32_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    if (int rc = raise_smem(select_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(select_kernel<int32_t>, maxsmem)) return rc;
     return GPGA_OK;
 }
 

@@ -110,6 +110,17 @@ int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *
 int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
                         const double *C, int N, int32_t *canon_out, double *L_out, cudaStream_t s);
 
+// raise a kernel's dynamic shared-memory limit to what the device allows beside
+// the kernel's static shared memory
+template <typename F> inline int raise_smem(F *f, int maxsmem)
+{
+    cudaFuncAttributes a;
+    GPGA_CUDA(cudaFuncGetAttributes(&a, (const void *)f));
+    GPGA_CUDA(cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   maxsmem - (int)a.sharedSizeBytes));
+    return GPGA_OK;
+}
+
 // one-time per-device raise of the dynamic shared-memory limit of the kernels
 // that need more than 48 KB (outside any stream capture)
 int prepare_score_kernels(int maxsmem);

@@ -169,12 +169,9 @@ template int launch_init_threshold<int32_t>(int32_t *, int, int, int, const int3
 
 int prepare_init_kernels(int maxsmem)
 {
-    GPGA_CUDA(cudaFuncSetAttribute(mst_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(init_threshold_kernel<uint16_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(init_threshold_kernel<int32_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    if (int rc = raise_smem(mst_kernel, maxsmem)) return rc;
+    if (int rc = raise_smem(init_threshold_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(init_threshold_kernel<int32_t>, maxsmem)) return rc;
     return GPGA_OK;
 }
 

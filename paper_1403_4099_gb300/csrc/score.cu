@@ -387,20 +387,13 @@ int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, con
 
 int prepare_score_kernels(int maxsmem)
 {
-    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<uint16_t, 16>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<uint16_t, 8>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<int32_t, 16>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(pair_plain_kernel<int32_t, 8>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(assemble_kernel<uint16_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(assemble_kernel<int32_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
-    GPGA_CUDA(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   maxsmem));
+    if (int rc = raise_smem(pair_plain_kernel<uint16_t, 16>, maxsmem)) return rc;
+    if (int rc = raise_smem(pair_plain_kernel<uint16_t, 8>, maxsmem)) return rc;
+    if (int rc = raise_smem(pair_plain_kernel<int32_t, 16>, maxsmem)) return rc;
+    if (int rc = raise_smem(pair_plain_kernel<int32_t, 8>, maxsmem)) return rc;
+    if (int rc = raise_smem(assemble_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(assemble_kernel<int32_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(rescore_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }
 
