@@ -145,8 +145,19 @@ __device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t
     return ((uint64_t)q[1] << 32) | q[2];
 }
 
+// FP64 fitness as an unsigned key with the same order (NaN mapped to -inf and
+// -0 to +0 first): flip all bits of negatives, set the sign bit of the rest. Integer compares
+// keep the sort off the FP64 pipe.
+__device__ __forceinline__ unsigned long long order_key(double x)
+{
+    if (isnan(x)) x = -INFINITY;
+    if (x == 0.0) x = 0.0; // -0 ties with +0, as in an FP64 comparison
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // strict "fitter than" of (key, index) pairs: key descending, index ascending
-__device__ __forceinline__ bool fitter(double ka, int ia, double kb, int ib)
+__device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned long long kb, int ib)
 {
     return ka > kb || (ka == kb && ia < ib);
 }
@@ -168,7 +179,7 @@ __global__ void __launch_bounds__(1024)
                   const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
                   unsigned long long *__restrict__ ts, int Pp)
 {
-    extern __shared__ double sm_key[];
+    extern __shared__ unsigned long long sm_key[];
     int *sm_idx = reinterpret_cast<int *>(sm_key + Pp);
     __shared__ int s_done;
     __shared__ double s_red[32];
@@ -183,12 +194,7 @@ __global__ void __launch_bounds__(1024)
     }
     const int P = cfg.P;
     for (int i = tid; i < Pp; i += nt) {
-        double k = -INFINITY;
-        if (i < P) {
-            k = L[i];
-            if (isnan(k)) k = -INFINITY;
-        }
-        sm_key[i] = k;
+        sm_key[i] = i < P ? order_key(L[i]) : 0ull; // padding below every real key
         sm_idx[i] = i;
     }
     __syncthreads();
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(1024)
             for (int t = tid; t < (Pp >> 1); t += nt) {
                 const int i = ((t / j) * 2 * j) + (t % j);
                 const int l = i + j;
-                const double ki = sm_key[i], kl = sm_key[l];
+                const unsigned long long ki = sm_key[i], kl = sm_key[l];
                 const int ii = sm_idx[i], il = sm_idx[l];
                 const bool up = (i & k) == 0;
                 const bool swap = up ? fitter(kl, il, ki, ii) : fitter(ki, ii, kl, il);
@@ -221,8 +227,9 @@ __global__ void __launch_bounds__(1024)
         for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if ((tid & 31) == 0) s_red[tid >> 5] = part;
         __syncthreads();
-        const double best = sm_key[0];
         const int bidx = sm_idx[0];
+        double best = L[bidx];
+        if (isnan(best)) best = -INFINITY;
         if (tid == 0) {
             double m = 0.0;
             for (int w = 0; w < (nt >> 5); ++w) m += s_red[w];
@@ -263,12 +270,13 @@ __global__ void __launch_bounds__(1024)
         for (int r = tid; r < P; r += nt) pre[r] = rank_prefix[r];
         __syncthreads();
     } else {
-        const double lmax = sm_key[0];
+        double lmax = L[sm_idx[0]];
+        if (isnan(lmax)) lmax = -INFINITY;
         __syncthreads();
         for (int r = tid; r < P; r += nt) {
             uint64_t w = 1;
             if (lmax > 0.0) {
-                double x = sm_key[r];
+                double x = L[sm_idx[r]];
                 if (!(x > 0.0)) x = 0.0;
                 w = (uint64_t)floor(__dmul_rn(__ddiv_rn(x, lmax), 4294967296.0));
             }
@@ -299,20 +307,55 @@ __global__ void __launch_bounds__(1024)
         __syncthreads();
     }
 
-    // SUS: M pointers, parent = first rank whose prefix exceeds the pointer
+    // SUS: M pointers, parent = first rank whose prefix exceeds the pointer.
+    // Thread t takes a contiguous run of pointers: the first by exact 128-bit
+    // division, the next ones by exact increments (numerator + 2^32 W, carried
+    // against the divisor M 2^32).
     const uint64_t W = pre[P - 1];
     const U4 w = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
-    for (int k = tid; k < cfg.M; k += nt) {
-        const uint64_t x = sus_pointer((uint32_t)k, w.x, W, (uint32_t)cfg.M);
-        int lo = 0, hi = P - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (pre[mid] > x)
-                hi = mid;
-            else
-                lo = mid + 1;
+    const int M = cfg.M;
+    const int per = (M + nt - 1) / nt;
+    const int k_lo = tid * per, k_hi = min(M, k_lo + per);
+    if (k_lo < k_hi) {
+        uint64_t x = sus_pointer((uint32_t)k_lo, w.x, W, (uint32_t)M);
+        // remainder of the first numerator modulo M 2^32, as (rem_hi < M, rem_lo)
+        const uint64_t num = ((uint64_t)(uint32_t)k_lo << 32) | w.x;
+        const uint64_t plo = num * W, phi = __umul64hi(num, W);
+        // (phi:plo) - x * M * 2^32
+        const uint64_t xm_lo = (x * (uint64_t)M) << 32;
+        const uint64_t xm_hi = __umul64hi(x, (uint64_t)M << 32);
+        uint64_t r_lo = plo - xm_lo;
+        uint64_t r_hi = phi - xm_hi - (plo < xm_lo ? 1ull : 0ull);
+        // step 2^32 W = qs (M 2^32) + rs, qs = W / M, rs = (W mod M) 2^32
+        const uint64_t qs = W / (uint64_t)M, rsm = W % (uint64_t)M;
+        const uint64_t dm = (uint64_t)M; // divisor is dm * 2^32: compare (r_hi:r_lo) >= (dm:0)
+        int lo = 0;
+        for (int k = k_lo; k < k_hi; ++k) {
+            if (k > k_lo) {
+                x += qs;
+                // remainder += rsm * 2^32
+                const uint64_t add_lo = rsm << 32, add_hi = rsm >> 32;
+                const uint64_t nlo = r_lo + add_lo;
+                r_hi = r_hi + add_hi + (nlo < r_lo ? 1ull : 0ull);
+                r_lo = nlo;
+                if (r_hi > (dm >> 32) || (r_hi == (dm >> 32) && r_lo >= (dm << 32))) {
+                    const uint64_t sub_lo = dm << 32, sub_hi = dm >> 32;
+                    const uint64_t n2 = r_lo - sub_lo;
+                    r_hi = r_hi - sub_hi - (r_lo < sub_lo ? 1ull : 0ull);
+                    r_lo = n2;
+                    x += 1;
+                }
+            }
+            int hi = P - 1;
+            while (lo < hi) { // pointers grow with k: the search restarts at the last hit
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid] > x)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            parents[k] = sm_idx[lo];
         }
-        parents[k] = sm_idx[lo];
     }
 }
 
@@ -323,7 +366,7 @@ int launch_select(const double *L, const SelectCfg &cfg, const uint64_t *rank_pr
 {
     int Pp = 1;
     while (Pp < cfg.P) Pp <<= 1;
-    const size_t smem = (size_t)Pp * (sizeof(double) + sizeof(int));
+    const size_t smem = (size_t)Pp * (sizeof(unsigned long long) + sizeof(int));
     select_kernel<LabT><<<1, 1024, smem, s>>>(L, cfg, rank_prefix, perm, parents, st, hist,
                             pop2 ? pop2[0] : nullptr, pop2 ? pop2[1] : nullptr, ring, ts, Pp);
     GPGA_LAUNCH_CHECK();

@@ -245,19 +245,39 @@ __global__ void __launch_bounds__(256)
         }
         bad = __any_sync(0xffffffffu, bad);
         __syncwarp();
-        double part = 0.0;
-        for (int s = lane; s < N; s += 32) {
-            const int n = cnt[s];
-            if (n >= 2) {
-                const double dn = (double)n;
-                double d = (double)(long long)dfx[s] * inv;
-                double c = dn * dn - d;
-                const double cmin = dn * cl_eps, dmin = dn * (dn - 1.0) * cl_eps;
-                if (!(c >= cmin)) c = cmin;
-                if (!(d >= dmin)) d = dmin;
-                const double ln = logtab[n], ln1 = logtab[n - 1];
-                part += 0.5 * ((ln - log(c)) + (dn - 1.0) * ((ln + ln1) - log(d)));
+        // compact the non-singleton clusters to the front of the bins (in place:
+        // every entry moves left, and each chunk is read before it is written) so
+        // that the FP64 log terms run on full warps
+        int nlist = 0;
+        for (int base = 0; base < N; base += 32) {
+            const int s = base + lane;
+            int n = 0;
+            unsigned long long f = 0ull;
+            if (s < N) {
+                n = cnt[s];
+                f = dfx[s];
             }
+            const unsigned m = __ballot_sync(0xffffffffu, n >= 2);
+            __syncwarp();
+            if (n >= 2) {
+                const int k = nlist + __popc(m & ((1u << lane) - 1u));
+                cnt[k] = n;
+                dfx[k] = f;
+            }
+            nlist += __popc(m);
+            __syncwarp();
+        }
+        double part = 0.0;
+        for (int k = lane; k < nlist; k += 32) {
+            const int n = cnt[k];
+            const double dn = (double)n;
+            double d = (double)(long long)dfx[k] * inv;
+            double c = dn * dn - d;
+            const double cmin = dn * cl_eps, dmin = dn * (dn - 1.0) * cl_eps;
+            if (!(c >= cmin)) c = cmin;
+            if (!(d >= dmin)) d = dmin;
+            const double ln = logtab[n], ln1 = logtab[n - 1];
+            part += 0.5 * ((ln - log(c)) + (dn - 1.0) * ((ln + ln1) - log(d)));
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);

@@ -168,9 +168,9 @@ def test_global_max_n10(g, orc):
 def test_bad_params_rejected(g, orc):
     C = orc.pearson(synth.small16().R)
     for kw in (dict(P=1), dict(elite=64), dict(pm=1.5), dict(scaling=7), dict(form=9)):
-        gp = _gparams(g, 64, **{k: v for k, v in kw.items() if k != "P"})
-        if "P" in kw:
-            gp.P = kw["P"]
+        gp = _gparams(g, 64)
+        for k, v in kw.items():
+            setattr(gp, k, v)
         with pytest.raises(g.GpgaError) as e:
             g.GA(dev(C), gp, seed=1)
         assert e.value.code == g.ERR_ARG
