@@ -213,6 +213,15 @@ GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count);
  */
 GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
 
+/*
+ * gpga_log_selftest -- diagnostic with no counterpart in the paper: evaluates
+ * the library's table-driven FP64 logarithm (used for the Eq. 8 log terms) and
+ * CUDA's log on the same n inputs. x: device, n positive normal doubles;
+ * y_table, y_cuda: device, n doubles (written). Asynchronous.
+ */
+GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *y_cuda,
+                               void *stream);
+
 /* ga_free -- release the handle and all its device memory (NULL is a no-op). */
 GPGA_API int ga_free(gpga_ga *h);
 

@@ -104,8 +104,10 @@ struct gpga_ga {
     uint16_t *pop[2] = {nullptr, nullptr};
     double *L = nullptr;
     float *acc = nullptr;
-    int32_t *perm = nullptr, *parents = nullptr;
-    uint64_t *rank_prefix = nullptr;
+    int32_t *perm = nullptr;
+    int *rank = nullptr;
+    unsigned *ticket = nullptr;
+    uint64_t *rank_prefix = nullptr, *work_prefix = nullptr;
     DevState *st = nullptr;
     double *hist = nullptr;
     uint16_t *ring = nullptr;
@@ -148,14 +150,16 @@ size_t carve(gpga_ga *h, char *base)
     h->D32 = c.take<float>(Np * Np);
     h->Dhi = c.take<__nv_bfloat16>(Np * Np);
     h->Dlo = c.take<__nv_bfloat16>(Np * Np);
-    h->logtab = c.take<double>(N + 1);
+    h->logtab = c.take<double>(logtab_len(h->N));
     h->pop[0] = c.take<uint16_t>(P * Np);
     h->pop[1] = c.take<uint16_t>(P * Np);
     h->L = c.take<double>(P);
     h->acc = c.take<float>(P * Np);
     h->perm = c.take<int32_t>(P);
-    h->parents = c.take<int32_t>(P);
+    h->rank = c.take<int>(P);
+    h->ticket = c.take<unsigned>(1);
     h->rank_prefix = c.take<uint64_t>(P);
+    h->work_prefix = c.take<uint64_t>(P);
     h->st = c.take<DevState>(1);
     h->hist = c.take<double>(G);
     h->ring = h->prm.record ? c.take<uint16_t>(G * N) : nullptr;
@@ -213,8 +217,9 @@ SelectCfg select_cfg(const gpga_ga *h, int gen_off)
 int enqueue_select(gpga_ga *h, int gen_off)
 {
     const uint16_t *pop2[2] = {h->pop[0], h->pop[1]};
-    return launch_select<uint16_t>(h->L, select_cfg(h, gen_off), h->rank_prefix, h->perm,
-                                   h->parents, h->st, h->hist, pop2, h->ring, h->ts, h->stream);
+    return launch_select<uint16_t>(h->L, select_cfg(h, gen_off), h->rank, h->perm,
+                                   h->work_prefix, h->ticket, h->st, h->hist, pop2, h->ring,
+                                   h->ts, h->stream);
 }
 
 static int mark(gpga_ga *h, cudaEvent_t *evs, int k)
@@ -240,8 +245,9 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs)
     e.gen = 0;
     const uint16_t *pop2[2] = {h->pop[0], h->pop[1]};
     uint16_t *next2[2] = {h->pop[1], h->pop[0]};
+    const uint64_t *prefix = h->prm.scaling == GPGA_SCALING_PROP ? h->work_prefix : h->rank_prefix;
     int rc = mark(h, evs, 0);
-    if (!rc) rc = launch_evolve<uint16_t>(pop2, next2, e, h->perm, h->parents, h->st, h->stream);
+    if (!rc) rc = launch_evolve<uint16_t>(pop2, next2, e, h->perm, prefix, nullptr, h->st, h->stream);
     if (!rc) rc = mark(h, evs, 1);
     if (!rc) rc = enqueue_score(h, 1, evs);
     if (!rc) rc = enqueue_select(h, 1);
@@ -254,6 +260,8 @@ int enqueue_start(gpga_ga *h, const double *C)
     const size_t nn = (size_t)h->N * h->N * sizeof(double);
     GPGA_CUDA(cudaMemcpyAsync(h->C64, C, nn, cudaMemcpyDeviceToDevice, h->stream));
     GPGA_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    GPGA_CUDA(cudaMemsetAsync(h->rank, 0, (size_t)h->P * sizeof(int), h->stream));
+    GPGA_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
     int rc = launch_state_init(h->st, h->ts, h->k0, h->k1, h->stream);
     if (rc) return rc;
     rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->logtab, h->stream);
@@ -358,7 +366,7 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
     const size_t b_d = (size_t)Np * Np * sizeof(float);
     const size_t b_h = (size_t)Np * Np * sizeof(__nv_bfloat16);
     const size_t b_acc = (size_t)P * Np * sizeof(float);
-    const size_t b_log = (size_t)(N + 1) * sizeof(double);
+    const size_t b_log = logtab_len(N) * sizeof(double);
     size_t tc_bytes = 0;
     if (form == GPGA_FORM_TENSOR) tc_bytes = tc_scratch_bytes(N, Np, P);
     const size_t total = b_d + 2 * b_h + b_acc + b_log + tc_bytes + 4096;
@@ -369,7 +377,7 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
     __nv_bfloat16 *Dhi = c.take<__nv_bfloat16>((size_t)Np * Np);
     __nv_bfloat16 *Dlo = c.take<__nv_bfloat16>((size_t)Np * Np);
     float *acc = c.take<float>((size_t)P * Np);
-    double *logtab = c.take<double>(N + 1);
+    double *logtab = c.take<double>(logtab_len(N));
     int *err = c.take<int>(1);
     TcWork tc{};
     if (form == GPGA_FORM_TENSOR) tc_carve(&tc, N, Np, P, &c.off, ws);
@@ -418,15 +426,22 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int P = p->P, E = p->elite, M = P - E;
-    const size_t total = (size_t)P * (sizeof(uint64_t) + 2 * sizeof(int32_t)) + 1024;
+    const size_t total = (size_t)P * (2 * sizeof(uint64_t) + 3 * sizeof(int32_t)) + 2048;
     char *ws = nullptr;
     GPGA_CUDA(cudaMallocAsync((void **)&ws, total, s));
     Carver c(ws);
-    uint64_t *pre = c.take<uint64_t>(P);
+    uint64_t *rpre = c.take<uint64_t>(P);
+    uint64_t *wpre = c.take<uint64_t>(P);
+    int *rank = c.take<int>(P);
+    unsigned *ticket = c.take<unsigned>(1);
     int32_t *pm_ = perm ? perm : c.take<int32_t>(P);
-    int32_t *pa_ = parents ? parents : c.take<int32_t>(P);
     do {
-        rc = rank_prefix_table(pre, P, s);
+        if (cudaMemsetAsync(rank, 0, (size_t)P * sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess) {
+            rc = set_error(GPGA_ERR_CUDA, "ga_evolve: memset failed");
+            break;
+        }
+        rc = rank_prefix_table(rpre, P, s);
         if (rc) break;
         SelectCfg sc;
         sc.P = P;
@@ -442,8 +457,8 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
         sc.k1 = (uint32_t)(seed >> 32);
         sc.gen_off = generation;
         sc.record = 0;
-        rc = launch_select<int32_t>(L, sc, pre, pm_, pa_, nullptr, nullptr, nullptr, nullptr,
-                                    nullptr, s);
+        rc = launch_select<int32_t>(L, sc, rank, pm_, wpre, ticket, nullptr, nullptr, nullptr,
+                                    nullptr, nullptr, s);
         if (rc) break;
         EvolveCfg e;
         e.P = P;
@@ -459,7 +474,9 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
         e.gen = generation;
         const int32_t *pop2[2] = {pop, pop};
         int32_t *next2[2] = {next, next};
-        rc = launch_evolve<int32_t>(pop2, next2, e, pm_, pa_, nullptr, s);
+        rc = launch_evolve<int32_t>(pop2, next2, e, pm_,
+                                    p->scaling == GPGA_SCALING_PROP ? wpre : rpre, parents,
+                                    nullptr, s);
     } while (0);
     cudaFreeAsync(ws, s);
     return rc;
@@ -663,6 +680,15 @@ GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L)
     }
     if (L) GPGA_CUDA(cudaMemcpy(L, h->L, (size_t)h->P * sizeof(double), cudaMemcpyDefault));
     return GPGA_OK;
+}
+
+GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *y_cuda,
+                               void *stream)
+{
+    g_err[0] = 0;
+    if (!x || !y_table || !y_cuda || n < 0) return set_error(GPGA_ERR_ARG, "gpga_log_selftest: bad argument");
+    if (n == 0) return GPGA_OK;
+    return launch_log_selftest(x, n, y_table, y_cuda, (cudaStream_t)stream);
 }
 
 GPGA_API int ga_free(gpga_ga *h)

@@ -163,76 +163,83 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 }
 
 // ---------------------------------------------------------------------------
-// Selection kernel (one CTA of 1024 threads). Stateful use (st != nullptr):
-// g = st->gen + gen_off becomes the current generation; records best L, best
-// labels and the device clock; tests termination and sets st->done.
-// Then: bitonic sort of (L, index) -> perm; scaling weights -> inclusive
-// prefix (RANK: precomputed table; PROP: computed and scanned here); SUS.
-// Shared memory: Pp keys (double, later reused for the uint64 prefix) and
-// Pp indices, Pp = next power of two >= P.
+// "Isolate fittest individuals": rank_i = #{j : (L_j, j) fitter than (L_i, i)},
+// counted over all pairs by a grid (slices of j per CTA row, integer atomics,
+// so the ranks are exact and order-independent). perm[rank_i] = i follows in
+// the finalize kernel, which also zeroes rank for the next use.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    rank_count_kernel(const double *__restrict__ L, int P, int slice, int *__restrict__ rank,
+                      const DevState *__restrict__ st)
+{
+    if (st && st->done) return;
+    extern __shared__ unsigned long long keys[];
+    const int j0 = blockIdx.y * slice, j1 = min(P, j0 + slice);
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) keys[j - j0] = order_key(L[j]);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const unsigned long long ki = order_key(L[i]);
+    int cnt = 0;
+    for (int j = j0; j < j1; ++j) {
+        const unsigned long long kj = keys[j - j0];
+        cnt += (kj > ki) | ((kj == ki) & (j < i));
+    }
+    if (cnt) atomicAdd(&rank[i], cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: perm[rank_i] = i over the grid; the CTA that arrives last (ticket,
+// no waiting) then holds the whole permutation and does the per-generation
+// bookkeeping of Algorithm 1 -- "evaluate state and statistics" (best, mean),
+// the record of the best configuration and the device clock, "determine if
+// termination criteria are met" -- and, for proportional scaling, the weights
+// by rank and their inclusive prefix. Stateful use: g = st->gen + gen_off.
 // ---------------------------------------------------------------------------
 template <typename LabT>
-__global__ void __launch_bounds__(1024)
-    select_kernel(const double *__restrict__ L, SelectCfg cfg,
-                  const uint64_t *__restrict__ rank_prefix, int32_t *__restrict__ perm,
-                  int32_t *__restrict__ parents, DevState *st, double *__restrict__ hist,
-                  const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
-                  unsigned long long *__restrict__ ts, int Pp)
+__global__ void __launch_bounds__(256)
+    finalize_kernel(const double *__restrict__ L, SelectCfg cfg, int *__restrict__ rank,
+                    int32_t *__restrict__ perm, uint64_t *__restrict__ work_prefix,
+                    unsigned *__restrict__ ticket, DevState *st, double *__restrict__ hist,
+                    const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
+                    unsigned long long *__restrict__ ts)
 {
-    extern __shared__ unsigned long long sm_key[];
-    int *sm_idx = reinterpret_cast<int *>(sm_key + Pp);
-    __shared__ int s_done;
-    __shared__ double s_red[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    int g = cfg.gen_off;
-    uint32_t k0 = cfg.k0, k1 = cfg.k1;
-    if (st) {
-        if (st->done) return;
-        g = st->gen + cfg.gen_off;
-        k0 = st->k0;
-        k1 = st->k1;
-    }
+    if (st && st->done) return;
     const int P = cfg.P;
-    for (int i = tid; i < Pp; i += nt) {
-        sm_key[i] = i < P ? order_key(L[i]) : 0ull; // padding below every real key
-        sm_idx[i] = i;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) {
+        perm[rank[i]] = i;
+        rank[i] = 0;
     }
+    __shared__ int s_last;
+    __shared__ double s_red[8];
+    __shared__ uint64_t s_part[256];
+    __threadfence();
     __syncthreads();
-    // bitonic sort into "fitter first" order
-    for (int k = 2; k <= Pp; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = tid; t < (Pp >> 1); t += nt) {
-                const int i = ((t / j) * 2 * j) + (t % j);
-                const int l = i + j;
-                const unsigned long long ki = sm_key[i], kl = sm_key[l];
-                const int ii = sm_idx[i], il = sm_idx[l];
-                const bool up = (i & k) == 0;
-                const bool swap = up ? fitter(kl, il, ki, ii) : fitter(ki, ii, kl, il);
-                if (swap) {
-                    sm_key[i] = kl;
-                    sm_key[l] = ki;
-                    sm_idx[i] = il;
-                    sm_idx[l] = ii;
-                }
-            }
-            __syncthreads();
-        }
-    }
-
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) *ticket = 0u;
+    const int bidx = __ldcg(perm);
     if (st) {
-        // statistics: best, mean (fixed-order reduction)
+        const int g = st->gen + cfg.gen_off;
         double part = 0.0;
-        for (int i = tid; i < P; i += nt) part += L[i];
+        for (int k = tid; k < P; k += nt) part += L[k];
 #pragma unroll
         for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         if ((tid & 31) == 0) s_red[tid >> 5] = part;
+        if (cfg.record && ring) {
+            const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
+            for (int j = tid; j < cfg.N; j += nt) ring[(size_t)g * cfg.N + j] = src[j];
+        }
         __syncthreads();
-        const int bidx = sm_idx[0];
-        double best = L[bidx];
-        if (isnan(best)) best = -INFINITY;
         if (tid == 0) {
             double m = 0.0;
             for (int w = 0; w < (nt >> 5); ++w) m += s_red[w];
+            double best = L[bidx];
+            if (isnan(best)) best = -INFINITY;
             st->gen = g;
             st->best = best;
             st->best_idx = bidx;
@@ -243,163 +250,119 @@ __global__ void __launch_bounds__(1024)
                 const double prev = hist[g - cfg.stall_gens];
                 done = (best - prev) <= cfg.tol * fmax(1.0, fabs(best));
             }
-            s_done = done;
-        }
-        if (cfg.record && ring) {
-            const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
-            for (int j = tid; j < cfg.N; j += nt) ring[(size_t)g * cfg.N + j] = src[j];
+            if (cfg.record && ts) {
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                ts[1 + g] = t;
+            }
+            st->done = done;
+            s_last = done;
         }
         __syncthreads();
-        if (cfg.record && ts && tid == 0) {
-            unsigned long long t;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-            ts[1 + g] = t;
+        if (s_last) return;
+    }
+    if (cfg.scaling != GPGA_SCALING_PROP) return;
+    // proportional weights by rank, w = floor(max(L, 0) / L_max 2^32) (all 1 if
+    // L_max <= 0), and their inclusive prefix: chunked sequential scan
+    double lmax = L[bidx];
+    if (isnan(lmax)) lmax = -INFINITY;
+    const int chunk = (P + nt - 1) / nt;
+    const int lo = tid * chunk, hi = min(P, lo + chunk);
+    uint64_t s = 0;
+    for (int r = lo; r < hi; ++r) {
+        uint64_t w = 1;
+        if (lmax > 0.0) {
+            double x = L[__ldcg(perm + r)];
+            if (!(x > 0.0)) x = 0.0;
+            w = (uint64_t)floor(__dmul_rn(__ddiv_rn(x, lmax), 4294967296.0));
         }
-        if (s_done) {
-            if (tid == 0) st->done = 1;
-            return;
+        s += w;
+        work_prefix[r] = s;
+    }
+    s_part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t run = 0;
+        for (int k = 0; k < nt; ++k) {
+            const uint64_t v = s_part[k];
+            s_part[k] = run;
+            run += v;
         }
     }
-
-    for (int r = tid; r < P; r += nt) perm[r] = sm_idx[r];
-
-    // scaling -> inclusive prefix in the key array (reinterpreted as uint64)
-    uint64_t *pre = reinterpret_cast<uint64_t *>(sm_key);
-    if (cfg.scaling == GPGA_SCALING_RANK) {
-        __syncthreads();
-        for (int r = tid; r < P; r += nt) pre[r] = rank_prefix[r];
-        __syncthreads();
-    } else {
-        double lmax = L[sm_idx[0]];
-        if (isnan(lmax)) lmax = -INFINITY;
-        __syncthreads();
-        for (int r = tid; r < P; r += nt) {
-            uint64_t w = 1;
-            if (lmax > 0.0) {
-                double x = L[sm_idx[r]];
-                if (!(x > 0.0)) x = 0.0;
-                w = (uint64_t)floor(__dmul_rn(__ddiv_rn(x, lmax), 4294967296.0));
-            }
-            pre[r] = w; // same slot, read above by this thread only
-        }
-        __syncthreads();
-        // chunked inclusive scan
-        const int chunk = (P + nt - 1) / nt;
-        const int lo = tid * chunk, hi = min(P, lo + chunk);
-        uint64_t s = 0;
-        for (int r = lo; r < hi; ++r) {
-            s += pre[r];
-            pre[r] = s;
-        }
-        __shared__ uint64_t s_part[1024];
-        s_part[tid] = s;
-        __syncthreads();
-        if (tid == 0) {
-            uint64_t run = 0;
-            for (int k = 0; k < nt; ++k) {
-                const uint64_t v = s_part[k];
-                s_part[k] = run;
-                run += v;
-            }
-        }
-        __syncthreads();
-        for (int r = lo; r < hi; ++r) pre[r] += s_part[tid];
-        __syncthreads();
-    }
-
-    // SUS: M pointers, parent = first rank whose prefix exceeds the pointer.
-    // Thread t takes a contiguous run of pointers: the first by exact 128-bit
-    // division, the next ones by exact increments (numerator + 2^32 W, carried
-    // against the divisor M 2^32).
-    const uint64_t W = pre[P - 1];
-    const U4 w = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
-    const int M = cfg.M;
-    const int per = (M + nt - 1) / nt;
-    const int k_lo = tid * per, k_hi = min(M, k_lo + per);
-    if (k_lo < k_hi) {
-        uint64_t x = sus_pointer((uint32_t)k_lo, w.x, W, (uint32_t)M);
-        // remainder of the first numerator modulo M 2^32, as (rem_hi < M, rem_lo)
-        const uint64_t num = ((uint64_t)(uint32_t)k_lo << 32) | w.x;
-        const uint64_t plo = num * W, phi = __umul64hi(num, W);
-        // (phi:plo) - x * M * 2^32
-        const uint64_t xm_lo = (x * (uint64_t)M) << 32;
-        const uint64_t xm_hi = __umul64hi(x, (uint64_t)M << 32);
-        uint64_t r_lo = plo - xm_lo;
-        uint64_t r_hi = phi - xm_hi - (plo < xm_lo ? 1ull : 0ull);
-        // step 2^32 W = qs (M 2^32) + rs, qs = W / M, rs = (W mod M) 2^32
-        const uint64_t qs = W / (uint64_t)M, rsm = W % (uint64_t)M;
-        const uint64_t dm = (uint64_t)M; // divisor is dm * 2^32: compare (r_hi:r_lo) >= (dm:0)
-        int lo = 0;
-        for (int k = k_lo; k < k_hi; ++k) {
-            if (k > k_lo) {
-                x += qs;
-                // remainder += rsm * 2^32
-                const uint64_t add_lo = rsm << 32, add_hi = rsm >> 32;
-                const uint64_t nlo = r_lo + add_lo;
-                r_hi = r_hi + add_hi + (nlo < r_lo ? 1ull : 0ull);
-                r_lo = nlo;
-                if (r_hi > (dm >> 32) || (r_hi == (dm >> 32) && r_lo >= (dm << 32))) {
-                    const uint64_t sub_lo = dm << 32, sub_hi = dm >> 32;
-                    const uint64_t n2 = r_lo - sub_lo;
-                    r_hi = r_hi - sub_hi - (r_lo < sub_lo ? 1ull : 0ull);
-                    r_lo = n2;
-                    x += 1;
-                }
-            }
-            int hi = P - 1;
-            while (lo < hi) { // pointers grow with k: the search restarts at the last hit
-                const int mid = (lo + hi) >> 1;
-                if (pre[mid] > x)
-                    hi = mid;
-                else
-                    lo = mid + 1;
-            }
-            parents[k] = sm_idx[lo];
-        }
-    }
+    __syncthreads();
+    for (int r = lo; r < hi; ++r) work_prefix[r] += s_part[tid];
 }
 
 template <typename LabT>
-int launch_select(const double *L, const SelectCfg &cfg, const uint64_t *rank_prefix,
-                  int32_t *perm, int32_t *parents, DevState *st, double *hist,
+int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *perm,
+                  uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,
                   const LabT *const *pop2, LabT *ring, unsigned long long *ts, cudaStream_t s)
 {
-    int Pp = 1;
-    while (Pp < cfg.P) Pp <<= 1;
-    const size_t smem = (size_t)Pp * (sizeof(unsigned long long) + sizeof(int));
-    select_kernel<LabT><<<1, 1024, smem, s>>>(L, cfg, rank_prefix, perm, parents, st, hist,
-                            pop2 ? pop2[0] : nullptr, pop2 ? pop2[1] : nullptr, ring, ts, Pp);
+    const int P = cfg.P;
+    const int bx = (P + 127) / 128;
+    int sy = (2 * 152 + bx - 1) / bx; // about two CTAs per SM
+    if (sy < 1) sy = 1;
+    int slice = (P + sy - 1) / sy;
+    if (slice > 8192) slice = 8192;
+    sy = (P + slice - 1) / slice;
+    rank_count_kernel<<<dim3(bx, sy), 128, (size_t)slice * sizeof(unsigned long long), s>>>(
+        L, P, slice, rank, st);
+    GPGA_LAUNCH_CHECK();
+    finalize_kernel<LabT><<<(P + 255) / 256, 256, 0, s>>>(
+        L, cfg, rank, perm, work_prefix, ticket, st, hist, pop2 ? pop2[0] : nullptr,
+        pop2 ? pop2[1] : nullptr, ring, ts);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
 
-template int launch_select<uint16_t>(const double *, const SelectCfg &, const uint64_t *,
-                                     int32_t *, int32_t *, DevState *, double *,
+template int launch_select<uint16_t>(const double *, const SelectCfg &, int *, int32_t *,
+                                     uint64_t *, unsigned *, DevState *, double *,
                                      const uint16_t *const *, uint16_t *, unsigned long long *,
                                      cudaStream_t);
-template int launch_select<int32_t>(const double *, const SelectCfg &, const uint64_t *,
-                                    int32_t *, int32_t *, DevState *, double *,
+template int launch_select<int32_t>(const double *, const SelectCfg &, int *, int32_t *,
+                                    uint64_t *, unsigned *, DevState *, double *,
                                     const int32_t *const *, int32_t *, unsigned long long *,
                                     cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Crossover + mutation + replacement, one warp per slot of the next population.
-// Slots 0..E-1: elites in rank order, copied. Slot E + k: child k of
-//   a = parents[k], b = parents[(k + M/2) mod M];
-//   Philox(g, k, 0, XOVER) = (x, y, z, .): crossover if x < thr(P_c); then
-//   knowledge-based merge if y < thr(P_kb) with anchor q = draw(z, N):
-//   child_j = a_q where b_j = b_q, else a_j; otherwise one-point at
-//   cut = 1 + draw(z, N - 1): child_j = a_j for j < cut, b_j after.
-//   Mutation, gene pair (2m, 2m+1): Philox(g, k, m, MUT) = (f0, v0, f1, v1):
-//   child_j = draw(v, N) if f < thr(P_m).
+// "Apply genetic operator: selection" (SUS), crossover, mutation and
+// replacement, one warp per slot of the next population.
+// Slots 0..E-1: elites in rank order, copied. Slot E + k: child k.
+// Selection: the P individuals lie on a line in rank order over segments of
+// their scaled weights (prefix[r] inclusive, W = prefix[P-1]); pointer
+// x_k = floor((k 2^32 + u) W / (M 2^32)), u = word 0 of Philox(g, 0, 0, SUS),
+// selects rank r with prefix[r-1] <= x_k < prefix[r]. Child k pairs
+// a = parent(k) with b = parent((k + M/2) mod M).
+// Crossover: Philox(g, k, 0, XOVER) = (x, y, z, .): if x < thr(P_c), then the
+// knowledge-based merge if y < thr(P_kb) with anchor q = draw(z, N):
+// child_j = a_q where b_j = b_q, else a_j; otherwise one-point at
+// cut = 1 + draw(z, N - 1): child_j = a_j for j < cut, b_j after.
+// Mutation, gene pair (2m, 2m+1): Philox(g, k, m, MUT) = (f0, v0, f1, v1):
+// child_j = draw(v, N) if f < thr(P_m).
 // Every gene is a function of (a_j, b_j) and warp-uniform values, so lanes
 // stream gene pairs with no shared memory.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int sus_parent(int k, uint32_t u, uint64_t W, int M, int P,
+                                          const uint64_t *__restrict__ prefix,
+                                          const int32_t *__restrict__ perm)
+{
+    const uint64_t x = sus_pointer((uint32_t)k, u, W, (uint32_t)M);
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) > x)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return perm[lo];
+}
+
 template <typename LabT>
 __global__ void __launch_bounds__(256)
     evolve_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1, EvolveCfg cfg,
-                  const int32_t *__restrict__ perm, const int32_t *__restrict__ parents,
-                  const DevState *__restrict__ st)
+                  const int32_t *__restrict__ perm, const uint64_t *__restrict__ prefix,
+                  int32_t *__restrict__ parents_out, const DevState *__restrict__ st)
 {
     int g = cfg.gen;
     uint32_t k0 = cfg.k0, k1 = cfg.k1;
@@ -425,8 +388,17 @@ __global__ void __launch_bounds__(256)
     }
     const int k = slot - cfg.E;
     const int M = cfg.M;
-    const LabT *a = cur + (size_t)parents[k] * ldp;
-    const LabT *b = cur + (size_t)parents[(k + M / 2) % M] * ldp;
+    int par = 0;
+    if (lane < 2) {
+        const uint64_t W = __ldg(prefix + cfg.P - 1);
+        const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
+        par = sus_parent(lane == 0 ? k : (k + M / 2) % M, su.x, W, M, cfg.P, prefix, perm);
+    }
+    const int ia = __shfl_sync(0xffffffffu, par, 0);
+    const int ib = __shfl_sync(0xffffffffu, par, 1);
+    if (parents_out && lane == 0) parents_out[k] = ia;
+    const LabT *a = cur + (size_t)ia * ldp;
+    const LabT *b = cur + (size_t)ib * ldp;
     const U4 xw = philox((uint32_t)g, (uint32_t)k, 0u, STREAM_XOVER, k0, k1);
     int mode = 0, cut = N;
     int bq = 0, aq = 0;
@@ -468,27 +440,26 @@ __global__ void __launch_bounds__(256)
 
 template <typename LabT>
 int launch_evolve(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
-                  const int32_t *perm, const int32_t *parents, const DevState *st,
-                  cudaStream_t s)
+                  const int32_t *perm, const uint64_t *prefix, int32_t *parents_out,
+                  const DevState *st, cudaStream_t s)
 {
     const int grid = (cfg.P + 7) / 8;
     evolve_kernel<LabT><<<grid, 256, 0, s>>>(pop2[0], pop2[1], next2[0], next2[1], cfg, perm,
-                                             parents, st);
+                                             prefix, parents_out, st);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
 
 template int launch_evolve<uint16_t>(const uint16_t *const *, uint16_t *const *,
-                                     const EvolveCfg &, const int32_t *, const int32_t *,
-                                     const DevState *, cudaStream_t);
+                                     const EvolveCfg &, const int32_t *, const uint64_t *,
+                                     int32_t *, const DevState *, cudaStream_t);
 template int launch_evolve<int32_t>(const int32_t *const *, int32_t *const *, const EvolveCfg &,
-                                    const int32_t *, const int32_t *, const DevState *,
-                                    cudaStream_t);
+                                    const int32_t *, const uint64_t *, int32_t *,
+                                    const DevState *, cudaStream_t);
 
 int prepare_ga_kernels(int maxsmem)
 {
-    if (int rc = raise_smem(select_kernel<uint16_t>, maxsmem)) return rc;
-    if (int rc = raise_smem(select_kernel<int32_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(rank_count_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }
 

@@ -93,6 +93,37 @@ inline int pad_n(int N) { return (N + 63) & ~63; }
 int fix_bits_for(int N);
 
 // ---------------------------------------------------------------------------
+// Natural log in FP64 for x > 0 normal, table-driven (P. T. P. Tang, "Table-
+// driven implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16(4), 1990): x = 2^e m, m in [1, 2); the top 8
+// mantissa bits pick c_k = 1 + (k + 1/2)/256, with tab[k] = (inv_k, -log inv_k)
+// and inv_k = fl(1/c_k); r = m inv_k - 1 (one FMA, |r| <= 2^-9 + ulp) and
+// log x = e ln2 - log inv_k + log1p(r), log1p by its Taylor series to r^6
+// (truncation < |r|^7/7 < 2e-20). About 9 FP64 operations.
+// ---------------------------------------------------------------------------
+constexpr int LOG_TAB = 256;
+
+__device__ __forceinline__ double table_log(double x, const double2 *__restrict__ tab)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023;
+    const int k = (int)((b >> 44) & 0xff);
+    const double m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+    const double2 t = tab[k];
+    const double r = fma(m, t.x, -1.0);
+    double q = fma(r, -1.0 / 6.0, 0.2);
+    q = fma(r, q, -0.25);
+    q = fma(r, q, 1.0 / 3.0);
+    q = fma(r, q, -0.5);
+    q = fma(r, q, 1.0);
+    return fma((double)e, 0.6931471805599453, fma(r, q, t.y));
+}
+
+// layout of the per-run log table (doubles): LOG_TAB pairs (inv_k, -log inv_k),
+// then K1[n], n = 0..N (see score.cu)
+inline size_t logtab_len(int N) { return 2 * LOG_TAB + (size_t)N + 1; }
+
+// ---------------------------------------------------------------------------
 // host launchers (score.cu)
 // ---------------------------------------------------------------------------
 int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,
@@ -106,6 +137,8 @@ template <typename LabT>
 int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *acc, int Np,
                     const float *D32, int full_rows, int P, int N, const double *logtab,
                     double *L, int *err, const DevState *st, cudaStream_t s);
+
+int launch_log_selftest(const double *x, int n, double *yt, double *yc, cudaStream_t s);
 
 int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
                         const double *C, int N, int32_t *canon_out, double *L_out, cudaStream_t s);
@@ -147,9 +180,11 @@ template <typename LabT>
 int launch_init_uniform(LabT *pop, int ldp, int P, int N, int K0, uint32_t k0, uint32_t k1,
                         cudaStream_t s);
 
+// rank (counting, grid) + finalize (perm, stats, termination, records, PROP
+// prefix); rank[] and *ticket must be zero on entry and are left zero
 template <typename LabT>
-int launch_select(const double *L, const SelectCfg &cfg, const uint64_t *rank_prefix,
-                  int32_t *perm, int32_t *parents, DevState *st, double *hist,
+int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *perm,
+                  uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,
                   const LabT *const *pop2, LabT *ring, unsigned long long *ts, cudaStream_t s);
 
 struct EvolveCfg {
@@ -159,10 +194,12 @@ struct EvolveCfg {
     int gen; // stateless generation (when st == nullptr)
 };
 
+// prefix: inclusive prefix of the scaled weights by rank (RANK: the fixed
+// table; PROP: the work prefix written by finalize); parents_out optional
 template <typename LabT>
 int launch_evolve(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
-                  const int32_t *perm, const int32_t *parents, const DevState *st,
-                  cudaStream_t s);
+                  const int32_t *perm, const uint64_t *prefix, int32_t *parents_out,
+                  const DevState *st, cudaStream_t s);
 
 int launch_state_init(DevState *st, unsigned long long *ts0, uint32_t k0, uint32_t k1,
                       cudaStream_t s);

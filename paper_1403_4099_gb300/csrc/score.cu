@@ -23,13 +23,23 @@ int fix_bits_for(int N)
     return bits;
 }
 
+// entry k of the table_log() table: (inv_k, -log inv_k), inv_k = fl(1 / c_k)
+__device__ __forceinline__ void log_tab_entry(int k, double *out)
+{
+    const double c = 1.0 + ((double)k + 0.5) / (double)LOG_TAB;
+    const double inv = 1.0 / c;
+    out[0] = inv;
+    out[1] = -log(inv);
+}
+
 // ---------------------------------------------------------------------------
 // D forms: D32 = fp32(1 - (C + C^T)/2), Dhi = bf16(D), Dlo = bf16(D - Dhi),
 // all Np x Np, zero outside N x N; logtab[k] = log(k) for k = 1..N.
 // ---------------------------------------------------------------------------
 __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int Np,
                               float *__restrict__ D32, __nv_bfloat16 *__restrict__ Dhi,
-                              __nv_bfloat16 *__restrict__ Dlo, double *__restrict__ logtab)
+                              __nv_bfloat16 *__restrict__ Dlo, double *__restrict__ logtab,
+                              int fix_bits)
 {
     const size_t total = (size_t)Np * Np;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -50,8 +60,19 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
         }
     }
     if (logtab) {
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= N; k += gridDim.x * blockDim.x)
-            logtab[k] = k > 0 ? log((double)k) : 0.0;
+        // log table of table_log(), then the per-size constant of the assembly:
+        // K1[n] = 1/2 (n B + log n + (n - 1) log(n (n - 1))), B = fix_bits ln 2
+        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+        for (int k = tid; k < LOG_TAB; k += nt) log_tab_entry(k, logtab + 2 * k);
+        const double B = (double)fix_bits * 0.6931471805599453;
+        for (int n = tid; n <= N; n += nt) {
+            double v = 0.0;
+            if (n >= 2) {
+                const double dn = (double)n;
+                v = 0.5 * (dn * B + log(dn) + (dn - 1.0) * (log(dn) + log(dn - 1.0)));
+            }
+            logtab[2 * LOG_TAB + n] = v;
+        }
     }
 }
 
@@ -61,7 +82,7 @@ int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bflo
     const size_t total = (size_t)Np * Np;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, logtab);
+    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, logtab, fix_bits_for(N));
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
@@ -188,12 +209,15 @@ int launch_pair_plain(const float *D32, int Np, const LabT *const *lab2, int ldl
 
 // ---------------------------------------------------------------------------
 // Assembly (Eq. 5 and Eq. 8): one warp per individual. Row sums are turned into
-// fixed point and added into per-label bins with integer shared-memory atomics,
-// so d_s is independent of the order of the additions (the score is
-// deterministic). Then, per label with n_s > 1,
-//   t_s = 1/2 [ log n_s - log c_s + (n_s - 1)(log n_s + log(n_s - 1) - log d_s) ]
-// in FP64 (log of the integers from a table), summed per lane in ascending s and
-// across lanes by a fixed butterfly.
+// fixed point (scale 2^b) and added into per-label bins with integer shared-
+// memory atomics, so d_s is independent of the order of the additions (the score
+// is deterministic). The non-singleton clusters are compacted, then each term
+// is taken from the exact integers dfix = d_s 2^b and cfix = n_s^2 2^b - dfix:
+//   t_s = K1[n] - 1/2 [ log cfix + (n - 1) log dfix ],
+//   K1[n] = 1/2 [ n b ln2 + log n + (n - 1) log(n (n - 1)) ]
+// which is Eq. 8 with c_s = cfix 2^-b, d_s = dfix 2^-b. For n <= 16 the bracket
+// is one log of cfix dfix^(n-1) (< 2^800, no overflow). Terms are summed per
+// lane in compacted order and across lanes by a fixed butterfly.
 //   full_rows = 0: row value = 2 u_i + D_ii (upper-triangle sums of the plain form)
 //   full_rows = 1: row value = y_i = sum_j D_ij [s_j = s_i] (tensor form)
 // ---------------------------------------------------------------------------
@@ -214,8 +238,10 @@ __global__ void __launch_bounds__(256)
     unsigned long long *dfx = smem_u64 + (size_t)warp * Np;
     int *cnt = reinterpret_cast<int *>(smem_u64 + (size_t)nw * Np) + warp * Np;
     const float fscale = exp2f((float)fix_bits);
-    const double inv = exp2(-(double)fix_bits);
-    const double cl_eps = 9.094947017729282e-13; // 2^-40
+    // domain floor of Eq. 8 (c_s >= n 2^-40, d_s >= n (n - 1) 2^-40) in units of 2^-b
+    const double clamp_unit = exp2((double)(fix_bits - 40));
+    const double2 *__restrict__ ltab = reinterpret_cast<const double2 *>(logtab);
+    const double *__restrict__ k1tab = logtab + 2 * LOG_TAB;
 
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
         for (int s = lane; s < N; s += 32) {
@@ -270,14 +296,22 @@ __global__ void __launch_bounds__(256)
         double part = 0.0;
         for (int k = lane; k < nlist; k += 32) {
             const int n = cnt[k];
-            const double dn = (double)n;
-            double d = (double)(long long)dfx[k] * inv;
-            double c = dn * dn - d;
-            const double cmin = dn * cl_eps, dmin = dn * (dn - 1.0) * cl_eps;
+            const long long df = (long long)dfx[k];
+            const long long cf = (((long long)n * n) << fix_bits) - df;
+            double c = (double)cf, d = (double)df;
+            const double cmin = (double)n * clamp_unit;
+            const double dmin = (double)(n * (n - 1)) * clamp_unit;
             if (!(c >= cmin)) c = cmin;
             if (!(d >= dmin)) d = dmin;
-            const double ln = logtab[n], ln1 = logtab[n - 1];
-            part += 0.5 * ((ln - log(c)) + (dn - 1.0) * ((ln + ln1) - log(d)));
+            double lg;
+            if (n <= 16) {
+                double pw = c * d;
+                for (int t = 2; t < n; ++t) pw *= d;
+                lg = table_log(pw, ltab);
+            } else {
+                lg = fma((double)(n - 1), table_log(d, ltab), table_log(c, ltab));
+            }
+            part += fma(-0.5, lg, k1tab[n]);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -401,6 +435,26 @@ int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, con
 {
     const size_t smem = (size_t)N * (2 * sizeof(double) + 2 * sizeof(int));
     rescore_kernel<<<1, 1024, smem, s>>>(pop0, pop1, ldp, st, C, N, canon_out, L_out);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+// diagnostic: table_log() and CUDA's log on the same inputs
+__global__ void log_selftest_kernel(const double *__restrict__ x, int n, double *__restrict__ yt,
+                                    double *__restrict__ yc)
+{
+    __shared__ double tab[2 * LOG_TAB];
+    for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) log_tab_entry(k, tab + 2 * k);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        yt[i] = table_log(x[i], reinterpret_cast<const double2 *>(tab));
+        yc[i] = log(x[i]);
+    }
+}
+
+int launch_log_selftest(const double *x, int n, double *yt, double *yc, cudaStream_t s)
+{
+    log_selftest_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(x, n, yt, yc);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }

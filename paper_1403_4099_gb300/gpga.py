@@ -24,7 +24,7 @@ MAX_N, MAX_P = 4096, 16384
 
 EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score", "ga_evolve",
            "ga_init", "ga_reset", "ga_step", "ga_best", "ga_history", "ga_kernel_times",
-           "ga_population", "ga_free"]
+           "ga_population", "gpga_log_selftest", "ga_free"]
 
 
 class GpgaError(RuntimeError):
@@ -85,6 +85,7 @@ def lib() -> ct.CDLL:
             "ga_history": (i32, [vp, vp, vp, vp, i32, ct.POINTER(i32)]),
             "ga_kernel_times": (i32, [vp, vp, i32, ct.POINTER(i32)]),
             "ga_population": (i32, [vp, vp, vp]),
+            "gpga_log_selftest": (i32, [vp, i32, vp, vp, vp]),
             "ga_free": (i32, [vp]),
         }
         for name, (res, args) in sigs.items():
@@ -164,6 +165,16 @@ def ga_evolve(pop, L, params: Params, seed: int, generation: int, stream=None):
                            _dev(perm, "int32"), _dev(par, "int32") if par.numel() else None,
                            _stream_ptr(stream)))
     return nxt, perm, par
+
+
+def log_selftest(x, stream=None):
+    """(table_log(x), CUDA log(x)) for a device FP64 tensor x (diagnostic)."""
+    import torch
+    yt = torch.empty_like(x)
+    yc = torch.empty_like(x)
+    _check(lib().gpga_log_selftest(_dev(x, "float64"), x.numel(), _dev(yt, "float64"),
+                                   _dev(yc, "float64"), _stream_ptr(stream)))
+    return yt, yc
 
 
 class GA:
