@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpga", choices=["gpga", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "tensor"])
+    ap.add_argument("--form", default="gather", choices=["plain", "tensor", "gather"])
     ap.add_argument("--gens", type=int, default=100, help="generations per step")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -138,11 +138,26 @@ def run_reference(args, ranks):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def gather_roofline(launch_ms, pk, pk_kind, pairs_per_gen):
+    """Fused generation kernel (gather form): algorithmic bytes per launch =
+    per child 2 parents read + child written (2 B labels, N genes) + one 4-byte
+    D entry per same-cluster pair + 8 B of fitness; pairs measured on the
+    device for the timed generations."""
+    bytes_per_launch = P * (3 * 2 * N + 8) + 4.0 * pairs_per_gen
+    t = launch_ms / 1e3
+    gbs = bytes_per_launch / t / 1e9
+    peak = pk["hbm_gbs"]
+    return {"bound": "hbm", "kernel": "gather_generation", "achieved": gbs, "peak": peak,
+            "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+            "peak_source": f"hbm_gbs ({pk_kind})", "algorithmic_bytes_per_launch": bytes_per_launch,
+            "same_cluster_pairs_per_launch": pairs_per_gen, "launch_ms": launch_ms}
+
 def launches_per_step(form: str, gens: int) -> int:
     corr = 7                      # colsum x2, colfinal x2, normalise, gram, gram_final
-    score = 2 if form == "plain" else 4
-    start = 4 + score + 1         # state, prep_d, rank table, init, score, select
-    return corr + start + gens * (2 + score)
+    score = {"plain": 2, "tensor": 4, "gather": 1}[form]
+    start = 4 + score + 2         # state, prep_d, rank table, init, score, rank, finalize
+    per_gen = (1 if form == "gather" else 1 + score) + 2  # (fused | evolve + score), rank, finalize
+    return corr + start + gens * per_gen
 
 
 def run_gpu(args, ranks):
@@ -153,7 +168,7 @@ def run_gpu(args, ranks):
     torch.cuda.set_device(ranks.local)
     dev = torch.device("cuda", ranks.local)
     runtime.init_dist(ranks, "nccl")
-    form = gpga.FORM_PLAIN if args.form == "plain" else gpga.FORM_TENSOR
+    form = {"plain": gpga.FORM_PLAIN, "tensor": gpga.FORM_TENSOR, "gather": gpga.FORM_GATHER}[args.form]
     G = args.gens
     planted = synth.n500(replicate=ranks.rank)
     R_host = torch.from_numpy(planted.R).pin_memory()
@@ -209,10 +224,11 @@ def run_gpu(args, ranks):
 
     stage = np.concatenate(stage)  # rows: generations; cols: evolve, pair, assemble, select
     stage_mean = stage.mean(axis=0)
-    names = ["evolve", "pair_plain" if form == gpga.FORM_PLAIN else "tc_contract", "assemble",
-             "select"]
-    kernel_ms = {n: float(v) for n, v in zip(names, stage_mean)}
-    dominant = names[int(np.argmax(stage_mean))]
+    names = {gpga.FORM_PLAIN: ["evolve", "pair_plain", "assemble", "select"],
+             gpga.FORM_TENSOR: ["evolve", "tc_contract", "assemble", "select"],
+             gpga.FORM_GATHER: ["gather_generation", "-", "-", "select"]}[form]
+    kernel_ms = {n: float(v) for n, v in zip(names, stage_mean) if n != "-"}
+    dominant = max(kernel_ms, key=kernel_ms.get)
 
     pk, pk_kind = peaks()
     if form == gpga.FORM_PLAIN:
@@ -226,6 +242,10 @@ def run_gpu(args, ranks):
                 "peak_source": f"{SMS} SMs x {ALU_LANES} FP32/INT32 lanes x "
                                f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
                 "algorithmic_ops_per_launch": ops, "launch_ms": kernel_ms["pair_plain"]}
+    elif form == gpga.FORM_GATHER:
+        pairs = hist["pairs"]
+        roof = gather_roofline(kernel_ms["gather_generation"], pk, pk_kind,
+                               float(np.mean(pairs[1:])) if len(pairs) > 1 else 0.0)
     else:
         roof = None  # filled by the tensor form
 
@@ -268,6 +288,10 @@ def run_gpu(args, ranks):
                        "generations_per_step": G, "form": args.form, "init": "uniform",
                        "l2": "flushed between steps (256 MB memset outside the step events)"},
             "generations_per_s": gens_per_s,
+            "same_cluster_pairs_per_individual": {
+                "first_generation": float(hist["pairs"][0]) / P,
+                "last_generation": float(hist["pairs"][-1]) / P,
+                "dense_pairs_per_individual": N * (N - 1) / 2},
             "ms_to_recover": ms_rec,
             "kernel_ms": kernel_ms, "dominant_kernel": dominant,
             "roofline": roof,

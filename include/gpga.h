@@ -52,6 +52,8 @@ extern "C" {
 /* scoring forms (both end in the same FP64 log-term assembly) */
 #define GPGA_FORM_PLAIN 0  /* FP32 CUDA-core pair accumulation */
 #define GPGA_FORM_TENSOR 1 /* tcgen05 one-hot contraction, D split BF16 hi+lo */
+#define GPGA_FORM_GATHER 2 /* same-cluster pairs only (sorted by label), FP32 gathers;
+                              in a run, fused with the generation's operators */
 
 /* fitness scaling before selection ("apply scaling", Algorithm 1) */
 #define GPGA_SCALING_RANK 0 /* w(r) = floor(2^32 / sqrt(r + 1)), r = 0-based rank */
@@ -124,7 +126,7 @@ GPGA_API int cluster_corr(const double *R, int T, int N, int ld, double *C, void
  * labels: device, P x N int32 in [0, N), leading dimension ld >= N.
  * C: device, N x N FP64 (read; asymmetric input is used through (C + C^T)/2,
  * which leaves Eq. 6 unchanged). L: device, P FP64 (written).
- * form: GPGA_FORM_PLAIN or GPGA_FORM_TENSOR.
+ * form: GPGA_FORM_PLAIN, GPGA_FORM_TENSOR or GPGA_FORM_GATHER.
  * Errors: GPGA_ERR_ARG for sizes out of range or any label outside [0, N)
  * (found on the device; the matching L entries are NaN). Blocks the host until
  * the stream reaches the end of the call.
@@ -190,13 +192,15 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation);
 
 /*
  * ga_history -- per-generation records kept when params.record != 0: best L
- * (FP64), best labels (int32, as stored), and the device clock (ns, %globaltimer)
- * at the end of each generation, for generations 0..count-1, count <= cap.
- * Host pointers (each optional). t_ns[0] is taken at the start of ga_init /
- * ga_reset, t_ns[1 + g] at the end of generation g. Waits for the stream.
+ * (FP64), best labels (int32, as stored), the device clock (ns, %globaltimer)
+ * and the number of same-cluster gene pairs sum_s n_s (n_s - 1) / 2 summed over
+ * the population (the work Eq. 6 needs), for generations 0..count-1,
+ * count <= cap. Host pointers (each optional). t_ns[0] is taken at the start
+ * of ga_init / ga_reset, t_ns[1 + g] at the end of generation g (so t_ns holds
+ * count + 1 values). Waits for the stream.
  */
-GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns, int cap,
-                        int *count);
+GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns,
+                        uint64_t *pairs, int cap, int *count);
 
 /*
  * ga_kernel_times -- stage durations (ms, CUDA events on the handle's stream) of

@@ -50,7 +50,7 @@ static int check_params(const gpga_params *p, int N)
     if (p->max_gens < 0) return set_error(GPGA_ERR_ARG, "max_gens < 0");
     if (p->scaling != GPGA_SCALING_RANK && p->scaling != GPGA_SCALING_PROP)
         return set_error(GPGA_ERR_ARG, "unknown scaling %d", p->scaling);
-    if (p->form != GPGA_FORM_PLAIN && p->form != GPGA_FORM_TENSOR)
+    if (p->form != GPGA_FORM_PLAIN && p->form != GPGA_FORM_TENSOR && p->form != GPGA_FORM_GATHER)
         return set_error(GPGA_ERR_ARG, "unknown form %d", p->form);
     if (p->init != GPGA_INIT_UNIFORM && p->init != GPGA_INIT_THRESHOLD)
         return set_error(GPGA_ERR_ARG, "unknown init %d", p->init);
@@ -79,6 +79,7 @@ int prepare_device()
     if (!rc) rc = prepare_ga_kernels(maxsmem);
     if (!rc) rc = prepare_init_kernels(maxsmem);
     if (!rc) rc = prepare_tc_kernels(maxsmem);
+    if (!rc) rc = prepare_gather_kernels(maxsmem);
     if (rc) return rc;
     ready[dev] = true;
     return GPGA_OK;
@@ -112,9 +113,11 @@ struct gpga_ga {
     double *hist = nullptr;
     uint16_t *ring = nullptr;
     unsigned long long *ts = nullptr;
+    unsigned long long *pairs = nullptr;
     int32_t *mst_order = nullptr, *mst_from = nullptr;
     double *mst_w = nullptr;
     int *err = nullptr;
+    int *diag = nullptr;
     int32_t *canon = nullptr;
     double *Lbest = nullptr;
     TcWork tc{};
@@ -164,10 +167,12 @@ size_t carve(gpga_ga *h, char *base)
     h->hist = c.take<double>(G);
     h->ring = h->prm.record ? c.take<uint16_t>(G * N) : nullptr;
     h->ts = h->prm.record ? c.take<unsigned long long>(G + 1) : nullptr;
+    h->pairs = h->prm.record ? c.take<unsigned long long>(G) : nullptr;
     h->mst_order = c.take<int32_t>(N);
     h->mst_from = c.take<int32_t>(N);
     h->mst_w = c.take<double>(N);
     h->err = c.take<int>(1);
+    h->diag = c.take<int>(1);
     h->canon = c.take<int32_t>(N);
     h->Lbest = c.take<double>(1);
     if (h->prm.form == GPGA_FORM_TENSOR) tc_carve(&h->tc, h->N, h->Np, h->P, &c.off, c.base);
@@ -181,6 +186,14 @@ int enqueue_score(gpga_ga *h, int sel_off, cudaEvent_t *evs = nullptr)
     const uint16_t *lab2[2] = {h->pop[0], h->pop[1]};
     const int tensor = h->prm.form == GPGA_FORM_TENSOR;
     int rc;
+    if (h->prm.form == GPGA_FORM_GATHER) {
+        rc = launch_gather_score<uint16_t>(lab2, h->Np, sel_off, h->P, h->N, h->Np, h->D32,
+                                           h->diag, h->logtab, h->L, h->err, h->st, h->pairs,
+                                           h->stream);
+        if (!rc) rc = mark(h, evs, 2);
+        if (!rc) rc = mark(h, evs, 3);
+        return rc;
+    }
     if (tensor)
         rc = tc_score<uint16_t>(&h->tc, h->Dhi, h->Dlo, h->Np, lab2, h->Np, sel_off, h->P, h->N,
                                 h->acc, h->st, h->stream);
@@ -190,7 +203,7 @@ int enqueue_score(gpga_ga *h, int sel_off, cudaEvent_t *evs = nullptr)
     if (!rc) rc = mark(h, evs, 2);
     if (!rc)
         rc = launch_assemble<uint16_t>(lab2, h->Np, sel_off, h->acc, h->Np, h->D32, tensor, h->P,
-                                       h->N, h->logtab, h->L, h->err, h->st, h->stream);
+                                       h->N, h->logtab, h->L, h->err, h->st, h->pairs, h->stream);
     if (!rc) rc = mark(h, evs, 3);
     return rc;
 }
@@ -247,9 +260,20 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs)
     uint16_t *next2[2] = {h->pop[1], h->pop[0]};
     const uint64_t *prefix = h->prm.scaling == GPGA_SCALING_PROP ? h->work_prefix : h->rank_prefix;
     int rc = mark(h, evs, 0);
-    if (!rc) rc = launch_evolve<uint16_t>(pop2, next2, e, h->perm, prefix, nullptr, h->st, h->stream);
-    if (!rc) rc = mark(h, evs, 1);
-    if (!rc) rc = enqueue_score(h, 1, evs);
+    if (h->prm.form == GPGA_FORM_GATHER) {
+        // selection, crossover, mutation, replacement and scoring in one kernel
+        if (!rc)
+            rc = launch_gather_generation<uint16_t>(pop2, next2, e, h->perm, prefix, h->Np, h->D32,
+                                                    h->diag, h->logtab, h->L, h->st, h->pairs,
+                                                    h->stream);
+        if (!rc) rc = mark(h, evs, 1);
+        if (!rc) rc = mark(h, evs, 2);
+        if (!rc) rc = mark(h, evs, 3);
+    } else {
+        if (!rc) rc = launch_evolve<uint16_t>(pop2, next2, e, h->perm, prefix, nullptr, h->st, h->stream);
+        if (!rc) rc = mark(h, evs, 1);
+        if (!rc) rc = enqueue_score(h, 1, evs);
+    }
     if (!rc) rc = enqueue_select(h, 1);
     if (!rc) rc = mark(h, evs, 4);
     return rc;
@@ -262,9 +286,14 @@ int enqueue_start(gpga_ga *h, const double *C)
     GPGA_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
     GPGA_CUDA(cudaMemsetAsync(h->rank, 0, (size_t)h->P * sizeof(int), h->stream));
     GPGA_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
+    GPGA_CUDA(cudaMemsetAsync(h->diag, 0, sizeof(int), h->stream));
+    if (h->pairs)
+        GPGA_CUDA(cudaMemsetAsync(h->pairs, 0, ((size_t)h->prm.max_gens + 1) * sizeof(unsigned long long),
+                                  h->stream));
     int rc = launch_state_init(h->st, h->ts, h->k0, h->k1, h->stream);
     if (rc) return rc;
-    rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->logtab, h->stream);
+    rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->logtab, h->diag,
+                       h->stream);
     if (rc) return rc;
     rc = rank_prefix_table(h->rank_prefix, h->P, h->stream);
     if (rc) return rc;
@@ -357,7 +386,7 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
     if (!labels || !C || !L) return set_error(GPGA_ERR_ARG, "ga_score: NULL pointer");
     if (N < 2 || N > GPGA_MAX_N || P < 1 || P > (1 << 24) || ld < N)
         return set_error(GPGA_ERR_ARG, "ga_score: P=%d N=%d ld=%d out of range", P, N, ld);
-    if (form != GPGA_FORM_PLAIN && form != GPGA_FORM_TENSOR)
+    if (form != GPGA_FORM_PLAIN && form != GPGA_FORM_TENSOR && form != GPGA_FORM_GATHER)
         return set_error(GPGA_ERR_ARG, "ga_score: unknown form %d", form);
     int rc = prepare_device();
     if (rc) return rc;
@@ -378,29 +407,32 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
     __nv_bfloat16 *Dlo = c.take<__nv_bfloat16>((size_t)Np * Np);
     float *acc = c.take<float>((size_t)P * Np);
     double *logtab = c.take<double>(logtab_len(N));
-    int *err = c.take<int>(1);
+    int *err = c.take<int>(2); // [0] label error, [1] diagonal flag
     TcWork tc{};
     if (form == GPGA_FORM_TENSOR) tc_carve(&tc, N, Np, P, &c.off, ws);
     int herr = 0;
     do {
-        if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
+        if (cudaMemsetAsync(err, 0, 2 * sizeof(int), s) != cudaSuccess) {
             rc = set_error(GPGA_ERR_CUDA, "ga_score: memset failed");
             break;
         }
         rc = launch_prep_d(C, N, N, Np, D32, form == GPGA_FORM_TENSOR ? Dhi : nullptr, Dlo,
-                           logtab, s);
+                           logtab, err + 1, s);
         if (rc) break;
         const int32_t *lab2[2] = {labels, labels};
-        if (form == GPGA_FORM_TENSOR) {
+        if (form == GPGA_FORM_GATHER) {
+            rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, D32, err + 1, logtab, L, err,
+                                              nullptr, nullptr, s);
+        } else if (form == GPGA_FORM_TENSOR) {
             rc = tc_score<int32_t>(&tc, Dhi, Dlo, Np, lab2, ld, 0, P, N, acc, nullptr, s);
             if (rc) break;
             rc = launch_assemble<int32_t>(lab2, ld, 0, acc, Np, D32, 1, P, N, logtab, L, err,
-                                          nullptr, s);
+                                          nullptr, nullptr, s);
         } else {
             rc = launch_pair_plain<int32_t>(D32, Np, lab2, ld, 0, P, N, acc, nullptr, s);
             if (rc) break;
             rc = launch_assemble<int32_t>(lab2, ld, 0, acc, Np, D32, 0, P, N, logtab, L, err,
-                                          nullptr, s);
+                                          nullptr, nullptr, s);
         }
         if (rc) break;
         cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -599,8 +631,8 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation)
     return GPGA_OK;
 }
 
-GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns, int cap,
-                        int *count)
+GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns,
+                        uint64_t *pairs, int cap, int *count)
 {
     g_err[0] = 0;
     if (!h) return set_error(GPGA_ERR_ARG, "ga_history: NULL handle");
@@ -612,7 +644,7 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
     if (count) *count = n;
     if (n <= 0) return GPGA_OK;
     if (best_L) GPGA_CUDA(cudaMemcpy(best_L, h->hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
-    if (best_labels || t_ns) {
+    if (best_labels || t_ns || pairs) {
         if (!h->prm.record) return set_error(GPGA_ERR_STATE, "ga_history: run created with record = 0");
     }
     if (best_labels) {
@@ -625,6 +657,7 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
         delete[] tmp;
         if (e != cudaSuccess) return cuda_error(e, "ga_history copy", __FILE__, __LINE__);
     }
+    if (pairs) GPGA_CUDA(cudaMemcpy(pairs, h->pairs, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (t_ns) GPGA_CUDA(cudaMemcpy(t_ns, h->ts, (size_t)(n + 1 > cap ? cap : n + 1) * sizeof(int64_t),
                                    cudaMemcpyDeviceToHost));
     return GPGA_OK;

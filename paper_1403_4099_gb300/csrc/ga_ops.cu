@@ -120,31 +120,6 @@ int launch_state_init(DevState *st, unsigned long long *ts0, uint32_t k0, uint32
     return GPGA_OK;
 }
 
-// ---------------------------------------------------------------------------
-// SUS pointer x_k = floor((k 2^32 + u) W / (M 2^32)) in exact integer
-// arithmetic: A = (k 2^32 + u) W < 2^127 as two 64-bit words, divided by M with
-// 32-bit long division, then shifted right by 32.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t W, uint32_t M)
-{
-    const uint64_t num = ((uint64_t)k << 32) | u;
-    const uint64_t lo = num * W;
-    const uint64_t hi = __umul64hi(num, W);
-    // 128-bit (hi:lo) / M, limb by limb (32-bit limbs, most significant first)
-    const uint32_t limb[4] = {(uint32_t)(hi >> 32), (uint32_t)hi, (uint32_t)(lo >> 32),
-                              (uint32_t)lo};
-    uint32_t q[4];
-    uint64_t rem = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const uint64_t cur = (rem << 32) | limb[t];
-        q[t] = (uint32_t)(cur / M);
-        rem = cur % M;
-    }
-    // quotient >> 32 = limbs q0 q1 q2 (q0 is zero since the pointer is below W)
-    return ((uint64_t)q[1] << 32) | q[2];
-}
-
 // FP64 fitness as an unsigned key with the same order (NaN mapped to -inf and
 // -0 to +0 first): flip all bits of negatives, set the sign bit of the rest. Integer compares
 // keep the sort off the FP64 pipe.
@@ -342,22 +317,6 @@ template int launch_select<int32_t>(const double *, const SelectCfg &, int *, in
 // Every gene is a function of (a_j, b_j) and warp-uniform values, so lanes
 // stream gene pairs with no shared memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int sus_parent(int k, uint32_t u, uint64_t W, int M, int P,
-                                          const uint64_t *__restrict__ prefix,
-                                          const int32_t *__restrict__ perm)
-{
-    const uint64_t x = sus_pointer((uint32_t)k, u, W, (uint32_t)M);
-    int lo = 0, hi = P - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(prefix + mid) > x)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return perm[lo];
-}
-
 template <typename LabT>
 __global__ void __launch_bounds__(256)
     evolve_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1, EvolveCfg cfg,
@@ -386,56 +345,8 @@ __global__ void __launch_bounds__(256)
         for (int j = lane; j < N; j += 32) dst[j] = src[j];
         return;
     }
-    const int k = slot - cfg.E;
-    const int M = cfg.M;
-    int par = 0;
-    if (lane < 2) {
-        const uint64_t W = __ldg(prefix + cfg.P - 1);
-        const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
-        par = sus_parent(lane == 0 ? k : (k + M / 2) % M, su.x, W, M, cfg.P, prefix, perm);
-    }
-    const int ia = __shfl_sync(0xffffffffu, par, 0);
-    const int ib = __shfl_sync(0xffffffffu, par, 1);
-    if (parents_out && lane == 0) parents_out[k] = ia;
-    const LabT *a = cur + (size_t)ia * ldp;
-    const LabT *b = cur + (size_t)ib * ldp;
-    const U4 xw = philox((uint32_t)g, (uint32_t)k, 0u, STREAM_XOVER, k0, k1);
-    int mode = 0, cut = N;
-    int bq = 0, aq = 0;
-    if ((uint64_t)xw.x < cfg.thr_pc) {
-        if ((uint64_t)xw.y < cfg.thr_pkb) {
-            mode = 2;
-            const int q = draw_below(xw.z, (uint32_t)N);
-            bq = (int)b[q];
-            aq = (int)a[q];
-        } else {
-            mode = 1;
-            cut = 1 + draw_below(xw.z, (uint32_t)(N - 1));
-        }
-    }
-    const int npair = (N + 1) >> 1;
-    for (int m = lane; m < npair; m += 32) {
-        const int j0 = 2 * m, j1 = 2 * m + 1;
-        int a0 = (int)a[j0], b0 = (int)b[j0];
-        int a1 = 0, b1 = 0;
-        if (j1 < N) {
-            a1 = (int)a[j1];
-            b1 = (int)b[j1];
-        }
-        int c0 = a0, c1 = a1;
-        if (mode == 1) {
-            if (j0 >= cut) c0 = b0;
-            if (j1 >= cut) c1 = b1;
-        } else if (mode == 2) {
-            if (b0 == bq) c0 = aq;
-            if (b1 == bq) c1 = aq;
-        }
-        const U4 mw = philox((uint32_t)g, (uint32_t)k, (uint32_t)m, STREAM_MUT, k0, k1);
-        if ((uint64_t)mw.x < cfg.thr_pm) c0 = draw_below(mw.y, (uint32_t)N);
-        if ((uint64_t)mw.z < cfg.thr_pm) c1 = draw_below(mw.w, (uint32_t)N);
-        dst[j0] = (LabT)c0;
-        if (j1 < N) dst[j1] = (LabT)c1;
-    }
+    child_genes<LabT>(cur, ldp, N, cfg, g, slot - cfg.E, k0, k1, perm, prefix, parents_out, dst,
+                      nullptr, lane);
 }
 
 template <typename LabT>

@@ -1,0 +1,352 @@
+// gather.cu -- gather form of the likelihood (Eq. 5, 6, 8) and the fused GA
+// generation (selection, crossover, mutation, replacement + scoring).
+//
+// Work per configuration is what Eq. 6 needs, not N^2: genes are sorted by
+// label (stable counting sort), and only same-cluster pairs are visited:
+//   d_s = sum_{i,j in s} D_ij = 2 sum_{a<b} D_{m_a m_b} + sum_a D_{m_a m_a},
+// sum_s n_s (n_s - 1) / 2 gathers of D (FP32, L2-resident) instead of a dense
+// sweep. One warp per individual; everything (labels, histogram, members,
+// per-label fixed-point bins) lives in that warp's slice of shared memory.
+// Pairs of all non-singleton clusters are flattened and dealt to lanes; a lane
+// sums its pairs of one cluster in FP32 and adds the sum, in fixed point, to
+// the cluster's bin with an integer atomic (order-independent: deterministic).
+// Eq. 8 then follows in the one-log product form.
+#include <math.h>
+
+#include "gpga_internal.cuh"
+
+namespace gpga {
+
+// per-warp shared-memory slice for Np padded genes
+struct GatherSlice {
+    unsigned long long *dfx; // Np: fixed-point d per label
+    int *start;              // Np + 1: cluster start in mem (then compacted starts)
+    int *fill;               // Np: counts / fill pointers (then compacted sizes)
+    int *cpp;                // Np + 1: exclusive prefix of pair counts, compacted
+    uint16_t *lab;           // Np: labels
+    uint16_t *mem;           // Np: gene indices sorted by label, stable
+};
+
+__host__ __device__ inline size_t gather_slice_bytes(int Np)
+{
+    return (size_t)Np * 8 + (size_t)(Np + 4) * 4 * 3 + (size_t)Np * 2 * 2;
+}
+
+__device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
+{
+    GatherSlice s;
+    s.dfx = reinterpret_cast<unsigned long long *>(base);
+    s.start = reinterpret_cast<int *>(base + (size_t)Np * 8);
+    s.fill = s.start + (Np + 4);
+    s.cpp = s.fill + (Np + 4);
+    s.lab = reinterpret_cast<uint16_t *>(s.cpp + (Np + 4));
+    s.mem = s.lab + Np;
+    return s;
+}
+
+// exclusive warp scan of x (lane order)
+__device__ __forceinline__ int warp_excl_scan(int x, int lane, int &total)
+{
+    int v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    total = __shfl_sync(0xffffffffu, v, 31);
+    return v - x;
+}
+
+// Score one configuration held in sl.lab[0..N) (labels < N). Returns L on all
+// lanes. D32: Np x Np FP32 D = 1 - C; diag: nonzero if some D_ii != 0.
+__device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
+                                    const float *__restrict__ D32, int diag, int fix_bits,
+                                    const double2 *__restrict__ ltab,
+                                    const double *__restrict__ ktab, int lane,
+                                    unsigned long long *pairs_out)
+{
+    // histogram
+    for (int s = lane; s < N; s += 32) {
+        sl.fill[s] = 0;
+        sl.dfx[s] = 0ull;
+    }
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) atomicAdd(&sl.fill[sl.lab[i]], 1);
+    __syncwarp();
+    // exclusive scan -> start; fill pointers = start
+    {
+        const int per = (N + 31) >> 5;
+        const int lo = lane * per, hi = min(N, lo + per);
+        int sum = 0;
+        for (int s = lo; s < hi; ++s) sum += sl.fill[s];
+        int total;
+        int run = warp_excl_scan(sum, lane, total);
+        __syncwarp();
+        for (int s = lo; s < hi; ++s) {
+            const int c = sl.fill[s];
+            sl.start[s] = run;
+            sl.fill[s] = run;
+            run += c;
+        }
+        if (lane == 0) sl.start[N] = N;
+    }
+    __syncwarp();
+    // stable scatter of gene indices by label, 32 genes at a time in index order
+    for (int base = 0; base < N; base += 32) {
+        const int i = base + lane;
+        const unsigned act = __ballot_sync(0xffffffffu, i < N);
+        if (i < N) {
+            const int s = sl.lab[i];
+            const unsigned peers = __match_any_sync(act, s);
+            const int pos = sl.fill[s] + __popc(peers & ((1u << lane) - 1u));
+            sl.mem[pos] = (uint16_t)i;
+            __syncwarp(act);
+            if ((peers & ((1u << lane) - 1u)) == 0u) sl.fill[s] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    // diagonal terms D_ii into the bins (zero for a Pearson C)
+    if (diag) {
+        const float fs = exp2f((float)fix_bits);
+        for (int i = lane; i < N; i += 32)
+            atomicAdd(&sl.dfx[sl.lab[i]],
+                      (unsigned long long)__float2ll_rn(D32[(size_t)i * Np + i] * fs));
+    }
+    // compact non-singleton clusters in place: start[c] = cluster start in mem,
+    // fill[c] = size, cpp[c] = pair count (prefix below)
+    int nlist = 0;
+    for (int base = 0; base < N; base += 32) {
+        const int s = base + lane;
+        int st = 0, n = 0;
+        if (s < N) {
+            st = sl.start[s];
+            n = sl.fill[s] - st;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, n >= 2);
+        __syncwarp();
+        if (n >= 2) {
+            const int c = nlist + __popc(m & ((1u << lane) - 1u));
+            sl.start[c] = st;
+            sl.fill[c] = n;
+        }
+        nlist += __popc(m);
+        __syncwarp();
+    }
+    {
+        const int per = (nlist + 31) >> 5;
+        const int lo = lane * per, hi = min(nlist, lo + per);
+        int sum = 0;
+        for (int c = lo; c < hi; ++c) {
+            const int n = sl.fill[c];
+            sum += n * (n - 1) / 2;
+        }
+        int total;
+        int run = warp_excl_scan(sum, lane, total);
+        for (int c = lo; c < hi; ++c) {
+            const int n = sl.fill[c];
+            sl.cpp[c] = run;
+            run += n * (n - 1) / 2;
+        }
+        if (lane == 0) sl.cpp[nlist] = total;
+    }
+    __syncwarp();
+    // pairs, flattened over clusters and dealt round-robin to lanes
+    const int tot = sl.cpp[nlist];
+    if (pairs_out && lane == 0) atomicAdd(pairs_out, (unsigned long long)tot);
+    const float fs2 = 2.f * exp2f((float)fix_bits);
+    int c = 0, cur = -1;
+    float accf = 0.f;
+    for (int t = lane; t < tot; t += 32) {
+        while (sl.cpp[c + 1] <= t) ++c;
+        if (c != cur) {
+            if (cur >= 0)
+                atomicAdd(&sl.dfx[sl.lab[sl.mem[sl.start[cur]]]],
+                          (unsigned long long)__float2ll_rn(accf * fs2));
+            cur = c;
+            accf = 0.f;
+        }
+        // pair u of the cluster in column order: u = b (b - 1) / 2 + a, a < b
+        const int u = t - sl.cpp[c];
+        int b;
+        if (u < (1 << 21)) {
+            b = (int)((1.0f + sqrtf((float)(8 * u + 1))) * 0.5f);
+        } else {
+            b = (int)((1.0 + sqrt((double)(8.0 * u + 1.0))) * 0.5);
+        }
+        if (b * (b - 1) / 2 > u) --b;
+        else if ((b + 1) * b / 2 <= u) ++b;
+        const int a = u - b * (b - 1) / 2;
+        const int st = sl.start[c];
+        const int i = sl.mem[st + a], j = sl.mem[st + b];
+        accf += __ldg(D32 + (size_t)i * Np + j);
+    }
+    if (cur >= 0)
+        atomicAdd(&sl.dfx[sl.lab[sl.mem[sl.start[cur]]]],
+                  (unsigned long long)__float2ll_rn(accf * fs2));
+    __syncwarp();
+    LogProd acc_l;
+    for (int k = lane; k < nlist; k += 32) {
+        const int lb = sl.lab[sl.mem[sl.start[k]]];
+        logprod_add(acc_l, sl.fill[k], (long long)sl.dfx[lb], fix_bits, ktab);
+    }
+    const double L = logprod_finish(acc_l, ltab, nlist);
+    __syncwarp();
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Score-only: one warp per individual of lab (stateful: the buffer selected by
+// st->gen + sel_off).
+// ---------------------------------------------------------------------------
+template <typename LabT>
+__global__ void __launch_bounds__(256)
+    gather_score_kernel(const LabT *lab0, const LabT *lab1, int ldl, int sel_off, int P, int N,
+                        int Np, const float *__restrict__ D32, const int *__restrict__ diag_flag,
+                        const double *__restrict__ logtab, int fix_bits, double *__restrict__ L,
+                        int *__restrict__ err, const DevState *__restrict__ st,
+                        unsigned long long *__restrict__ pairs)
+{
+    const LabT *__restrict__ lab = lab0;
+    unsigned long long *pairs_g = nullptr;
+    if (st) {
+        if (st->done) return;
+        const int gen = st->gen + sel_off;
+        lab = (gen & 1) ? lab1 : lab0;
+        if (pairs) pairs_g = pairs + gen;
+    }
+    extern __shared__ unsigned char smem_g[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
+    const double2 *ltab = reinterpret_cast<const double2 *>(logtab);
+    const double *ktab = logtab + 2 * LOG_TAB;
+    const int diag = *diag_flag;
+    for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
+        bool bad = false;
+        const LabT *lp = lab + (size_t)p * ldl;
+        for (int i = lane; i < N; i += 32) {
+            const int v = (int)lp[i];
+            const bool ok = v >= 0 && v < N;
+            bad |= !ok;
+            sl.lab[i] = (uint16_t)(ok ? v : 0);
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        __syncwarp();
+        const double v = gather_score_warp(sl, N, Np, D32, diag, fix_bits, ltab, ktab, lane, pairs_g);
+        if (lane == 0) {
+            L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v;
+            if (bad && err) atomicOr(err, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused generation: warp `slot` builds slot of the next population exactly as
+// the evolve kernel does (elite copy, or SUS parents + crossover + mutation)
+// into global memory and its shared slice, then scores it.
+// ---------------------------------------------------------------------------
+template <typename LabT>
+__global__ void __launch_bounds__(256)
+    gather_generation_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1,
+                             EvolveCfg cfg, const int32_t *__restrict__ perm,
+                             const uint64_t *__restrict__ prefix, int Np,
+                             const float *__restrict__ D32, const int *__restrict__ diag_flag,
+                             const double *__restrict__ logtab, int fix_bits,
+                             double *__restrict__ L, const DevState *__restrict__ st,
+                             unsigned long long *__restrict__ pairs)
+{
+    if (st->done) return;
+    const int g = st->gen;
+    const uint32_t k0 = st->k0, k1 = st->k1;
+    const LabT *cur = (g & 1) ? pop1 : pop0;
+    LabT *nxt = (g & 1) ? next1 : next0;
+    extern __shared__ unsigned char smem_g[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int slot = blockIdx.x * nw + warp;
+    if (slot >= cfg.P) return;
+    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
+    const int N = cfg.N, ldp = cfg.ldp;
+    LabT *dst = nxt + (size_t)slot * ldp;
+    if (slot < cfg.E) {
+        const LabT *src = cur + (size_t)perm[slot] * ldp;
+        for (int j = lane; j < N; j += 32) {
+            const LabT v = src[j];
+            dst[j] = v;
+            sl.lab[j] = (uint16_t)v;
+        }
+    } else {
+        const int k = slot - cfg.E;
+        child_genes<LabT>(cur, ldp, N, cfg, g, k, k0, k1, perm, prefix, nullptr, dst, sl.lab,
+                          lane);
+    }
+    __syncwarp();
+    const double v = gather_score_warp(sl, N, Np, D32, *diag_flag, fix_bits,
+                                       reinterpret_cast<const double2 *>(logtab),
+                                       logtab + 2 * LOG_TAB, lane, pairs ? pairs + g + 1 : nullptr);
+    if (lane == 0) L[slot] = v;
+}
+
+static int warps_for(int Np)
+{
+    const size_t per = gather_slice_bytes(Np);
+    int nw = 8;
+    while (nw > 1 && nw * per > (size_t)200 * 1024) nw >>= 1;
+    return nw;
+}
+
+template <typename LabT>
+int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, int N, int Np,
+                        const float *D32, const int *diag_flag, const double *logtab,
+                        double *L, int *err, const DevState *st, unsigned long long *pairs,
+                        cudaStream_t s)
+{
+    const int nw = warps_for(Np);
+    const size_t smem = nw * gather_slice_bytes(Np);
+    const int grid = (P + nw - 1) / nw;
+    gather_score_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, P, N,
+                                                          Np, D32, diag_flag, logtab,
+                                                          fix_bits_for(N), L, err, st, pairs);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+template <typename LabT>
+int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
+                             const int32_t *perm, const uint64_t *prefix, int Np,
+                             const float *D32, const int *diag_flag, const double *logtab,
+                             double *L, const DevState *st, unsigned long long *pairs,
+                             cudaStream_t s)
+{
+    const int nw = warps_for(Np);
+    const size_t smem = nw * gather_slice_bytes(Np);
+    const int grid = (cfg.P + nw - 1) / nw;
+    gather_generation_kernel<LabT><<<grid, 32 * nw, smem, s>>>(
+        pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, D32, diag_flag, logtab,
+        fix_bits_for(cfg.N), L, st, pairs);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+template int launch_gather_score<uint16_t>(const uint16_t *const *, int, int, int, int, int,
+                                           const float *, const int *, const double *, double *,
+                                           int *, const DevState *, unsigned long long *,
+                                           cudaStream_t);
+template int launch_gather_score<int32_t>(const int32_t *const *, int, int, int, int, int,
+                                          const float *, const int *, const double *, double *,
+                                          int *, const DevState *, unsigned long long *,
+                                          cudaStream_t);
+template int launch_gather_generation<uint16_t>(const uint16_t *const *, uint16_t *const *,
+                                                const EvolveCfg &, const int32_t *,
+                                                const uint64_t *, int, const float *,
+                                                const int *, const double *, double *,
+                                                const DevState *, unsigned long long *,
+                                                cudaStream_t);
+
+int prepare_gather_kernels(int maxsmem)
+{
+    if (int rc = raise_smem(gather_score_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(gather_score_kernel<int32_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(gather_generation_kernel<uint16_t>, maxsmem)) return rc;
+    return GPGA_OK;
+}
+
+} // namespace gpga

@@ -120,23 +120,102 @@ __device__ __forceinline__ double table_log(double x, const double2 *__restrict_
 }
 
 // layout of the per-run log table (doubles): LOG_TAB pairs (inv_k, -log inv_k),
-// then K1[n], n = 0..N (see score.cu)
+// then K[n] = 1/2 (log n + (n - 1) log(n (n - 1))), n = 0..N
 inline size_t logtab_len(int N) { return 2 * LOG_TAB + (size_t)N + 1; }
+
+// ---------------------------------------------------------------------------
+// Eq. 8 of one configuration from its non-singleton clusters, with one log:
+//   L = sum_s K[n_s] - 1/2 log prod_s c_s d_s^(n_s - 1)
+// (the bracket of Eq. 8 is log(n/c) + (n-1) log(n(n-1)/d)). c_s, d_s arrive as
+// exact fixed-point integers cf = c_s 2^b, df = d_s 2^b; the product is kept as
+// a mantissa in [1, 2) and an integer exponent, renormalised after every
+// multiply from the bit pattern (no overflow, no FP64 log per cluster), and
+// the 2^(b n_s) of each cluster's factor is removed from the exponent exactly.
+// Domain floor of Eq. 8 (degenerate data only): c_s >= n_s 2^-40,
+// d_s >= n_s (n_s - 1) 2^-40, applied in fixed point (at least 1 unit).
+// ---------------------------------------------------------------------------
+struct LogProd {
+    double m = 1.0;  // mantissa in [1, 2)
+    long long e = 0; // binary exponent
+    double k = 0.0;  // sum of K[n_s]
+};
+
+__device__ __forceinline__ void renorm(double &m, long long &e)
+{
+    const long long b = __double_as_longlong(m);
+    e += ((b >> 52) & 0x7ff) - 1023;
+    m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+}
+
+__device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int fix_bits,
+                                            const double *__restrict__ ktab)
+{
+    long long cf = (((long long)n * n) << fix_bits) - df;
+    const int sh = 40 - fix_bits; // fix_bits <= 40
+    long long cmin = (long long)n >> sh, dmin = ((long long)n * (n - 1)) >> sh;
+    if (cmin < 1) cmin = 1;
+    if (dmin < 1) dmin = 1;
+    if (cf < cmin) cf = cmin;
+    if (df < dmin) df = dmin;
+    a.m *= (double)cf;
+    renorm(a.m, a.e);
+    double md = (double)df;
+    long long ed = 0;
+    renorm(md, ed);
+    for (int q = n - 1;;) { // d^(n-1) by binary exponentiation
+        if (q & 1) {
+            a.m *= md;
+            a.e += ed;
+            renorm(a.m, a.e);
+        }
+        q >>= 1;
+        if (!q) break;
+        md *= md;
+        ed *= 2;
+        renorm(md, ed);
+    }
+    a.e -= (long long)fix_bits * n; // c and the n - 1 factors d each carried 2^b
+    a.k += ktab[n];
+}
+
+// combine the lanes' partial products (fixed xor butterfly: every lane ends
+// with the same value) and return L
+__device__ __forceinline__ double logprod_finish(LogProd a, const double2 *__restrict__ ltab,
+                                                 int nclusters)
+{
+    if (nclusters == 0) return 0.0; // all singletons: Eq. 8 is an empty sum
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double m2 = __shfl_xor_sync(0xffffffffu, a.m, o);
+        const long long e2 = __shfl_xor_sync(0xffffffffu, a.e, o);
+        const double k2 = __shfl_xor_sync(0xffffffffu, a.k, o);
+        a.m *= m2;
+        a.e += e2;
+        renorm(a.m, a.e);
+        a.k += k2;
+    }
+    return fma(-0.5, fma((double)a.e, 0.6931471805599453, table_log(a.m, ltab)), a.k);
+}
 
 // ---------------------------------------------------------------------------
 // host launchers (score.cu)
 // ---------------------------------------------------------------------------
+// D forms and log tables; *diag_flag (zeroed by the caller) becomes nonzero if
+// some D_ii != 0
 int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,
-                  __nv_bfloat16 *Dlo, double *logtab, cudaStream_t s);
+                  __nv_bfloat16 *Dlo, double *logtab, int *diag_flag, cudaStream_t s);
 
 template <typename LabT>
 int launch_pair_plain(const float *D32, int Np, const LabT *const *lab2, int ldl, int sel_off,
                       int P, int N, float *acc, const DevState *st, cudaStream_t s);
 
+// pairs (optional, stateful): per-generation sum of n_s (n_s - 1) / 2, indexed
+// by the generation being scored
 template <typename LabT>
 int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *acc, int Np,
                     const float *D32, int full_rows, int P, int N, const double *logtab,
-                    double *L, int *err, const DevState *st, cudaStream_t s);
+                    double *L, int *err, const DevState *st, unsigned long long *pairs,
+                    cudaStream_t s);
 
 int launch_log_selftest(const double *x, int n, double *yt, double *yc, cudaStream_t s);
 
@@ -160,6 +239,8 @@ int prepare_score_kernels(int maxsmem);
 int prepare_ga_kernels(int maxsmem);
 int prepare_init_kernels(int maxsmem);
 int prepare_tc_kernels(int maxsmem);
+int prepare_gather_kernels(int maxsmem);
+
 
 // ---------------------------------------------------------------------------
 // host launchers (ga_ops.cu)
@@ -196,10 +277,144 @@ struct EvolveCfg {
 
 // prefix: inclusive prefix of the scaled weights by rank (RANK: the fixed
 // table; PROP: the work prefix written by finalize); parents_out optional
+// ---------------------------------------------------------------------------
+// One child of the next population (warp-cooperative; all lanes call).
+// "Apply genetic operator: selection" (SUS): the P individuals lie on a line
+// in rank order over segments of their scaled weights (prefix[r] inclusive,
+// W = prefix[P-1]); pointer x_k = floor((k 2^32 + u) W / (M 2^32)) with
+// u = word 0 of Philox(g, 0, 0, SUS) selects rank r with
+// prefix[r-1] <= x_k < prefix[r]. Child k pairs a = parent(k) with
+// b = parent((k + M/2) mod M).
+// Crossover: Philox(g, k, 0, XOVER) = (x, y, z, .): if x < thr(P_c), then the
+// knowledge-based merge if y < thr(P_kb) with anchor q = draw(z, N):
+// child_j = a_q where b_j = b_q, else a_j; otherwise one-point at
+// cut = 1 + draw(z, N - 1): child_j = a_j for j < cut, b_j after.
+// Mutation, gene pair (2m, 2m+1): Philox(g, k, m, MUT) = (f0, v0, f1, v1):
+// child_j = draw(v, N) if f < thr(P_m).
+// Every gene is a function of (a_j, b_j) and warp-uniform values, so lanes
+// stream gene pairs. Writes dst (global) and, if given, lab_s (shared).
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// SUS pointer x_k = floor((k 2^32 + u) W / (M 2^32)) in exact integer
+// arithmetic: A = (k 2^32 + u) W < 2^127 as two 64-bit words, divided by M with
+// 32-bit long division, then shifted right by 32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t W, uint32_t M)
+{
+    const uint64_t num = ((uint64_t)k << 32) | u;
+    const uint64_t lo = num * W;
+    const uint64_t hi = __umul64hi(num, W);
+    // 128-bit (hi:lo) / M, limb by limb (32-bit limbs, most significant first)
+    const uint32_t limb[4] = {(uint32_t)(hi >> 32), (uint32_t)hi, (uint32_t)(lo >> 32),
+                              (uint32_t)lo};
+    uint32_t q[4];
+    uint64_t rem = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const uint64_t cur = (rem << 32) | limb[t];
+        q[t] = (uint32_t)(cur / M);
+        rem = cur % M;
+    }
+    // quotient >> 32 = limbs q0 q1 q2 (q0 is zero since the pointer is below W)
+    return ((uint64_t)q[1] << 32) | q[2];
+}
+
+__device__ __forceinline__ int sus_parent(int k, uint32_t u, uint64_t W, int M, int P,
+                                          const uint64_t *__restrict__ prefix,
+                                          const int32_t *__restrict__ perm)
+{
+    const uint64_t x = sus_pointer((uint32_t)k, u, W, (uint32_t)M);
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) > x)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return perm[lo];
+}
+
+template <typename LabT>
+__device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, const EvolveCfg &cfg,
+                                            int g, int k, uint32_t k0, uint32_t k1,
+                                            const int32_t *__restrict__ perm,
+                                            const uint64_t *__restrict__ prefix,
+                                            int32_t *__restrict__ parents_out, LabT *dst,
+                                            uint16_t *lab_s, int lane)
+{
+    const int M = cfg.M;
+    int par = 0;
+    if (lane < 2) {
+        const uint64_t W = __ldg(prefix + cfg.P - 1);
+        const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
+        par = sus_parent(lane == 0 ? k : (k + M / 2) % M, su.x, W, M, cfg.P, prefix, perm);
+    }
+    const int ia = __shfl_sync(0xffffffffu, par, 0);
+    const int ib = __shfl_sync(0xffffffffu, par, 1);
+    if (parents_out && lane == 0) parents_out[k] = ia;
+    const LabT *a = cur + (size_t)ia * ldp;
+    const LabT *b = cur + (size_t)ib * ldp;
+    const U4 xw = philox((uint32_t)g, (uint32_t)k, 0u, STREAM_XOVER, k0, k1);
+    int mode = 0, cut = N;
+    int bq = 0, aq = 0;
+    if ((uint64_t)xw.x < cfg.thr_pc) {
+        if ((uint64_t)xw.y < cfg.thr_pkb) {
+            mode = 2;
+            const int q = draw_below(xw.z, (uint32_t)N);
+            bq = (int)b[q];
+            aq = (int)a[q];
+        } else {
+            mode = 1;
+            cut = 1 + draw_below(xw.z, (uint32_t)(N - 1));
+        }
+    }
+    const int npair = (N + 1) >> 1;
+    for (int m = lane; m < npair; m += 32) {
+        const int j0 = 2 * m, j1 = 2 * m + 1;
+        int a0 = (int)a[j0], b0 = (int)b[j0];
+        int a1 = 0, b1 = 0;
+        if (j1 < N) {
+            a1 = (int)a[j1];
+            b1 = (int)b[j1];
+        }
+        int c0 = a0, c1 = a1;
+        if (mode == 1) {
+            if (j0 >= cut) c0 = b0;
+            if (j1 >= cut) c1 = b1;
+        } else if (mode == 2) {
+            if (b0 == bq) c0 = aq;
+            if (b1 == bq) c1 = aq;
+        }
+        const U4 mw = philox((uint32_t)g, (uint32_t)k, (uint32_t)m, STREAM_MUT, k0, k1);
+        if ((uint64_t)mw.x < cfg.thr_pm) c0 = draw_below(mw.y, (uint32_t)N);
+        if ((uint64_t)mw.z < cfg.thr_pm) c1 = draw_below(mw.w, (uint32_t)N);
+        dst[j0] = (LabT)c0;
+        if (lab_s) lab_s[j0] = (uint16_t)c0;
+        if (j1 < N) {
+            dst[j1] = (LabT)c1;
+            if (lab_s) lab_s[j1] = (uint16_t)c1;
+        }
+    }
+}
+
 template <typename LabT>
 int launch_evolve(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
                   const int32_t *perm, const uint64_t *prefix, int32_t *parents_out,
                   const DevState *st, cudaStream_t s);
+
+// gather form (gather.cu)
+template <typename LabT>
+int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, int N, int Np,
+                        const float *D32, const int *diag_flag, const double *logtab,
+                        double *L, int *err, const DevState *st, unsigned long long *pairs,
+                        cudaStream_t s);
+template <typename LabT>
+int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
+                             const int32_t *perm, const uint64_t *prefix, int Np,
+                             const float *D32, const int *diag_flag, const double *logtab,
+                             double *L, const DevState *st, unsigned long long *pairs,
+                             cudaStream_t s);
 
 int launch_state_init(DevState *st, unsigned long long *ts0, uint32_t k0, uint32_t k1,
                       cudaStream_t s);

@@ -39,7 +39,7 @@ __device__ __forceinline__ void log_tab_entry(int k, double *out)
 __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int Np,
                               float *__restrict__ D32, __nv_bfloat16 *__restrict__ Dhi,
                               __nv_bfloat16 *__restrict__ Dlo, double *__restrict__ logtab,
-                              int fix_bits)
+                              int *__restrict__ diag_flag)
 {
     const size_t total = (size_t)Np * Np;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -52,6 +52,7 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
         }
         const float df = (float)d;
         D32[idx] = df;
+        if (diag_flag && i == j && df != 0.f) *diag_flag = 1;
         if (Dhi) {
             const __nv_bfloat16 hi = __double2bfloat16(d);
             const double rem = d - (double)__bfloat162float(hi);
@@ -61,15 +62,14 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
     }
     if (logtab) {
         // log table of table_log(), then the per-size constant of the assembly:
-        // K1[n] = 1/2 (n B + log n + (n - 1) log(n (n - 1))), B = fix_bits ln 2
+        // K[n] = 1/2 (log n + (n - 1) log(n (n - 1)))
         const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
         for (int k = tid; k < LOG_TAB; k += nt) log_tab_entry(k, logtab + 2 * k);
-        const double B = (double)fix_bits * 0.6931471805599453;
         for (int n = tid; n <= N; n += nt) {
             double v = 0.0;
             if (n >= 2) {
                 const double dn = (double)n;
-                v = 0.5 * (dn * B + log(dn) + (dn - 1.0) * (log(dn) + log(dn - 1.0)));
+                v = 0.5 * (log(dn) + (dn - 1.0) * (log(dn) + log(dn - 1.0)));
             }
             logtab[2 * LOG_TAB + n] = v;
         }
@@ -77,12 +77,12 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
 }
 
 int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,
-                  __nv_bfloat16 *Dlo, double *logtab, cudaStream_t s)
+                  __nv_bfloat16 *Dlo, double *logtab, int *diag_flag, cudaStream_t s)
 {
     const size_t total = (size_t)Np * Np;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, logtab, fix_bits_for(N));
+    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, logtab, diag_flag);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
@@ -211,13 +211,9 @@ int launch_pair_plain(const float *D32, int Np, const LabT *const *lab2, int ldl
 // Assembly (Eq. 5 and Eq. 8): one warp per individual. Row sums are turned into
 // fixed point (scale 2^b) and added into per-label bins with integer shared-
 // memory atomics, so d_s is independent of the order of the additions (the score
-// is deterministic). The non-singleton clusters are compacted, then each term
-// is taken from the exact integers dfix = d_s 2^b and cfix = n_s^2 2^b - dfix:
-//   t_s = K1[n] - 1/2 [ log cfix + (n - 1) log dfix ],
-//   K1[n] = 1/2 [ n b ln2 + log n + (n - 1) log(n (n - 1)) ]
-// which is Eq. 8 with c_s = cfix 2^-b, d_s = dfix 2^-b. For n <= 16 the bracket
-// is one log of cfix dfix^(n-1) (< 2^800, no overflow). Terms are summed per
-// lane in compacted order and across lanes by a fixed butterfly.
+// is deterministic). The non-singleton clusters are compacted and Eq. 8 is
+// evaluated from the exact integers dfix = d_s 2^b, cfix = n_s^2 2^b - dfix by
+// the one-log product form (LogProd, gpga_internal.cuh).
 //   full_rows = 0: row value = 2 u_i + D_ii (upper-triangle sums of the plain form)
 //   full_rows = 1: row value = y_i = sum_j D_ij [s_j = s_i] (tensor form)
 // ---------------------------------------------------------------------------
@@ -226,22 +222,23 @@ __global__ void __launch_bounds__(256)
     assemble_kernel(const LabT *lab0, const LabT *lab1, int ldl, int sel_off,
                     const float *__restrict__ acc, int Np, const float *__restrict__ D32,
                     int full_rows, int P, int N, const double *__restrict__ logtab, int fix_bits,
-                    double *__restrict__ L, int *__restrict__ err, const DevState *__restrict__ st)
+                    double *__restrict__ L, int *__restrict__ err, const DevState *__restrict__ st,
+                    unsigned long long *__restrict__ pairs)
 {
     const LabT *__restrict__ lab = lab0;
+    int gen = 0;
     if (st) {
         if (st->done) return;
-        lab = ((st->gen + sel_off) & 1) ? lab1 : lab0;
+        gen = st->gen + sel_off;
+        lab = (gen & 1) ? lab1 : lab0;
     }
     extern __shared__ unsigned long long smem_u64[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     unsigned long long *dfx = smem_u64 + (size_t)warp * Np;
     int *cnt = reinterpret_cast<int *>(smem_u64 + (size_t)nw * Np) + warp * Np;
     const float fscale = exp2f((float)fix_bits);
-    // domain floor of Eq. 8 (c_s >= n 2^-40, d_s >= n (n - 1) 2^-40) in units of 2^-b
-    const double clamp_unit = exp2((double)(fix_bits - 40));
     const double2 *__restrict__ ltab = reinterpret_cast<const double2 *>(logtab);
-    const double *__restrict__ k1tab = logtab + 2 * LOG_TAB;
+    const double *__restrict__ ktab = logtab + 2 * LOG_TAB;
 
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
         for (int s = lane; s < N; s += 32) {
@@ -293,28 +290,18 @@ __global__ void __launch_bounds__(256)
             nlist += __popc(m);
             __syncwarp();
         }
-        double part = 0.0;
+        LogProd acc_l;
+        int npairs = 0;
         for (int k = lane; k < nlist; k += 32) {
-            const int n = cnt[k];
-            const long long df = (long long)dfx[k];
-            const long long cf = (((long long)n * n) << fix_bits) - df;
-            double c = (double)cf, d = (double)df;
-            const double cmin = (double)n * clamp_unit;
-            const double dmin = (double)(n * (n - 1)) * clamp_unit;
-            if (!(c >= cmin)) c = cmin;
-            if (!(d >= dmin)) d = dmin;
-            double lg;
-            if (n <= 16) {
-                double pw = c * d;
-                for (int t = 2; t < n; ++t) pw *= d;
-                lg = table_log(pw, ltab);
-            } else {
-                lg = fma((double)(n - 1), table_log(d, ltab), table_log(c, ltab));
-            }
-            part += fma(-0.5, lg, k1tab[n]);
+            logprod_add(acc_l, cnt[k], (long long)dfx[k], fix_bits, ktab);
+            npairs += cnt[k] * (cnt[k] - 1) / 2;
         }
+        if (pairs) {
 #pragma unroll
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            for (int o = 16; o; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+            if (lane == 0) atomicAdd(pairs + gen, (unsigned long long)npairs);
+        }
+        const double part = logprod_finish(acc_l, ltab, nlist);
         if (lane == 0) {
             L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : part;
             if (bad && err) atomicOr(err, 1);
@@ -326,7 +313,8 @@ __global__ void __launch_bounds__(256)
 template <typename LabT>
 int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *acc, int Np,
                     const float *D32, int full_rows, int P, int N, const double *logtab,
-                    double *L, int *err, const DevState *st, cudaStream_t s)
+                    double *L, int *err, const DevState *st, unsigned long long *pairs,
+                    cudaStream_t s)
 {
     // 8 warps (one individual each) unless the per-warp bins of a large N need
     // fewer to fit the 227 KB of shared memory
@@ -337,7 +325,7 @@ int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *
     const int grid = (P + nw - 1) / nw;
     assemble_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, acc, Np, D32,
                                                   full_rows, P, N, logtab, fix_bits_for(N), L,
-                                                  err, st);
+                                                  err, st, pairs);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
@@ -348,10 +336,12 @@ template int launch_pair_plain<int32_t>(const float *, int, const int32_t *const
                                         int, int, float *, const DevState *, cudaStream_t);
 template int launch_assemble<uint16_t>(const uint16_t *const *, int, int, const float *, int,
                                        const float *, int, int, int, const double *, double *,
-                                       int *, const DevState *, cudaStream_t);
+                                       int *, const DevState *, unsigned long long *,
+                                       cudaStream_t);
 template int launch_assemble<int32_t>(const int32_t *const *, int, int, const float *, int,
                                       const float *, int, int, int, const double *, double *,
-                                      int *, const DevState *, cudaStream_t);
+                                      int *, const DevState *, unsigned long long *,
+                                      cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Final re-score of one configuration in FP64 straight from C (Eq. 5, 6, 8),

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgpga.so")
 
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DEGENERATE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6
-FORM_PLAIN, FORM_TENSOR = 0, 1
+FORM_PLAIN, FORM_TENSOR, FORM_GATHER = 0, 1, 2
 SCALING_RANK, SCALING_PROP = 0, 1
 INIT_UNIFORM, INIT_THRESHOLD = 0, 1
 MAX_N, MAX_P = 4096, 16384
@@ -82,7 +82,7 @@ def lib() -> ct.CDLL:
             "ga_reset": (i32, [vp, vp, ct.c_uint64]),
             "ga_step": (i32, [vp, i32, ct.POINTER(i32)]),
             "ga_best": (i32, [vp, vp, vp, ct.POINTER(i32)]),
-            "ga_history": (i32, [vp, vp, vp, vp, i32, ct.POINTER(i32)]),
+            "ga_history": (i32, [vp, vp, vp, vp, vp, i32, ct.POINTER(i32)]),
             "ga_kernel_times": (i32, [vp, vp, i32, ct.POINTER(i32)]),
             "ga_population": (i32, [vp, vp, vp]),
             "gpga_log_selftest": (i32, [vp, i32, vp, vp, vp]),
@@ -221,11 +221,12 @@ class GA:
         if self.params.record:
             lab = np.zeros((cap, self.N), np.int32)
             ts = np.zeros(cap + 1, np.int64)
+            pairs = np.zeros(cap, np.uint64)
             _check(lib().ga_history(self._h, bl.ctypes.data, lab.ctypes.data, ts.ctypes.data,
-                                    cap, ct.byref(n)))
+                                    pairs.ctypes.data, cap, ct.byref(n)))
             k = n.value
-            return dict(best_L=bl[:k], labels=lab[:k], t_ns=ts[:k + 1])
-        _check(lib().ga_history(self._h, bl.ctypes.data, None, None, cap, ct.byref(n)))
+            return dict(best_L=bl[:k], labels=lab[:k], t_ns=ts[:k + 1], pairs=pairs[:k])
+        _check(lib().ga_history(self._h, bl.ctypes.data, None, None, None, cap, ct.byref(n)))
         return dict(best_L=bl[: n.value])
 
     def kernel_times(self):

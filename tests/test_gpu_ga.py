@@ -75,7 +75,7 @@ def test_uniform_init_bit_exact(g, orc):
 
 
 def test_threshold_init_bit_exact(g, orc):
-    for which in ("n100", "small16"):
+    for which in ("n100", "small16", "n500"):
         p = getattr(synth, which)()
         C = orc.pearson(p.R)
         gp = _gparams(g, 257, init=g.INIT_THRESHOLD, tau_lo=0.05, tau_hi=0.6)
@@ -85,14 +85,14 @@ def test_threshold_init_bit_exact(g, orc):
         ga.close()
 
 
-@pytest.mark.parametrize("scaling", [0, 1])
-def test_pipeline_generation_by_generation(g, orc, scaling):
+@pytest.mark.parametrize("scaling,form", [(0, 0), (1, 0), (0, 2), (1, 2)])
+def test_pipeline_generation_by_generation(g, orc, scaling, form):
     """Each device generation equals the oracle's operators applied to the
     device's own population and fitness (bit-exact), and the device fitness
     matches the oracle's likelihood of that population."""
     p = synth.n100()
     C = orc.pearson(p.R)
-    gp = _gparams(g, 1024, E=10, scaling=scaling, max_gens=50, tol=-1.0, record=1)
+    gp = _gparams(g, 1024, E=10, scaling=scaling, max_gens=50, tol=-1.0, record=1, form=form)
     seed = 4242
     ga = g.GA(dev(C), gp, seed=seed)
     op = _oparams(orc, gp, 100)
@@ -135,10 +135,11 @@ def test_termination_and_noop_after_done(g, orc):
     ga.close()
 
 
-def test_recovers_small16(g, orc):
+@pytest.mark.parametrize("form", [0, 2])
+def test_recovers_small16(g, orc, form):
     p = synth.small16()
     C = orc.pearson(p.R)
-    gp = _gparams(g, 64, max_gens=200, tol=-1.0)
+    gp = _gparams(g, 64, max_gens=200, tol=-1.0, form=form)
     ga = g.GA(dev(C), gp, seed=synth.seed_for(1))
     ga.step(200)
     lab, L, gen = ga.best()
@@ -147,13 +148,14 @@ def test_recovers_small16(g, orc):
     ga.close()
 
 
-def test_global_max_n10(g, orc):
+@pytest.mark.parametrize("form", [0, 2])
+def test_global_max_n10(g, orc, form):
     """Small-workload parameters on N=10: the exhaustive maximum in >= 99 of
     100 seeds."""
     p = synth.small10()
     C = orc.pearson(p.R)
     _, Lmax, _ = orc.brute_force(C)
-    gp = _gparams(g, 64, max_gens=200, tol=-1.0)
+    gp = _gparams(g, 64, max_gens=200, tol=-1.0, form=form)
     ga = g.GA(dev(C), gp, seed=1)
     hits = 0
     for k in range(100):

@@ -8,6 +8,8 @@ from gpu_util import assert_L_close, dev
 
 pytestmark = pytest.mark.gpu
 
+FORMS = [0, 2]  # plain, gather
+
 
 @pytest.fixture(scope="module")
 def g():
@@ -34,7 +36,7 @@ def _cases(rng, truth, P):
     }
 
 
-@pytest.mark.parametrize("form", [0])
+@pytest.mark.parametrize("form", FORMS)
 def test_small16(g, orc, form):
     p = synth.small16()
     C = orc.pearson(p.R)
@@ -44,10 +46,10 @@ def test_small16(g, orc, form):
     got = _score(g, pop, C, form)
     ref = orc.loglik_batch(pop, C)
     assert_L_close(got, ref, "small16")
-    assert got[61] == 0.0  # all singletons contribute nothing
+    assert got[61] == 0.0  # all singletons: an empty sum
 
 
-@pytest.mark.parametrize("form", [0])
+@pytest.mark.parametrize("form", FORMS)
 def test_n100_population(g, orc, form):
     p = synth.n100()
     C = orc.pearson(p.R)
@@ -57,7 +59,7 @@ def test_n100_population(g, orc, form):
         assert_L_close(got, orc.loglik_batch(pop, C), f"n100/{name}")
 
 
-@pytest.mark.parametrize("form", [0])
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("N", [2, 3, 31, 33, 63, 64, 65, 127, 129, 200, 1000, 2100])
 def test_ragged_sizes(g, orc, form, N):
     rng = np.random.default_rng(N)
@@ -69,7 +71,7 @@ def test_ragged_sizes(g, orc, form, N):
         assert_L_close(got, orc.loglik_batch(pop, C), f"N={N} P={P}")
 
 
-@pytest.mark.parametrize("form", [0])
+@pytest.mark.parametrize("form", FORMS)
 def test_full_size_n500_p4096(g, orc, form):
     """The benchmark's workload size, in the benchmark's launch shape: every
     individual compared (the oracle needs seconds)."""
@@ -83,20 +85,43 @@ def test_full_size_n500_p4096(g, orc, form):
     print("max |dL|", errs)
 
 
-def test_deterministic_and_relabel_invariant(g, orc):
+@pytest.mark.parametrize("form", FORMS)
+def test_deterministic_and_relabel_invariant(g, orc, form):
     p = synth.n100()
     C = orc.pearson(p.R)
     rng = np.random.default_rng(4)
     pop = synth.perturbed_population(rng, p.truth, 256, 0.1)
-    a = _score(g, pop, C)
-    b = _score(g, pop, C)
+    a = _score(g, pop, C, form)
+    b = _score(g, pop, C, form)
     assert np.array_equal(a, b)
     pi = rng.permutation(100).astype(np.int32)
-    c = _score(g, pi[pop], C)
+    c = _score(g, pi[pop], C, form)
     assert np.all(np.abs(c - a) <= 1e-12 * np.maximum(1, np.abs(a)))
 
 
-def test_invalid_label_is_reported(g, orc):
+def test_forms_agree(g, orc):
+    p = synth.n500()
+    C = orc.pearson(p.R)
+    rng = np.random.default_rng(44)
+    pop = synth.perturbed_population(rng, p.truth, 512, 0.02)
+    a, b = _score(g, pop, C, 0), _score(g, pop, C, 2)
+    assert np.all(np.abs(a - b) <= 1e-4 + 1e-6 * np.abs(a))
+
+
+def test_nonunit_diagonal_counts(g, orc):
+    """A C whose diagonal is not 1 (not a Pearson matrix): the D_ii terms of
+    Eq. 6 must still enter c_s."""
+    rng = np.random.default_rng(45)
+    C = orc.pearson(rng.standard_normal((90, 30)))
+    np.fill_diagonal(C, 0.8)
+    pop = synth.random_labels(rng, 40, 30, K=6)
+    ref = orc.loglik_batch(pop, C)
+    for form in FORMS:
+        assert_L_close(_score(g, pop, C, form), ref, f"diag form {form}")
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_invalid_label_is_reported(g, orc, form):
     p = synth.small16()
     C = orc.pearson(p.R)
     pop = np.tile(p.truth, (4, 1)).astype(np.int32)
@@ -104,7 +129,7 @@ def test_invalid_label_is_reported(g, orc):
     import torch
     L = torch.zeros(4, dtype=torch.float64, device="cuda")
     with pytest.raises(g.GpgaError) as e:
-        g.ga_score(dev(pop, torch.int32), dev(C), L=L)
+        g.ga_score(dev(pop, torch.int32), dev(C), form=form, L=L)
     assert e.value.code == g.ERR_ARG
     torch.cuda.synchronize()
     Lh = L.cpu().numpy()
