@@ -138,66 +138,60 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 }
 
 // ---------------------------------------------------------------------------
-// "Isolate fittest individuals": rank_i = #{j : (L_j, j) fitter than (L_i, i)},
-// counted over all pairs by a grid (slices of j per CTA row, integer atomics,
-// so the ranks are exact and order-independent). perm[rank_i] = i follows in
-// the finalize kernel, which also zeroes rank for the next use.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
-    rank_count_kernel(const double *__restrict__ L, int P, int slice, int *__restrict__ rank,
-                      const DevState *__restrict__ st)
-{
-    if (st && st->done) return;
-    extern __shared__ unsigned long long keys[];
-    const int j0 = blockIdx.y * slice, j1 = min(P, j0 + slice);
-    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) keys[j - j0] = order_key(L[j]);
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    const unsigned long long ki = order_key(L[i]);
-    int cnt = 0;
-    for (int j = j0; j < j1; ++j) {
-        const unsigned long long kj = keys[j - j0];
-        cnt += (kj > ki) | ((kj == ki) & (j < i));
-    }
-    if (cnt) atomicAdd(&rank[i], cnt);
-}
-
-// ---------------------------------------------------------------------------
-// Finalize: perm[rank_i] = i over the grid; the CTA that arrives last (ticket,
-// no waiting) then holds the whole permutation and does the per-generation
-// bookkeeping of Algorithm 1 -- "evaluate state and statistics" (best, mean),
-// the record of the best configuration and the device clock, "determine if
-// termination criteria are met" -- and, for proportional scaling, the weights
-// by rank and their inclusive prefix. Stateful use: g = st->gen + gen_off.
+// "Isolate fittest individuals" and the per-generation bookkeeping, one launch.
+// rank_i = #{j : (L_j, j) fitter than (L_i, i)} is counted over all pairs by
+// a grid (CTA row y takes a slice of j; integer atomics, so the ranks are
+// exact and order-independent). The CTA that arrives last (ticket; nobody
+// waits) then holds every rank: it scatters perm[rank_i] = i, zeroes rank for
+// the next use, and does "evaluate state and statistics" (best, mean), the
+// record of the best configuration and the device clock, "determine if
+// termination criteria are met", and for proportional scaling the weights by
+// rank with their inclusive prefix. Stateful use: g = st->gen + gen_off.
 // ---------------------------------------------------------------------------
 template <typename LabT>
 __global__ void __launch_bounds__(256)
-    finalize_kernel(const double *__restrict__ L, SelectCfg cfg, int *__restrict__ rank,
-                    int32_t *__restrict__ perm, uint64_t *__restrict__ work_prefix,
-                    unsigned *__restrict__ ticket, DevState *st, double *__restrict__ hist,
-                    const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
-                    unsigned long long *__restrict__ ts)
+    select_kernel(const double *__restrict__ L, SelectCfg cfg, int slice, int *__restrict__ rank,
+                  int32_t *__restrict__ perm, uint64_t *__restrict__ work_prefix,
+                  unsigned *__restrict__ ticket, DevState *st, double *__restrict__ hist,
+                  const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
+                  unsigned long long *__restrict__ ts)
 {
     if (st && st->done) return;
     const int P = cfg.P;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P) {
-        perm[rank[i]] = i;
-        rank[i] = 0;
-    }
+    extern __shared__ unsigned long long keys[];
     __shared__ int s_last;
     __shared__ double s_red[8];
     __shared__ uint64_t s_part[256];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    {
+        const int j0 = blockIdx.y * slice, j1 = min(P, j0 + slice);
+        for (int j = j0 + tid; j < j1; j += nt) keys[j - j0] = order_key(L[j]);
+        __syncthreads();
+        const int i = blockIdx.x * nt + tid;
+        if (i < P) {
+            const unsigned long long ki = order_key(L[i]);
+            int cnt = 0;
+            for (int j = j0; j < j1; ++j) {
+                const unsigned long long kj = keys[j - j0];
+                cnt += (kj > ki) | ((kj == ki) & (j < i));
+            }
+            if (cnt) atomicAdd(&rank[i], cnt);
+        }
+    }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) *ticket = 0u;
-    const int bidx = __ldcg(perm);
+    for (int i = tid; i < P; i += nt) {
+        perm[__ldcg(rank + i)] = i;
+        rank[i] = 0;
+    }
+    __threadfence_block();
+    __syncthreads();
+    const int bidx = perm[0];
     if (st) {
         const int g = st->gen + cfg.gen_off;
         double part = 0.0;
@@ -243,18 +237,18 @@ __global__ void __launch_bounds__(256)
     if (isnan(lmax)) lmax = -INFINITY;
     const int chunk = (P + nt - 1) / nt;
     const int lo = tid * chunk, hi = min(P, lo + chunk);
-    uint64_t s = 0;
+    uint64_t sacc = 0;
     for (int r = lo; r < hi; ++r) {
         uint64_t w = 1;
         if (lmax > 0.0) {
-            double x = L[__ldcg(perm + r)];
+            double x = L[perm[r]];
             if (!(x > 0.0)) x = 0.0;
             w = (uint64_t)floor(__dmul_rn(__ddiv_rn(x, lmax), 4294967296.0));
         }
-        s += w;
-        work_prefix[r] = s;
+        sacc += w;
+        work_prefix[r] = sacc;
     }
-    s_part[tid] = s;
+    s_part[tid] = sacc;
     __syncthreads();
     if (tid == 0) {
         uint64_t run = 0;
@@ -274,17 +268,14 @@ int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *per
                   const LabT *const *pop2, LabT *ring, unsigned long long *ts, cudaStream_t s)
 {
     const int P = cfg.P;
-    const int bx = (P + 127) / 128;
+    const int bx = (P + 255) / 256;
     int sy = (2 * 152 + bx - 1) / bx; // about two CTAs per SM
     if (sy < 1) sy = 1;
     int slice = (P + sy - 1) / sy;
     if (slice > 8192) slice = 8192;
     sy = (P + slice - 1) / slice;
-    rank_count_kernel<<<dim3(bx, sy), 128, (size_t)slice * sizeof(unsigned long long), s>>>(
-        L, P, slice, rank, st);
-    GPGA_LAUNCH_CHECK();
-    finalize_kernel<LabT><<<(P + 255) / 256, 256, 0, s>>>(
-        L, cfg, rank, perm, work_prefix, ticket, st, hist, pop2 ? pop2[0] : nullptr,
+    select_kernel<LabT><<<dim3(bx, sy), 256, (size_t)slice * sizeof(unsigned long long), s>>>(
+        L, cfg, slice, rank, perm, work_prefix, ticket, st, hist, pop2 ? pop2[0] : nullptr,
         pop2 ? pop2[1] : nullptr, ring, ts);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
@@ -370,7 +361,8 @@ template int launch_evolve<int32_t>(const int32_t *const *, int32_t *const *, co
 
 int prepare_ga_kernels(int maxsmem)
 {
-    if (int rc = raise_smem(rank_count_kernel, maxsmem)) return rc;
+    if (int rc = raise_smem(select_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(select_kernel<int32_t>, maxsmem)) return rc;
     return GPGA_OK;
 }
 

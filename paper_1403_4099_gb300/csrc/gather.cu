@@ -5,46 +5,38 @@
 // label (stable counting sort), and only same-cluster pairs are visited:
 //   d_s = sum_{i,j in s} D_ij = 2 sum_{a<b} D_{m_a m_b} + sum_a D_{m_a m_a},
 // sum_s n_s (n_s - 1) / 2 gathers of D (FP32, L2-resident) instead of a dense
-// sweep. One warp per individual; everything (labels, histogram, members,
-// per-label fixed-point bins) lives in that warp's slice of shared memory.
-// Pairs of all non-singleton clusters are flattened and dealt to lanes; a lane
-// sums its pairs of one cluster in FP32 and adds the sum, in fixed point, to
-// the cluster's bin with an integer atomic (order-independent: deterministic).
-// Eq. 8 then follows in the one-log product form.
+// sweep. One warp per individual; labels, counts and the sorted members live in
+// that warp's slice of shared memory. A cluster of at most 8 members is summed
+// by one lane in a fixed order; a larger one by the whole warp (fixed pair
+// assignment, exact integer reduction of the fixed-point partials), so the
+// score is deterministic. Eq. 8 then follows in the one-log product form.
 #include <math.h>
 
 #include "gpga_internal.cuh"
 
 namespace gpga {
 
-// per-warp shared-memory slice for Np padded genes
+// per-warp shared-memory slice for Np padded genes (12 Np bytes)
 struct GatherSlice {
-    unsigned long long *dfx; // Np: fixed-point d per label
-    int *start;              // Np + 1: cluster start in mem (then compacted starts)
-    int *fill;               // Np: counts / fill pointers (then compacted sizes)
-    int *cpp;                // Np + 1: exclusive prefix of pair counts, compacted
-    uint16_t *lab;           // Np: labels
-    uint16_t *mem;           // Np: gene indices sorted by label, stable
+    int *cnt;      // Np: label counts, then the compacted clusters (start << 16 | n)
+    int *fill;     // Np: fill pointers (cluster ends after the scatter), then big clusters
+    uint16_t *lab; // Np: labels
+    uint16_t *mem; // Np: gene indices sorted by label, stable
 };
 
-__host__ __device__ inline size_t gather_slice_bytes(int Np)
-{
-    return (size_t)Np * 8 + (size_t)(Np + 4) * 4 * 3 + (size_t)Np * 2 * 2;
-}
+__host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 12; }
 
 __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
 {
     GatherSlice s;
-    s.dfx = reinterpret_cast<unsigned long long *>(base);
-    s.start = reinterpret_cast<int *>(base + (size_t)Np * 8);
-    s.fill = s.start + (Np + 4);
-    s.cpp = s.fill + (Np + 4);
-    s.lab = reinterpret_cast<uint16_t *>(s.cpp + (Np + 4));
+    s.cnt = reinterpret_cast<int *>(base);
+    s.fill = s.cnt + Np;
+    s.lab = reinterpret_cast<uint16_t *>(s.fill + Np);
     s.mem = s.lab + Np;
     return s;
 }
 
-// exclusive warp scan of x (lane order)
+// exclusive warp scan of x (lane order); total = sum over the warp
 __device__ __forceinline__ int warp_excl_scan(int x, int lane, int &total)
 {
     int v = x;
@@ -57,139 +49,137 @@ __device__ __forceinline__ int warp_excl_scan(int x, int lane, int &total)
     return v - x;
 }
 
-// Score one configuration held in sl.lab[0..N) (labels < N). Returns L on all
-// lanes. D32: Np x Np FP32 D = 1 - C; diag: nonzero if some D_ii != 0.
+// clusters up to this size are summed by one lane (at most 28 pairs); larger
+// ones by the whole warp
+constexpr int SMALL_CLUSTER = 8;
+
+// Score one configuration held in sl.lab[0..N) (labels < N, N < 65536).
+// Returns L on all lanes. D32: Np x Np FP32 D = 1 - C; diag: nonzero if some
+// D_ii != 0. pairs_out (optional): += sum_s n_s (n_s - 1) / 2.
 __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
                                     const float *__restrict__ D32, int diag, int fix_bits,
                                     const double2 *__restrict__ ltab,
                                     const double *__restrict__ ktab, int lane,
                                     unsigned long long *pairs_out)
 {
+    const unsigned lt = (1u << lane) - 1u;
     // histogram
-    for (int s = lane; s < N; s += 32) {
-        sl.fill[s] = 0;
-        sl.dfx[s] = 0ull;
-    }
+    for (int s = lane; s < N; s += 32) sl.cnt[s] = 0;
     __syncwarp();
-    for (int i = lane; i < N; i += 32) atomicAdd(&sl.fill[sl.lab[i]], 1);
+    for (int i = lane; i < N; i += 32) atomicAdd(&sl.cnt[sl.lab[i]], 1);
     __syncwarp();
-    // exclusive scan -> start; fill pointers = start
+    // exclusive scan of the counts -> fill (cluster starts)
     {
         const int per = (N + 31) >> 5;
         const int lo = lane * per, hi = min(N, lo + per);
         int sum = 0;
-        for (int s = lo; s < hi; ++s) sum += sl.fill[s];
+        for (int s = lo; s < hi; ++s) sum += sl.cnt[s];
         int total;
         int run = warp_excl_scan(sum, lane, total);
-        __syncwarp();
         for (int s = lo; s < hi; ++s) {
-            const int c = sl.fill[s];
-            sl.start[s] = run;
             sl.fill[s] = run;
-            run += c;
+            run += sl.cnt[s];
         }
-        if (lane == 0) sl.start[N] = N;
     }
     __syncwarp();
-    // stable scatter of gene indices by label, 32 genes at a time in index order
+    // stable scatter of gene indices by label, 32 genes at a time in index order;
+    // afterwards fill[s] is the end of cluster s
     for (int base = 0; base < N; base += 32) {
         const int i = base + lane;
         const unsigned act = __ballot_sync(0xffffffffu, i < N);
         if (i < N) {
             const int s = sl.lab[i];
             const unsigned peers = __match_any_sync(act, s);
-            const int pos = sl.fill[s] + __popc(peers & ((1u << lane) - 1u));
-            sl.mem[pos] = (uint16_t)i;
+            sl.mem[sl.fill[s] + __popc(peers & lt)] = (uint16_t)i;
             __syncwarp(act);
-            if ((peers & ((1u << lane) - 1u)) == 0u) sl.fill[s] += __popc(peers);
+            if ((peers & lt) == 0u) sl.fill[s] += __popc(peers);
         }
         __syncwarp();
     }
-    // diagonal terms D_ii into the bins (zero for a Pearson C)
-    if (diag) {
-        const float fs = exp2f((float)fix_bits);
-        for (int i = lane; i < N; i += 32)
-            atomicAdd(&sl.dfx[sl.lab[i]],
-                      (unsigned long long)__float2ll_rn(D32[(size_t)i * Np + i] * fs));
-    }
-    // compact non-singleton clusters in place: start[c] = cluster start in mem,
-    // fill[c] = size, cpp[c] = pair count (prefix below)
+    // compact the non-singleton clusters in place: cnt[c] = start << 16 | n
     int nlist = 0;
     for (int base = 0; base < N; base += 32) {
         const int s = base + lane;
-        int st = 0, n = 0;
+        int n = 0, st = 0;
         if (s < N) {
-            st = sl.start[s];
-            n = sl.fill[s] - st;
+            n = sl.cnt[s];
+            st = sl.fill[s] - n;
         }
         const unsigned m = __ballot_sync(0xffffffffu, n >= 2);
         __syncwarp();
-        if (n >= 2) {
-            const int c = nlist + __popc(m & ((1u << lane) - 1u));
-            sl.start[c] = st;
-            sl.fill[c] = n;
-        }
+        if (n >= 2) sl.cnt[nlist + __popc(m & lt)] = (st << 16) | n;
         nlist += __popc(m);
         __syncwarp();
     }
-    {
-        const int per = (nlist + 31) >> 5;
-        const int lo = lane * per, hi = min(nlist, lo + per);
-        int sum = 0;
-        for (int c = lo; c < hi; ++c) {
-            const int n = sl.fill[c];
-            sum += n * (n - 1) / 2;
+    // small clusters: one lane each, pairs in fixed order, term in registers;
+    // big clusters: listed in fill[] for the whole warp
+    LogProd acc;
+    int nbig = 0;
+    long long npairs = 0;
+    for (int base = 0; base < nlist; base += 32) {
+        const int c = base + lane;
+        int v = 0, n = 0;
+        if (c < nlist) {
+            v = sl.cnt[c];
+            n = v & 0xffff;
         }
-        int total;
-        int run = warp_excl_scan(sum, lane, total);
-        for (int c = lo; c < hi; ++c) {
-            const int n = sl.fill[c];
-            sl.cpp[c] = run;
-            run += n * (n - 1) / 2;
+        const bool small = n >= 2 && n <= SMALL_CLUSTER;
+        if (small) {
+            const int st = v >> 16;
+            float accf = 0.f;
+            for (int a = 0; a < n - 1; ++a) {
+                const float *row = D32 + (size_t)sl.mem[st + a] * Np;
+                for (int b = a + 1; b < n; ++b) accf += __ldg(row + sl.mem[st + b]);
+            }
+            long long df = fix_of(accf, fix_bits + 1);
+            if (diag)
+                for (int a = 0; a < n; ++a) {
+                    const int i = sl.mem[st + a];
+                    df += fix_of(D32[(size_t)i * Np + i], fix_bits);
+                }
+            logprod_add(acc, n, df, fix_bits, ktab);
+            npairs += n * (n - 1) / 2;
         }
-        if (lane == 0) sl.cpp[nlist] = total;
+        const unsigned bm = __ballot_sync(0xffffffffu, n > SMALL_CLUSTER);
+        if (n > SMALL_CLUSTER) sl.fill[nbig + __popc(bm & lt)] = v;
+        nbig += __popc(bm);
     }
     __syncwarp();
-    // pairs, flattened over clusters and dealt round-robin to lanes
-    const int tot = sl.cpp[nlist];
-    if (pairs_out && lane == 0) atomicAdd(pairs_out, (unsigned long long)tot);
-    const float fs2 = 2.f * exp2f((float)fix_bits);
-    int c = 0, cur = -1;
-    float accf = 0.f;
-    for (int t = lane; t < tot; t += 32) {
-        while (sl.cpp[c + 1] <= t) ++c;
-        if (c != cur) {
-            if (cur >= 0)
-                atomicAdd(&sl.dfx[sl.lab[sl.mem[sl.start[cur]]]],
-                          (unsigned long long)__float2ll_rn(accf * fs2));
-            cur = c;
-            accf = 0.f;
+    for (int q = 0; q < nbig; ++q) {
+        const int v = sl.fill[q];
+        const int st = v >> 16, n = v & 0xffff;
+        const int np = n * (n - 1) / 2;
+        float accf = 0.f;
+        for (int u = lane; u < np; u += 32) {
+            // pair u in column order: u = b (b - 1) / 2 + a, a < b
+            int b = (u < (1 << 21)) ? (int)((1.0f + sqrtf((float)(8 * u + 1))) * 0.5f)
+                                    : (int)((1.0 + sqrt(8.0 * (double)u + 1.0)) * 0.5);
+            if (b * (b - 1) / 2 > u)
+                --b;
+            else if ((b + 1) * b / 2 <= u)
+                ++b;
+            const int a = u - b * (b - 1) / 2;
+            accf += __ldg(D32 + (size_t)sl.mem[st + a] * Np + sl.mem[st + b]);
         }
-        // pair u of the cluster in column order: u = b (b - 1) / 2 + a, a < b
-        const int u = t - sl.cpp[c];
-        int b;
-        if (u < (1 << 21)) {
-            b = (int)((1.0f + sqrtf((float)(8 * u + 1))) * 0.5f);
-        } else {
-            b = (int)((1.0 + sqrt((double)(8.0 * u + 1.0))) * 0.5);
+        long long f = fix_of(accf, fix_bits + 1);
+        if (diag)
+            for (int a = lane; a < n; a += 32) {
+                const int i = sl.mem[st + a];
+                f += fix_of(D32[(size_t)i * Np + i], fix_bits);
+            }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == (q & 31)) {
+            logprod_add(acc, n, f, fix_bits, ktab);
+            npairs += np;
         }
-        if (b * (b - 1) / 2 > u) --b;
-        else if ((b + 1) * b / 2 <= u) ++b;
-        const int a = u - b * (b - 1) / 2;
-        const int st = sl.start[c];
-        const int i = sl.mem[st + a], j = sl.mem[st + b];
-        accf += __ldg(D32 + (size_t)i * Np + j);
     }
-    if (cur >= 0)
-        atomicAdd(&sl.dfx[sl.lab[sl.mem[sl.start[cur]]]],
-                  (unsigned long long)__float2ll_rn(accf * fs2));
-    __syncwarp();
-    LogProd acc_l;
-    for (int k = lane; k < nlist; k += 32) {
-        const int lb = sl.lab[sl.mem[sl.start[k]]];
-        logprod_add(acc_l, sl.fill[k], (long long)sl.dfx[lb], fix_bits, ktab);
+    if (pairs_out) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0) atomicAdd(pairs_out, (unsigned long long)npairs);
     }
-    const double L = logprod_finish(acc_l, ltab, nlist);
+    const double L = logprod_finish(acc, ltab, nlist);
     __syncwarp();
     return L;
 }

@@ -134,6 +134,33 @@ inline size_t logtab_len(int N) { return 2 * LOG_TAB + (size_t)N + 1; }
 // Domain floor of Eq. 8 (degenerate data only): c_s >= n_s 2^-40,
 // d_s >= n_s (n_s - 1) 2^-40, applied in fixed point (at least 1 unit).
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Exact conversions on the integer pipe (the FP64 pipe, which the hardware's
+// float <-> int64 conversions use, is ~1/64 of the FP32 rate here).
+//   fix_of(y, b) = trunc(y 2^b) for float y with |y| 2^b < 2^62
+//   dbl_of(v)    = v as double, rounded toward zero (v > 0, relative error
+//                  below 2^-52)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long fix_of(float y, int bits)
+{
+    const unsigned u = __float_as_uint(y);
+    const int e = (int)((u >> 23) & 0xff);
+    if (e == 0) return 0; // zero (no subnormals in these sums)
+    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+    const int sh = e - 150 + bits; // y 2^b = m 2^(e - 150 + b)
+    long long v = sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0ll);
+    return (u >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ double dbl_of(long long v)
+{
+    const int lz = __clzll(v);
+    const int e = 63 - lz;                                         // leading bit
+    const unsigned long long mant = ((unsigned long long)v << lz) >> 11; // 53 bits, top set
+    return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) |
+                                            (mant & 0x000fffffffffffffull)));
+}
+
 struct LogProd {
     double m = 1.0;  // mantissa in [1, 2)
     long long e = 0; // binary exponent
@@ -157,9 +184,9 @@ __device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int
     if (dmin < 1) dmin = 1;
     if (cf < cmin) cf = cmin;
     if (df < dmin) df = dmin;
-    a.m *= (double)cf;
+    a.m *= dbl_of(cf);
     renorm(a.m, a.e);
-    double md = (double)df;
+    double md = dbl_of(df);
     long long ed = 0;
     renorm(md, ed);
     for (int q = n - 1;;) { // d^(n-1) by binary exponentiation
@@ -270,6 +297,7 @@ int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *per
 
 struct EvolveCfg {
     int P, E, M, N, ldp;
+    double inv_md; // 1 / (M 2^32), for the SUS pointer estimate
     uint64_t thr_pc, thr_pkb, thr_pm;
     uint32_t k0, k1;
     int gen; // stateless generation (when st == nullptr)
@@ -295,35 +323,37 @@ struct EvolveCfg {
 // stream gene pairs. Writes dst (global) and, if given, lab_s (shared).
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
-// SUS pointer x_k = floor((k 2^32 + u) W / (M 2^32)) in exact integer
-// arithmetic: A = (k 2^32 + u) W < 2^127 as two 64-bit words, divided by M with
-// 32-bit long division, then shifted right by 32.
+// SUS pointer x_k = floor((k 2^32 + u) W / (M 2^32)), exact: an FP64 estimate
+// (off by at most a unit or two) corrected against the exact 128-bit numerator
+// A = (k 2^32 + u) W and divisor D = M 2^32 (no integer division).
+// inv_md = 1 / (M 2^32) rounded.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t W, uint32_t M)
+__device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t W, uint32_t M,
+                                                double inv_md)
 {
+    typedef unsigned __int128 u128;
     const uint64_t num = ((uint64_t)k << 32) | u;
-    const uint64_t lo = num * W;
-    const uint64_t hi = __umul64hi(num, W);
-    // 128-bit (hi:lo) / M, limb by limb (32-bit limbs, most significant first)
-    const uint32_t limb[4] = {(uint32_t)(hi >> 32), (uint32_t)hi, (uint32_t)(lo >> 32),
-                              (uint32_t)lo};
-    uint32_t q[4];
-    uint64_t rem = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const uint64_t cur = (rem << 32) | limb[t];
-        q[t] = (uint32_t)(cur / M);
-        rem = cur % M;
+    const u128 A = (u128)num * W;
+    const u128 D = (u128)M << 32;
+    double est = (double)num * (double)W * inv_md;
+    uint64_t x = est > 0.0 ? (uint64_t)est : 0ull;
+    u128 X = (u128)x * D;
+    while (X > A) {
+        --x;
+        X -= D;
     }
-    // quotient >> 32 = limbs q0 q1 q2 (q0 is zero since the pointer is below W)
-    return ((uint64_t)q[1] << 32) | q[2];
+    while (A - X >= D) {
+        ++x;
+        X += D;
+    }
+    return x;
 }
 
 __device__ __forceinline__ int sus_parent(int k, uint32_t u, uint64_t W, int M, int P,
-                                          const uint64_t *__restrict__ prefix,
+                                          double inv_md, const uint64_t *__restrict__ prefix,
                                           const int32_t *__restrict__ perm)
 {
-    const uint64_t x = sus_pointer((uint32_t)k, u, W, (uint32_t)M);
+    const uint64_t x = sus_pointer((uint32_t)k, u, W, (uint32_t)M, inv_md);
     int lo = 0, hi = P - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -348,7 +378,8 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
     if (lane < 2) {
         const uint64_t W = __ldg(prefix + cfg.P - 1);
         const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
-        par = sus_parent(lane == 0 ? k : (k + M / 2) % M, su.x, W, M, cfg.P, prefix, perm);
+        par = sus_parent(lane == 0 ? k : (k + M / 2) % M, su.x, W, M, cfg.P, cfg.inv_md, prefix,
+                         perm);
     }
     const int ia = __shfl_sync(0xffffffffu, par, 0);
     const int ib = __shfl_sync(0xffffffffu, par, 1);

@@ -236,7 +236,6 @@ __global__ void __launch_bounds__(256)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     unsigned long long *dfx = smem_u64 + (size_t)warp * Np;
     int *cnt = reinterpret_cast<int *>(smem_u64 + (size_t)nw * Np) + warp * Np;
-    const float fscale = exp2f((float)fix_bits);
     const double2 *__restrict__ ltab = reinterpret_cast<const double2 *>(logtab);
     const double *__restrict__ ktab = logtab + 2 * LOG_TAB;
 
@@ -258,10 +257,9 @@ __global__ void __launch_bounds__(256)
             const float y = ap[i];
             long long f;
             if (full_rows) {
-                f = __float2ll_rn(y * fscale);
+                f = fix_of(y, fix_bits);
             } else {
-                f = __float2ll_rn((2.f * y) * fscale) +
-                    __float2ll_rn(D32[(size_t)i * Np + i] * fscale);
+                f = fix_of(y, fix_bits + 1) + fix_of(D32[(size_t)i * Np + i], fix_bits);
             }
             atomicAdd(&cnt[s], 1);
             atomicAdd(&dfx[s], (unsigned long long)f);
