@@ -101,6 +101,7 @@ struct gpga_ga {
     double *C64 = nullptr;
     float *D32 = nullptr;
     __nv_bfloat16 *Dhi = nullptr, *Dlo = nullptr;
+    int32_t *Dfix = nullptr;
     double *logtab = nullptr;
     uint16_t *pop[2] = {nullptr, nullptr};
     double *L = nullptr;
@@ -153,6 +154,7 @@ size_t carve(gpga_ga *h, char *base)
     h->D32 = c.take<float>(Np * Np);
     h->Dhi = c.take<__nv_bfloat16>(Np * Np);
     h->Dlo = c.take<__nv_bfloat16>(Np * Np);
+    h->Dfix = c.take<int32_t>(Np * Np);
     h->logtab = c.take<double>(logtab_len(h->N));
     h->pop[0] = c.take<uint16_t>(P * Np);
     h->pop[1] = c.take<uint16_t>(P * Np);
@@ -187,7 +189,7 @@ int enqueue_score(gpga_ga *h, int sel_off, cudaEvent_t *evs = nullptr)
     const int tensor = h->prm.form == GPGA_FORM_TENSOR;
     int rc;
     if (h->prm.form == GPGA_FORM_GATHER) {
-        rc = launch_gather_score<uint16_t>(lab2, h->Np, sel_off, h->P, h->N, h->Np, h->D32,
+        rc = launch_gather_score<uint16_t>(lab2, h->Np, sel_off, h->P, h->N, h->Np, h->Dfix,
                                            h->diag, h->logtab, h->L, h->err, h->st, h->pairs,
                                            h->stream);
         if (!rc) rc = mark(h, evs, 2);
@@ -264,7 +266,7 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs)
     if (h->prm.form == GPGA_FORM_GATHER) {
         // selection, crossover, mutation, replacement and scoring in one kernel
         if (!rc)
-            rc = launch_gather_generation<uint16_t>(pop2, next2, e, h->perm, prefix, h->Np, h->D32,
+            rc = launch_gather_generation<uint16_t>(pop2, next2, e, h->perm, prefix, h->Np, h->Dfix,
                                                     h->diag, h->logtab, h->L, h->st, h->pairs,
                                                     h->stream);
         if (!rc) rc = mark(h, evs, 1);
@@ -293,8 +295,8 @@ int enqueue_start(gpga_ga *h, const double *C)
                                   h->stream));
     int rc = launch_state_init(h->st, h->ts, h->k0, h->k1, h->stream);
     if (rc) return rc;
-    rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->logtab, h->diag,
-                       h->stream);
+    rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->Dfix, h->logtab,
+                       h->diag, h->stream);
     if (rc) return rc;
     rc = rank_prefix_table(h->rank_prefix, h->P, h->stream);
     if (rc) return rc;
@@ -397,9 +399,10 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
     const size_t b_h = (size_t)Np * Np * sizeof(__nv_bfloat16);
     const size_t b_acc = (size_t)P * Np * sizeof(float);
     const size_t b_log = logtab_len(N) * sizeof(double);
+    const size_t b_fix = (size_t)Np * Np * sizeof(int32_t);
     size_t tc_bytes = 0;
     if (form == GPGA_FORM_TENSOR) tc_bytes = tc_scratch_bytes(N, Np, P);
-    const size_t total = b_d + 2 * b_h + b_acc + b_log + tc_bytes + 4096;
+    const size_t total = b_d + 2 * b_h + b_fix + b_acc + b_log + tc_bytes + 4096;
     char *ws = nullptr;
     GPGA_CUDA(cudaMallocAsync((void **)&ws, total, s));
     Carver c(ws);
@@ -407,6 +410,7 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
     __nv_bfloat16 *Dhi = c.take<__nv_bfloat16>((size_t)Np * Np);
     __nv_bfloat16 *Dlo = c.take<__nv_bfloat16>((size_t)Np * Np);
     float *acc = c.take<float>((size_t)P * Np);
+    int32_t *Dfix = c.take<int32_t>((size_t)Np * Np);
     double *logtab = c.take<double>(logtab_len(N));
     int *err = c.take<int>(2); // [0] label error, [1] diagonal flag
     TcWork tc{};
@@ -418,11 +422,11 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
             break;
         }
         rc = launch_prep_d(C, N, N, Np, D32, form == GPGA_FORM_TENSOR ? Dhi : nullptr, Dlo,
-                           logtab, err + 1, s);
+                           form == GPGA_FORM_GATHER ? Dfix : nullptr, logtab, err + 1, s);
         if (rc) break;
         const int32_t *lab2[2] = {labels, labels};
         if (form == GPGA_FORM_GATHER) {
-            rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, D32, err + 1, logtab, L, err,
+            rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, Dfix, err + 1, logtab, L, err,
                                               nullptr, nullptr, s);
         } else if (form == GPGA_FORM_TENSOR) {
             rc = tc_score<int32_t>(&tc, Dhi, Dlo, Np, lab2, ld, 0, P, N, acc, nullptr, s);

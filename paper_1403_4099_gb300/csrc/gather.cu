@@ -4,12 +4,13 @@
 // Work per configuration is what Eq. 6 needs, not N^2: genes are sorted by
 // label (stable counting sort), and only same-cluster pairs are visited:
 //   d_s = sum_{i,j in s} D_ij = 2 sum_{a<b} D_{m_a m_b} + sum_a D_{m_a m_a},
-// sum_s n_s (n_s - 1) / 2 gathers of D (FP32, L2-resident) instead of a dense
-// sweep. One warp per individual; labels, counts and the sorted members live in
-// that warp's slice of shared memory. A cluster of at most 8 members is summed
-// by one lane in a fixed order; a larger one by the whole warp (fixed pair
-// assignment, exact integer reduction of the fixed-point partials), so the
-// score is deterministic. Eq. 8 then follows in the one-log product form.
+// sum_s n_s (n_s - 1) / 2 gathers of D (L2-resident) instead of a dense
+// sweep. D is read as int32 fixed point (2^-30), so every cluster sum is an
+// exact integer sum: independent of the order of the members, which are
+// therefore scattered with plain atomics, and deterministic. One warp per
+// individual; labels, counts and members live in that warp's slice of shared
+// memory. A cluster of at most 8 members is summed by one lane, a larger one by
+// the whole warp. Eq. 8 then follows in the one-log product form.
 #include <math.h>
 
 #include "gpga_internal.cuh"
@@ -21,7 +22,7 @@ struct GatherSlice {
     int *cnt;      // Np: label counts, then the compacted clusters (start << 16 | n)
     int *fill;     // Np: fill pointers (cluster ends after the scatter), then big clusters
     uint16_t *lab; // Np: labels
-    uint16_t *mem; // Np: gene indices sorted by label, stable
+    uint16_t *mem; // Np: gene indices grouped by label
 };
 
 __host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 12; }
@@ -36,30 +37,18 @@ __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
     return s;
 }
 
-// exclusive warp scan of x (lane order); total = sum over the warp
-__device__ __forceinline__ int warp_excl_scan(int x, int lane, int &total)
-{
-    int v = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    total = __shfl_sync(0xffffffffu, v, 31);
-    return v - x;
-}
-
 // clusters up to this size are summed by one lane (at most 28 pairs); larger
 // ones by the whole warp
 constexpr int SMALL_CLUSTER = 8;
 
 // Score one configuration held in sl.lab[0..N) (labels < N, N < 65536).
-// Returns L on all lanes. D32: Np x Np FP32 D = 1 - C; diag: nonzero if some
-// D_ii != 0. pairs_out (optional): += sum_s n_s (n_s - 1) / 2.
+// Returns L on all lanes. Dfix: Np x Np int32, D = 1 - C in fixed point
+// 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. pairs_out (optional):
+// += sum_s n_s (n_s - 1) / 2.
 __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
-                                    const float *__restrict__ D32, int diag, int fix_bits,
+                                    const int32_t *__restrict__ Dfix, int diag,
                                     const double2 *__restrict__ ltab,
-                                    const double *__restrict__ ktab, int lane,
+                                    const long long *__restrict__ kfix, int lane,
                                     unsigned long long *pairs_out)
 {
     const unsigned lt = (1u << lane) - 1u;
@@ -68,34 +57,25 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
     __syncwarp();
     for (int i = lane; i < N; i += 32) atomicAdd(&sl.cnt[sl.lab[i]], 1);
     __syncwarp();
-    // exclusive scan of the counts -> fill (cluster starts)
-    {
-        const int per = (N + 31) >> 5;
-        const int lo = lane * per, hi = min(N, lo + per);
-        int sum = 0;
-        for (int s = lo; s < hi; ++s) sum += sl.cnt[s];
-        int total;
-        int run = warp_excl_scan(sum, lane, total);
-        for (int s = lo; s < hi; ++s) {
-            sl.fill[s] = run;
-            run += sl.cnt[s];
+    // exclusive scan of the counts -> fill (cluster starts), 32 labels at a time
+    int carry = 0;
+    for (int base = 0; base < N; base += 32) {
+        const int s = base + lane;
+        const int c = s < N ? sl.cnt[s] : 0;
+        int v = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
         }
+        if (s < N) sl.fill[s] = carry + v - c;
+        carry += __shfl_sync(0xffffffffu, v, 31);
     }
     __syncwarp();
-    // stable scatter of gene indices by label, 32 genes at a time in index order;
-    // afterwards fill[s] is the end of cluster s
-    for (int base = 0; base < N; base += 32) {
-        const int i = base + lane;
-        const unsigned act = __ballot_sync(0xffffffffu, i < N);
-        if (i < N) {
-            const int s = sl.lab[i];
-            const unsigned peers = __match_any_sync(act, s);
-            sl.mem[sl.fill[s] + __popc(peers & lt)] = (uint16_t)i;
-            __syncwarp(act);
-            if ((peers & lt) == 0u) sl.fill[s] += __popc(peers);
-        }
-        __syncwarp();
-    }
+    // scatter gene indices by label (order inside a cluster is irrelevant: the
+    // pair sums below are exact integer sums); fill[s] ends at cluster s's end
+    for (int i = lane; i < N; i += 32) sl.mem[atomicAdd(&sl.fill[sl.lab[i]], 1)] = (uint16_t)i;
+    __syncwarp();
     // compact the non-singleton clusters in place: cnt[c] = start << 16 | n
     int nlist = 0;
     for (int base = 0; base < N; base += 32) {
@@ -111,8 +91,8 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         nlist += __popc(m);
         __syncwarp();
     }
-    // small clusters: one lane each, pairs in fixed order, term in registers;
-    // big clusters: listed in fill[] for the whole warp
+    // small clusters: one lane each, term in registers; big clusters: listed in
+    // fill[] for the whole warp. d_s = 2 sum_{a<b} Dfix + sum_a Dfix_aa.
     LogProd acc;
     int nbig = 0;
     long long npairs = 0;
@@ -123,21 +103,20 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
             v = sl.cnt[c];
             n = v & 0xffff;
         }
-        const bool small = n >= 2 && n <= SMALL_CLUSTER;
-        if (small) {
+        if (n >= 2 && n <= SMALL_CLUSTER) {
             const int st = v >> 16;
-            float accf = 0.f;
+            long long sum = 0;
             for (int a = 0; a < n - 1; ++a) {
-                const float *row = D32 + (size_t)sl.mem[st + a] * Np;
-                for (int b = a + 1; b < n; ++b) accf += __ldg(row + sl.mem[st + b]);
+                const int32_t *row = Dfix + (size_t)sl.mem[st + a] * Np;
+                for (int b = a + 1; b < n; ++b) sum += __ldg(row + sl.mem[st + b]);
             }
-            long long df = fix_of(accf, fix_bits + 1);
+            sum *= 2;
             if (diag)
                 for (int a = 0; a < n; ++a) {
                     const int i = sl.mem[st + a];
-                    df += fix_of(D32[(size_t)i * Np + i], fix_bits);
+                    sum += Dfix[(size_t)i * Np + i];
                 }
-            logprod_add(acc, n, df, fix_bits, ktab);
+            logprod_add(acc, n, sum, DFIX_BITS, kfix);
             npairs += n * (n - 1) / 2;
         }
         const unsigned bm = __ballot_sync(0xffffffffu, n > SMALL_CLUSTER);
@@ -148,30 +127,23 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
     for (int q = 0; q < nbig; ++q) {
         const int v = sl.fill[q];
         const int st = v >> 16, n = v & 0xffff;
-        const int np = n * (n - 1) / 2;
-        float accf = 0.f;
-        for (int u = lane; u < np; u += 32) {
-            // pair u in column order: u = b (b - 1) / 2 + a, a < b
-            int b = (u < (1 << 21)) ? (int)((1.0f + sqrtf((float)(8 * u + 1))) * 0.5f)
-                                    : (int)((1.0 + sqrt(8.0 * (double)u + 1.0)) * 0.5);
-            if (b * (b - 1) / 2 > u)
-                --b;
-            else if ((b + 1) * b / 2 <= u)
-                ++b;
-            const int a = u - b * (b - 1) / 2;
-            accf += __ldg(D32 + (size_t)sl.mem[st + a] * Np + sl.mem[st + b]);
+        long long sum = 0;
+        // rows a over lanes, each lane summing D[m_a][m_b] for b > a
+        for (int a = lane; a < n - 1; a += 32) {
+            const int32_t *row = Dfix + (size_t)sl.mem[st + a] * Np;
+            for (int b = a + 1; b < n; ++b) sum += __ldg(row + sl.mem[st + b]);
         }
-        long long f = fix_of(accf, fix_bits + 1);
+        sum *= 2;
         if (diag)
             for (int a = lane; a < n; a += 32) {
                 const int i = sl.mem[st + a];
-                f += fix_of(D32[(size_t)i * Np + i], fix_bits);
+                sum += Dfix[(size_t)i * Np + i];
             }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == (q & 31)) {
-            logprod_add(acc, n, f, fix_bits, ktab);
-            npairs += np;
+            logprod_add(acc, n, sum, DFIX_BITS, kfix);
+            npairs += n * (n - 1) / 2;
         }
     }
     if (pairs_out) {
@@ -191,8 +163,8 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
 template <typename LabT>
 __global__ void __launch_bounds__(256)
     gather_score_kernel(const LabT *lab0, const LabT *lab1, int ldl, int sel_off, int P, int N,
-                        int Np, const float *__restrict__ D32, const int *__restrict__ diag_flag,
-                        const double *__restrict__ logtab, int fix_bits, double *__restrict__ L,
+                        int Np, const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
+                        const double *__restrict__ logtab, double *__restrict__ L,
                         int *__restrict__ err, const DevState *__restrict__ st,
                         unsigned long long *__restrict__ pairs)
 {
@@ -208,7 +180,7 @@ __global__ void __launch_bounds__(256)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
     const double2 *ltab = reinterpret_cast<const double2 *>(logtab);
-    const double *ktab = logtab + 2 * LOG_TAB;
+    const long long *ktab = kfix_of(logtab);
     const int diag = *diag_flag;
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
         bool bad = false;
@@ -221,7 +193,7 @@ __global__ void __launch_bounds__(256)
         }
         bad = __any_sync(0xffffffffu, bad);
         __syncwarp();
-        const double v = gather_score_warp(sl, N, Np, D32, diag, fix_bits, ltab, ktab, lane, pairs_g);
+        const double v = gather_score_warp(sl, N, Np, Dfix, diag, ltab, ktab, lane, pairs_g);
         if (lane == 0) {
             L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v;
             if (bad && err) atomicOr(err, 1);
@@ -239,8 +211,8 @@ __global__ void __launch_bounds__(256)
     gather_generation_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1,
                              EvolveCfg cfg, const int32_t *__restrict__ perm,
                              const uint64_t *__restrict__ prefix, int Np,
-                             const float *__restrict__ D32, const int *__restrict__ diag_flag,
-                             const double *__restrict__ logtab, int fix_bits,
+                             const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
+                             const double *__restrict__ logtab,
                              double *__restrict__ L, const DevState *__restrict__ st,
                              unsigned long long *__restrict__ pairs)
 {
@@ -269,9 +241,9 @@ __global__ void __launch_bounds__(256)
                           lane);
     }
     __syncwarp();
-    const double v = gather_score_warp(sl, N, Np, D32, *diag_flag, fix_bits,
-                                       reinterpret_cast<const double2 *>(logtab),
-                                       logtab + 2 * LOG_TAB, lane, pairs ? pairs + g + 1 : nullptr);
+    const double v = gather_score_warp(sl, N, Np, Dfix, *diag_flag,
+                                       reinterpret_cast<const double2 *>(logtab), kfix_of(logtab),
+                                       lane, pairs ? pairs + g + 1 : nullptr);
     if (lane == 0) L[slot] = v;
 }
 
@@ -285,7 +257,7 @@ static int warps_for(int Np)
 
 template <typename LabT>
 int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, int N, int Np,
-                        const float *D32, const int *diag_flag, const double *logtab,
+                        const int32_t *Dfix, const int *diag_flag, const double *logtab,
                         double *L, int *err, const DevState *st, unsigned long long *pairs,
                         cudaStream_t s)
 {
@@ -293,8 +265,8 @@ int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, in
     const size_t smem = nw * gather_slice_bytes(Np);
     const int grid = (P + nw - 1) / nw;
     gather_score_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, P, N,
-                                                          Np, D32, diag_flag, logtab,
-                                                          fix_bits_for(N), L, err, st, pairs);
+                                                          Np, Dfix, diag_flag, logtab, L, err,
+                                                          st, pairs);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
@@ -302,7 +274,7 @@ int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, in
 template <typename LabT>
 int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
                              const int32_t *perm, const uint64_t *prefix, int Np,
-                             const float *D32, const int *diag_flag, const double *logtab,
+                             const int32_t *Dfix, const int *diag_flag, const double *logtab,
                              double *L, const DevState *st, unsigned long long *pairs,
                              cudaStream_t s)
 {
@@ -310,23 +282,23 @@ int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const 
     const size_t smem = nw * gather_slice_bytes(Np);
     const int grid = (cfg.P + nw - 1) / nw;
     gather_generation_kernel<LabT><<<grid, 32 * nw, smem, s>>>(
-        pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, D32, diag_flag, logtab,
-        fix_bits_for(cfg.N), L, st, pairs);
+        pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, Dfix, diag_flag, logtab, L,
+        st, pairs);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
 
 template int launch_gather_score<uint16_t>(const uint16_t *const *, int, int, int, int, int,
-                                           const float *, const int *, const double *, double *,
+                                           const int32_t *, const int *, const double *, double *,
                                            int *, const DevState *, unsigned long long *,
                                            cudaStream_t);
 template int launch_gather_score<int32_t>(const int32_t *const *, int, int, int, int, int,
-                                          const float *, const int *, const double *, double *,
+                                          const int32_t *, const int *, const double *, double *,
                                           int *, const DevState *, unsigned long long *,
                                           cudaStream_t);
 template int launch_gather_generation<uint16_t>(const uint16_t *const *, uint16_t *const *,
                                                 const EvolveCfg &, const int32_t *,
-                                                const uint64_t *, int, const float *,
+                                                const uint64_t *, int, const int32_t *,
                                                 const int *, const double *, double *,
                                                 const DevState *, unsigned long long *,
                                                 cudaStream_t);

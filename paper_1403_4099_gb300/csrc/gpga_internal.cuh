@@ -119,9 +119,14 @@ __device__ __forceinline__ double table_log(double x, const double2 *__restrict_
     return fma((double)e, 0.6931471805599453, fma(r, q, t.y));
 }
 
-// layout of the per-run log table (doubles): LOG_TAB pairs (inv_k, -log inv_k),
-// then K[n] = 1/2 (log n + (n - 1) log(n (n - 1))), n = 0..N
+// layout of the per-run log table (8-byte slots): LOG_TAB pairs
+// (inv_k, -log inv_k) as doubles, then K[n] = 1/2 (log n + (n - 1) log(n (n - 1)))
+// for n = 0..N as int64 fixed point 2^-44 (kfix_of)
 inline size_t logtab_len(int N) { return 2 * LOG_TAB + (size_t)N + 1; }
+__host__ __device__ inline const long long *kfix_of(const double *logtab)
+{
+    return reinterpret_cast<const long long *>(logtab + 2 * LOG_TAB);
+}
 
 // ---------------------------------------------------------------------------
 // Eq. 8 of one configuration from its non-singleton clusters, with one log:
@@ -161,21 +166,45 @@ __device__ __forceinline__ double dbl_of(long long v)
                                             (mant & 0x000fffffffffffffull)));
 }
 
+// Running product as an integer mantissa m in [2^62, 2^63) (value m 2^-62,
+// in [1, 2)) with a binary exponent e; products are 64 x 64 -> 128-bit integer
+// multiplies truncated back to 63 bits (relative error < 2^-62 each), so the
+// FP64 pipe is not used per cluster. k: sum of K[n_s] in fixed point 2^-44
+// (exact integer adds).
+constexpr int KFIX_BITS = 44;
+// fixed-point D of the gather form: int32 D 2^30 (D = 1 - C in [-2, 2))
+constexpr int DFIX_BITS = 30;
+
 struct LogProd {
-    double m = 1.0;  // mantissa in [1, 2)
-    long long e = 0; // binary exponent
-    double k = 0.0;  // sum of K[n_s]
+    unsigned long long m = 1ull << 62;
+    long long e = 0;
+    long long k = 0;
 };
 
-__device__ __forceinline__ void renorm(double &m, long long &e)
+// (mantissa, exponent) of an integer v > 0
+__device__ __forceinline__ void mant_of(long long v, unsigned long long &m, long long &e)
 {
-    const long long b = __double_as_longlong(m);
-    e += ((b >> 52) & 0x7ff) - 1023;
-    m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+    const int lz = __clzll(v); // >= 1
+    m = (unsigned long long)v << (lz - 1);
+    e = 63 - lz;
+}
+
+// m 2^-62 <- (m 2^-62)(x 2^-62), exponent carried in e
+__device__ __forceinline__ void mant_mul(unsigned long long &m, long long &e, unsigned long long x,
+                                         long long ex)
+{
+    const unsigned long long lo = m * x, hi = __umul64hi(m, x); // m x in [2^124, 2^126)
+    if (hi >> 61) {
+        m = (hi << 1) | (lo >> 63);
+        e += ex + 1;
+    } else {
+        m = (hi << 2) | (lo >> 62);
+        e += ex;
+    }
 }
 
 __device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int fix_bits,
-                                            const double *__restrict__ ktab)
+                                            const long long *__restrict__ kfix)
 {
     long long cf = (((long long)n * n) << fix_bits) - df;
     const int sh = 40 - fix_bits; // fix_bits <= 40
@@ -184,44 +213,42 @@ __device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int
     if (dmin < 1) dmin = 1;
     if (cf < cmin) cf = cmin;
     if (df < dmin) df = dmin;
-    a.m *= dbl_of(cf);
-    renorm(a.m, a.e);
-    double md = dbl_of(df);
-    long long ed = 0;
-    renorm(md, ed);
+    unsigned long long x;
+    long long ex;
+    mant_of(cf, x, ex);
+    mant_mul(a.m, a.e, x, ex);
+    unsigned long long md;
+    long long ed;
+    mant_of(df, md, ed);
     for (int q = n - 1;;) { // d^(n-1) by binary exponentiation
-        if (q & 1) {
-            a.m *= md;
-            a.e += ed;
-            renorm(a.m, a.e);
-        }
+        if (q & 1) mant_mul(a.m, a.e, md, ed);
         q >>= 1;
         if (!q) break;
-        md *= md;
-        ed *= 2;
-        renorm(md, ed);
+        mant_mul(md, ed, md, ed);
     }
     a.e -= (long long)fix_bits * n; // c and the n - 1 factors d each carried 2^b
-    a.k += ktab[n];
+    a.k += kfix[n];
 }
 
 // combine the lanes' partial products (fixed xor butterfly: every lane ends
-// with the same value) and return L
+// with the same value) and return L = k 2^-44 - 1/2 (e ln 2 + log(m 2^-62))
 __device__ __forceinline__ double logprod_finish(LogProd a, const double2 *__restrict__ ltab,
                                                  int nclusters)
 {
     if (nclusters == 0) return 0.0; // all singletons: Eq. 8 is an empty sum
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        const double m2 = __shfl_xor_sync(0xffffffffu, a.m, o);
+        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, a.m, o);
         const long long e2 = __shfl_xor_sync(0xffffffffu, a.e, o);
-        const double k2 = __shfl_xor_sync(0xffffffffu, a.k, o);
-        a.m *= m2;
-        a.e += e2;
-        renorm(a.m, a.e);
+        const long long k2 = __shfl_xor_sync(0xffffffffu, a.k, o);
+        mant_mul(a.m, a.e, m2, e2);
         a.k += k2;
     }
-    return fma(-0.5, fma((double)a.e, 0.6931471805599453, table_log(a.m, ltab)), a.k);
+    // m 2^-62 as a double in [1, 2) (truncated to 52 fraction bits)
+    const double md = __longlong_as_double((long long)(0x3ff0000000000000ull |
+                                                       ((a.m >> 10) & 0x000fffffffffffffull)));
+    const double kd = dbl_of(a.k) * 5.684341886080802e-14; // 2^-44
+    return fma(-0.5, fma((double)a.e, 0.6931471805599453, table_log(md, ltab)), kd);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,7 +257,8 @@ __device__ __forceinline__ double logprod_finish(LogProd a, const double2 *__res
 // D forms and log tables; *diag_flag (zeroed by the caller) becomes nonzero if
 // some D_ii != 0
 int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,
-                  __nv_bfloat16 *Dlo, double *logtab, int *diag_flag, cudaStream_t s);
+                  __nv_bfloat16 *Dlo, int32_t *Dfix, double *logtab, int *diag_flag,
+                  cudaStream_t s);
 
 template <typename LabT>
 int launch_pair_plain(const float *D32, int Np, const LabT *const *lab2, int ldl, int sel_off,
@@ -437,13 +465,13 @@ int launch_evolve(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &
 // gather form (gather.cu)
 template <typename LabT>
 int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, int N, int Np,
-                        const float *D32, const int *diag_flag, const double *logtab,
+                        const int32_t *Dfix, const int *diag_flag, const double *logtab,
                         double *L, int *err, const DevState *st, unsigned long long *pairs,
                         cudaStream_t s);
 template <typename LabT>
 int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
                              const int32_t *perm, const uint64_t *prefix, int Np,
-                             const float *D32, const int *diag_flag, const double *logtab,
+                             const int32_t *Dfix, const int *diag_flag, const double *logtab,
                              double *L, const DevState *st, unsigned long long *pairs,
                              cudaStream_t s);
 

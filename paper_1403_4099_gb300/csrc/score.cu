@@ -34,12 +34,12 @@ __device__ __forceinline__ void log_tab_entry(int k, double *out)
 
 // ---------------------------------------------------------------------------
 // D forms: D32 = fp32(1 - (C + C^T)/2), Dhi = bf16(D), Dlo = bf16(D - Dhi),
-// all Np x Np, zero outside N x N; logtab[k] = log(k) for k = 1..N.
+// Dfix = int32(D 2^30), all Np x Np, zero outside N x N; and the log tables.
 // ---------------------------------------------------------------------------
 __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int Np,
                               float *__restrict__ D32, __nv_bfloat16 *__restrict__ Dhi,
-                              __nv_bfloat16 *__restrict__ Dlo, double *__restrict__ logtab,
-                              int *__restrict__ diag_flag)
+                              __nv_bfloat16 *__restrict__ Dlo, int32_t *__restrict__ Dfix,
+                              double *__restrict__ logtab, int *__restrict__ diag_flag)
 {
     const size_t total = (size_t)Np * Np;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -53,6 +53,13 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
         const float df = (float)d;
         D32[idx] = df;
         if (diag_flag && i == j && df != 0.f) *diag_flag = 1;
+        if (Dfix) {
+            // D 2^30 rounded, saturated to the int32 range (D in [-2, 2))
+            double v = rint(d * 1073741824.0);
+            if (v > 2147483647.0) v = 2147483647.0;
+            if (v < -2147483648.0) v = -2147483648.0;
+            Dfix[idx] = (int32_t)v;
+        }
         if (Dhi) {
             const __nv_bfloat16 hi = __double2bfloat16(d);
             const double rem = d - (double)__bfloat162float(hi);
@@ -61,28 +68,30 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
         }
     }
     if (logtab) {
-        // log table of table_log(), then the per-size constant of the assembly:
-        // K[n] = 1/2 (log n + (n - 1) log(n (n - 1)))
+        // log table of table_log(), then the per-size constant of the assembly,
+        // K[n] = 1/2 (log n + (n - 1) log(n (n - 1))), in fixed point 2^-44
         const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
         for (int k = tid; k < LOG_TAB; k += nt) log_tab_entry(k, logtab + 2 * k);
+        long long *kfix = reinterpret_cast<long long *>(logtab + 2 * LOG_TAB);
         for (int n = tid; n <= N; n += nt) {
             double v = 0.0;
             if (n >= 2) {
                 const double dn = (double)n;
                 v = 0.5 * (log(dn) + (dn - 1.0) * (log(dn) + log(dn - 1.0)));
             }
-            logtab[2 * LOG_TAB + n] = v;
+            kfix[n] = __double2ll_rn(v * 17592186044416.0); // 2^44
         }
     }
 }
 
 int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,
-                  __nv_bfloat16 *Dlo, double *logtab, int *diag_flag, cudaStream_t s)
+                  __nv_bfloat16 *Dlo, int32_t *Dfix, double *logtab, int *diag_flag,
+                  cudaStream_t s)
 {
     const size_t total = (size_t)Np * Np;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, logtab, diag_flag);
+    prep_d_kernel<<<blocks, 256, 0, s>>>(C, N, ldc, Np, D32, Dhi, Dlo, Dfix, logtab, diag_flag);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(256)
     unsigned long long *dfx = smem_u64 + (size_t)warp * Np;
     int *cnt = reinterpret_cast<int *>(smem_u64 + (size_t)nw * Np) + warp * Np;
     const double2 *__restrict__ ltab = reinterpret_cast<const double2 *>(logtab);
-    const double *__restrict__ ktab = logtab + 2 * LOG_TAB;
+    const long long *__restrict__ ktab = kfix_of(logtab);
 
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
         for (int s = lane; s < N; s += 32) {
