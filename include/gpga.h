@@ -219,8 +219,9 @@ GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
 
 /*
  * gpga_log_selftest -- diagnostic with no counterpart in the paper: evaluates
- * the library's table-driven FP64 logarithm (used for the Eq. 8 log terms) and
- * CUDA's log on the same n inputs. x: device, n positive normal doubles;
+ * the library's table-driven fixed-point logarithm (Q62 mantissa log plus
+ * e ln 2, the kernel of the Eq. 8 assembly) and CUDA's log on the same n
+ * inputs. x: device, n positive normal doubles;
  * y_table, y_cuda: device, n doubles (written). Asynchronous.
  */
 GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *y_cuda,

@@ -139,18 +139,23 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 
 // ---------------------------------------------------------------------------
 // "Isolate fittest individuals" and the per-generation bookkeeping, one launch.
-// rank_i = #{j : (L_j, j) fitter than (L_i, i)} is counted over all pairs by
-// a grid (CTA row y takes a slice of j; integer atomics, so the ranks are
-// exact and order-independent). The CTA that arrives last (ticket; nobody
-// waits) then holds every rank: it scatters perm[rank_i] = i, zeroes rank for
-// the next use, and does "evaluate state and statistics" (best, mean), the
-// record of the best configuration and the device clock, "determine if
-// termination criteria are met", and for proportional scaling the weights by
-// rank with their inclusive prefix. Stateful use: g = st->gen + gen_off.
+// rank_i = #{j : (L_j, j) fitter than (L_i, i)} (key descending, index
+// ascending; NaN as -inf). CTA (x, y) sorts the 256 keys of chunk y in shared
+// memory (bitonic) and counts, for each key i of chunk x, the fitter keys of
+// chunk y by binary search; integer atomics sum the counts, so the ranks are
+// exact and order-independent (P^2/256 log 256 comparisons instead of P^2).
+// The CTA that arrives last (ticket; nobody waits) then holds every rank: it
+// scatters perm[rank_i] = i, zeroes rank for the next use, and does "evaluate
+// state and statistics" (best, mean), the record of the best configuration
+// and the device clock, "determine if termination criteria are met", and for
+// proportional scaling the weights by rank with their inclusive prefix.
+// Stateful use: g = st->gen + gen_off.
 // ---------------------------------------------------------------------------
+constexpr int RANK_CHUNK = 256;
+
 template <typename LabT>
-__global__ void __launch_bounds__(256)
-    select_kernel(const double *__restrict__ L, SelectCfg cfg, int slice, int *__restrict__ rank,
+__global__ void __launch_bounds__(RANK_CHUNK)
+    select_kernel(const double *__restrict__ L, SelectCfg cfg, int *__restrict__ rank,
                   int32_t *__restrict__ perm, uint64_t *__restrict__ work_prefix,
                   unsigned *__restrict__ ticket, DevState *st, double *__restrict__ hist,
                   const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
@@ -158,24 +163,47 @@ __global__ void __launch_bounds__(256)
 {
     if (st && st->done) return;
     const int P = cfg.P;
-    extern __shared__ unsigned long long keys[];
+    __shared__ unsigned long long sk[RANK_CHUNK];
+    __shared__ int si[RANK_CHUNK];
     __shared__ int s_last;
-    __shared__ double s_red[8];
-    __shared__ uint64_t s_part[256];
+    __shared__ double s_red[RANK_CHUNK / 32];
+    __shared__ uint64_t s_part[RANK_CHUNK];
     const int tid = threadIdx.x, nt = blockDim.x;
     {
-        const int j0 = blockIdx.y * slice, j1 = min(P, j0 + slice);
-        for (int j = j0 + tid; j < j1; j += nt) keys[j - j0] = order_key(L[j]);
+        const int jy = blockIdx.y * RANK_CHUNK + tid;
+        sk[tid] = jy < P ? order_key(L[jy]) : 0ull; // padding below every real key
+        si[tid] = jy < P ? jy : 0x7fffffff;
         __syncthreads();
-        const int i = blockIdx.x * nt + tid;
+        for (int k = 2; k <= RANK_CHUNK; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                if (tid < RANK_CHUNK / 2) {
+                    const int i = ((tid & ~(j - 1)) << 1) | (tid & (j - 1));
+                    const int l = i + j;
+                    const unsigned long long ki = sk[i], kl = sk[l];
+                    const int ii = si[i], il = si[l];
+                    const bool up = (i & k) == 0;
+                    if (up ? fitter(kl, il, ki, ii) : fitter(ki, ii, kl, il)) {
+                        sk[i] = kl;
+                        sk[l] = ki;
+                        si[i] = il;
+                        si[l] = ii;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const int i = blockIdx.x * RANK_CHUNK + tid;
         if (i < P) {
             const unsigned long long ki = order_key(L[i]);
-            int cnt = 0;
-            for (int j = j0; j < j1; ++j) {
-                const unsigned long long kj = keys[j - j0];
-                cnt += (kj > ki) | ((kj == ki) & (j < i));
+            int lo = 0, hi = RANK_CHUNK; // fitter keys form a prefix of the sorted chunk
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (fitter(sk[mid], si[mid], ki, i))
+                    lo = mid + 1;
+                else
+                    hi = mid;
             }
-            if (cnt) atomicAdd(&rank[i], cnt);
+            if (lo) atomicAdd(&rank[i], lo);
         }
     }
     __threadfence();
@@ -267,15 +295,9 @@ int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *per
                   uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,
                   const LabT *const *pop2, LabT *ring, unsigned long long *ts, cudaStream_t s)
 {
-    const int P = cfg.P;
-    const int bx = (P + 255) / 256;
-    int sy = (2 * 152 + bx - 1) / bx; // about two CTAs per SM
-    if (sy < 1) sy = 1;
-    int slice = (P + sy - 1) / sy;
-    if (slice > 8192) slice = 8192;
-    sy = (P + slice - 1) / slice;
-    select_kernel<LabT><<<dim3(bx, sy), 256, (size_t)slice * sizeof(unsigned long long), s>>>(
-        L, cfg, slice, rank, perm, work_prefix, ticket, st, hist, pop2 ? pop2[0] : nullptr,
+    const int nc = (cfg.P + RANK_CHUNK - 1) / RANK_CHUNK;
+    select_kernel<LabT><<<dim3(nc, nc), RANK_CHUNK, 0, s>>>(
+        L, cfg, rank, perm, work_prefix, ticket, st, hist, pop2 ? pop2[0] : nullptr,
         pop2 ? pop2[1] : nullptr, ring, ts);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
@@ -361,8 +383,7 @@ template int launch_evolve<int32_t>(const int32_t *const *, int32_t *const *, co
 
 int prepare_ga_kernels(int maxsmem)
 {
-    if (int rc = raise_smem(select_kernel<uint16_t>, maxsmem)) return rc;
-    if (int rc = raise_smem(select_kernel<int32_t>, maxsmem)) return rc;
+    (void)maxsmem; // select_kernel uses static shared memory only
     return GPGA_OK;
 }
 

@@ -47,7 +47,7 @@ constexpr int SMALL_CLUSTER = 8;
 // += sum_s n_s (n_s - 1) / 2.
 __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
                                     const int32_t *__restrict__ Dfix, int diag,
-                                    const double2 *__restrict__ ltab,
+                                    const long long *__restrict__ ltab,
                                     const long long *__restrict__ kfix, int lane,
                                     unsigned long long *pairs_out)
 {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256)
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
-    const double2 *ltab = reinterpret_cast<const double2 *>(logtab);
+    const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *ktab = kfix_of(logtab);
     const int diag = *diag_flag;
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256)
     }
     __syncwarp();
     const double v = gather_score_warp(sl, N, Np, Dfix, *diag_flag,
-                                       reinterpret_cast<const double2 *>(logtab), kfix_of(logtab),
+                                       reinterpret_cast<const long long *>(logtab), kfix_of(logtab),
                                        lane, pairs ? pairs + g + 1 : nullptr);
     if (lane == 0) L[slot] = v;
 }

@@ -92,36 +92,11 @@ inline int pad_n(int N) { return (N + 63) & ~63; }
 // FP32 row sums: |row sum| <= 2 N, n_s <= N, so 2 N^2 2^bits < 2^62
 int fix_bits_for(int N);
 
-// ---------------------------------------------------------------------------
-// Natural log in FP64 for x > 0 normal, table-driven (P. T. P. Tang, "Table-
-// driven implementation of the logarithm function in IEEE floating-point
-// arithmetic", ACM TOMS 16(4), 1990): x = 2^e m, m in [1, 2); the top 8
-// mantissa bits pick c_k = 1 + (k + 1/2)/256, with tab[k] = (inv_k, -log inv_k)
-// and inv_k = fl(1/c_k); r = m inv_k - 1 (one FMA, |r| <= 2^-9 + ulp) and
-// log x = e ln2 - log inv_k + log1p(r), log1p by its Taylor series to r^6
-// (truncation < |r|^7/7 < 2e-20). About 9 FP64 operations.
-// ---------------------------------------------------------------------------
-constexpr int LOG_TAB = 256;
+constexpr int LOG_TAB = 256; // cells of the table-driven logarithm (log_q62)
 
-__device__ __forceinline__ double table_log(double x, const double2 *__restrict__ tab)
-{
-    const long long b = __double_as_longlong(x);
-    const int e = (int)(b >> 52) - 1023;
-    const int k = (int)((b >> 44) & 0xff);
-    const double m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
-    const double2 t = tab[k];
-    const double r = fma(m, t.x, -1.0);
-    double q = fma(r, -1.0 / 6.0, 0.2);
-    q = fma(r, q, -0.25);
-    q = fma(r, q, 1.0 / 3.0);
-    q = fma(r, q, -0.5);
-    q = fma(r, q, 1.0);
-    return fma((double)e, 0.6931471805599453, fma(r, q, t.y));
-}
-
-// layout of the per-run log table (8-byte slots): LOG_TAB pairs
-// (inv_k, -log inv_k) as doubles, then K[n] = 1/2 (log n + (n - 1) log(n (n - 1)))
-// for n = 0..N as int64 fixed point 2^-44 (kfix_of)
+// layout of the per-run log table (8-byte slots): LOG_TAB pairs (inv_k, t_k)
+// of log_q62() as int64, then K[n] = 1/2 (log n + (n - 1) log(n (n - 1))) for
+// n = 0..N as int64 fixed point 2^-44 (kfix_of)
 inline size_t logtab_len(int N) { return 2 * LOG_TAB + (size_t)N + 1; }
 __host__ __device__ inline const long long *kfix_of(const double *logtab)
 {
@@ -230,9 +205,49 @@ __device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int
     a.k += kfix[n];
 }
 
+// signed Q62 product (a b) >> 62
+__device__ __forceinline__ long long mulq62(long long a, long long b)
+{
+    const long long hi = __mul64hi(a, b);
+    const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+    return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
+// log(m 2^-62) in Q62 for m in [2^62, 2^63), table-driven (Tang's method in
+// fixed point): the top 8 fraction bits pick inv_k ~ 2^62 / c_k with
+// c_k = 1 + (k + 1/2)/256 and t_k = -log(inv_k 2^-62) (tab[2k], tab[2k+1]);
+// r = m inv_k 2^-124 - 1 (|r| <= 2^-9), log = t_k + log1p(r), log1p by its
+// series to r^6 (truncation < 2^-65). Integer pipe only.
+__device__ __forceinline__ long long log_q62(unsigned long long m,
+                                             const long long *__restrict__ tab)
+{
+    const int k = (int)((m >> 54) & 0xff);
+    const unsigned long long inv = (unsigned long long)tab[2 * k];
+    const unsigned long long lo = m * inv, hi = __umul64hi(m, inv);
+    const long long r = (long long)(((hi << 2) | (lo >> 62)) - (1ull << 62));
+    long long q = 922337203685477581ll - mulq62(r, 768614336404564651ll); // 1/5 - r/6
+    q = -1152921504606846976ll + mulq62(r, q);                             // -1/4 + r q
+    q = 1537228672809129301ll + mulq62(r, q);                              // 1/3 + r q
+    q = -2305843009213693952ll + mulq62(r, q);                             // -1/2 + r q
+    q = 4611686018427387904ll + mulq62(r, q);                              // 1 + r q
+    return tab[2 * k + 1] + mulq62(r, q);
+}
+
+// x 2^-s as a double for a signed integer x (integer pipe; rounding toward zero)
+__device__ __forceinline__ double dbl_scaled(long long x, int s)
+{
+    if (x == 0) return 0.0;
+    const unsigned long long sign = x < 0 ? 0x8000000000000000ull : 0ull;
+    const long long b = __double_as_longlong(dbl_of(x < 0 ? -x : x)) - ((long long)s << 52);
+    return __longlong_as_double((long long)((unsigned long long)b | sign));
+}
+
+constexpr long long LN2_Q62 = 3196577161300663915ll; // round(ln 2 2^62)
+
 // combine the lanes' partial products (fixed xor butterfly: every lane ends
-// with the same value) and return L = k 2^-44 - 1/2 (e ln 2 + log(m 2^-62))
-__device__ __forceinline__ double logprod_finish(LogProd a, const double2 *__restrict__ ltab,
+// with the same value) and return L = k 2^-44 - 1/2 (e ln 2 + log(m 2^-62)),
+// evaluated in fixed point Q40 (absolute error ~1e-12)
+__device__ __forceinline__ double logprod_finish(LogProd a, const long long *__restrict__ ltab,
                                                  int nclusters)
 {
     if (nclusters == 0) return 0.0; // all singletons: Eq. 8 is an empty sum
@@ -244,11 +259,13 @@ __device__ __forceinline__ double logprod_finish(LogProd a, const double2 *__res
         mant_mul(a.m, a.e, m2, e2);
         a.k += k2;
     }
-    // m 2^-62 as a double in [1, 2) (truncated to 52 fraction bits)
-    const double md = __longlong_as_double((long long)(0x3ff0000000000000ull |
-                                                       ((a.m >> 10) & 0x000fffffffffffffull)));
-    const double kd = dbl_of(a.k) * 5.684341886080802e-14; // 2^-44
-    return fma(-0.5, fma((double)a.e, 0.6931471805599453, table_log(md, ltab)), kd);
+    // e ln2 in Q40 from the exact 128-bit product e LN2_Q62, then + log m
+    const long long ph = __mul64hi(a.e, LN2_Q62);
+    const unsigned long long pl = (unsigned long long)a.e * (unsigned long long)LN2_Q62;
+    const long long elog = (long long)(((unsigned long long)ph << 42) | (pl >> 22));
+    const long long tot = elog + (log_q62(a.m, ltab) >> 22);
+    const long long Lq = (a.k >> (KFIX_BITS - 40)) - (tot >> 1);
+    return dbl_scaled(Lq, 40);
 }
 
 // ---------------------------------------------------------------------------

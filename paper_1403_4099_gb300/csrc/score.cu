@@ -23,13 +23,14 @@ int fix_bits_for(int N)
     return bits;
 }
 
-// entry k of the table_log() table: (inv_k, -log inv_k), inv_k = fl(1 / c_k)
-__device__ __forceinline__ void log_tab_entry(int k, double *out)
+// entry k of the log_q62() table: inv_k = fl(1 / c_k) 2^62 (exact: a 53-bit
+// double scaled by a power of two), t_k = -log(inv_k 2^-62) in Q62
+__device__ __forceinline__ void log_tab_entry(int k, long long *out)
 {
     const double c = 1.0 + ((double)k + 0.5) / (double)LOG_TAB;
-    const double inv = 1.0 / c;
-    out[0] = inv;
-    out[1] = -log(inv);
+    const double v = 1.0 / c;
+    out[0] = (long long)(v * 4611686018427387904.0);
+    out[1] = __double2ll_rn(-log(v) * 4611686018427387904.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -68,10 +69,11 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
         }
     }
     if (logtab) {
-        // log table of table_log(), then the per-size constant of the assembly,
+        // table of log_q62(), then the per-size constant of the assembly,
         // K[n] = 1/2 (log n + (n - 1) log(n (n - 1))), in fixed point 2^-44
         const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-        for (int k = tid; k < LOG_TAB; k += nt) log_tab_entry(k, logtab + 2 * k);
+        for (int k = tid; k < LOG_TAB; k += nt)
+            log_tab_entry(k, reinterpret_cast<long long *>(logtab) + 2 * k);
         long long *kfix = reinterpret_cast<long long *>(logtab + 2 * LOG_TAB);
         for (int n = tid; n <= N; n += nt) {
             double v = 0.0;
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(256)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     unsigned long long *dfx = smem_u64 + (size_t)warp * Np;
     int *cnt = reinterpret_cast<int *>(smem_u64 + (size_t)nw * Np) + warp * Np;
-    const double2 *__restrict__ ltab = reinterpret_cast<const double2 *>(logtab);
+    const long long *__restrict__ ltab = reinterpret_cast<const long long *>(logtab);
     const long long *__restrict__ ktab = kfix_of(logtab);
 
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
@@ -436,15 +438,21 @@ int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, con
     return GPGA_OK;
 }
 
-// diagnostic: table_log() and CUDA's log on the same inputs
+// diagnostic: log_q62() (with the exponent term) and CUDA's log on the same
+// positive normal inputs
 __global__ void log_selftest_kernel(const double *__restrict__ x, int n, double *__restrict__ yt,
                                     double *__restrict__ yc)
 {
-    __shared__ double tab[2 * LOG_TAB];
+    __shared__ long long tab[2 * LOG_TAB];
     for (int k = threadIdx.x; k < LOG_TAB; k += blockDim.x) log_tab_entry(k, tab + 2 * k);
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        yt[i] = table_log(x[i], reinterpret_cast<const double2 *>(tab));
+        const long long b = __double_as_longlong(x[i]);
+        const int e = (int)(b >> 52) - 1023;
+        const unsigned long long m = (((unsigned long long)b & 0x000fffffffffffffull) |
+                                      0x0010000000000000ull) << 10; // Q62
+        const long long lq = log_q62(m, tab);
+        yt[i] = fma((double)e, 0.6931471805599453, (double)lq * 2.168404344971009e-19);
         yc[i] = log(x[i]);
     }
 }
