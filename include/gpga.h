@@ -227,6 +227,29 @@ GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
 GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *y_cuda,
                                void *stream);
 
+/*
+ * ga_score_noalloc -- the paper has no counterpart to this entry point. Same
+ * result as ga_score(..., GPGA_FORM_GATHER, ...), for callers that must not
+ * have the library allocate device memory while scoring (a host whose own
+ * pool allocator already owns nearly all GPU memory, or a latency-critical
+ * loop that forbids allocator calls). Its working memory is a fixed file-scope
+ * __device__ array of about 8 MiB that every GPU loading the library holds
+ * until the process exits; the call makes no cudaMalloc, cudaFree or other
+ * allocating call. The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture. The caller passes inputs and outputs exactly as
+ * for ga_score: labels (device, P x N int32 in [0, N), leading dimension
+ * ld >= N), C (device, N x N FP64), L (device, P FP64, written).
+ * Limits: 2 <= N <= 1024 (GPGA_ERR_ARG beyond), 1 <= P <= 2^24.
+ * All calls share the one array and it keeps the previous call's contents
+ * (the call clears what must start at zero): calls that overlap on the GPU,
+ * from different streams or threads, race and must be serialised by the
+ * caller. Errors as ga_score; blocks the host until the stream reaches the end
+ * of the call.
+ */
+GPGA_API int ga_score_noalloc(const int32_t *labels, int P, int N, int ld, const double *C,
+                              double *L, void *stream);
+
 /* ga_free -- release the handle and all its device memory (NULL is a no-op). */
 GPGA_API int ga_free(gpga_ga *h);
 

@@ -24,7 +24,7 @@ MAX_N, MAX_P = 4096, 16384
 
 EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score", "ga_evolve",
            "ga_init", "ga_reset", "ga_step", "ga_best", "ga_history", "ga_kernel_times",
-           "ga_population", "gpga_log_selftest", "ga_free"]
+           "ga_population", "gpga_log_selftest", "ga_score_noalloc", "ga_free"]
 
 
 class GpgaError(RuntimeError):
@@ -86,6 +86,7 @@ def lib() -> ct.CDLL:
             "ga_kernel_times": (i32, [vp, vp, i32, ct.POINTER(i32)]),
             "ga_population": (i32, [vp, vp, vp]),
             "gpga_log_selftest": (i32, [vp, i32, vp, vp, vp]),
+            "ga_score_noalloc": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "ga_free": (i32, [vp]),
         }
         for name, (res, args) in sigs.items():
@@ -148,6 +149,16 @@ def ga_score(labels, C, form: int = FORM_PLAIN, L=None, stream=None):
         L = torch.empty(P, dtype=torch.float64, device=labels.device)
     _check(lib().ga_score(_dev(labels, "int32"), P, N, N, _dev(C, "float64"), _dev(L, "float64"),
                           int(form), _stream_ptr(stream)))
+    return L
+
+
+def ga_score_noalloc(labels, C, L, stream=None):
+    """Gather-form L_c into the caller's L without any device allocation by the
+    library (its scratch is a fixed device array; N <= 1024; concurrent calls
+    race). labels: P x N int32 device, C: N x N FP64 device, L: P FP64 device."""
+    P, N = labels.shape
+    _check(lib().ga_score_noalloc(_dev(labels, "int32"), P, N, N, _dev(C, "float64"),
+                                  _dev(L, "float64"), _stream_ptr(stream)))
     return L
 
 
