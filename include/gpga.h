@@ -88,7 +88,8 @@ typedef struct gpga_params {
     double tau_lo;       /* threshold init: tau range */
     double tau_hi;
     int32_t record;      /* keep per-generation best L, best labels and device timestamps */
-    int32_t profile;     /* record CUDA events around every stage of every generation */
+    int32_t profile;     /* CUDA events in every generation: 1 around the dominant
+                            kernel only, 2 around every stage */
     int32_t reserved[2];
 } gpga_params;
 
@@ -206,8 +207,10 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
  * ga_kernel_times -- stage durations (ms, CUDA events on the handle's stream) of
  * the generations run by the most recent graph launch of ga_step, available
  * when params.profile != 0. Row g of ms (count x 4, count <= cap) holds
- * [evolve, pair accumulation (plain) or contraction (tensor), assembly,
- * selection]. Waits for the stream. GPGA_ERR_STATE without profile.
+ * [evolve (gather form: the fused generation kernel), pair accumulation
+ * (plain) or contraction (tensor), assembly, selection]; with profile = 1 only
+ * the dominant kernel's entry is measured (the others are 0). Waits for the
+ * stream. GPGA_ERR_STATE without profile.
  */
 GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count);
 

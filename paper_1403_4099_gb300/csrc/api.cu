@@ -162,7 +162,7 @@ size_t carve(gpga_ga *h, char *base)
     h->acc = c.take<float>(P * Np);
     h->perm = c.take<int32_t>(P);
     h->rank = c.take<int>(P);
-    h->ticket = c.take<unsigned>(1);
+    h->ticket = c.take<unsigned>(TICKETS);
     h->rank_prefix = c.take<uint64_t>(P);
     h->work_prefix = c.take<uint64_t>(P);
     h->st = c.take<DevState>(1);
@@ -237,9 +237,19 @@ int enqueue_select(gpga_ga *h, int gen_off)
                                    h->ts, h->stream);
 }
 
+// event boundaries 0..4 of a generation: before evolve, after evolve (or the
+// fused kernel), after the main scoring kernel, after assembly, after selection.
+// profile 1 records only the boundaries of the dominant kernel, profile 2 all.
+static bool marked(const gpga_ga *h, int k)
+{
+    if (h->prm.profile >= 2) return true;
+    if (h->prm.form == GPGA_FORM_GATHER) return k == 0 || k == 1;
+    return k == 1 || k == 2;
+}
+
 static int mark(gpga_ga *h, cudaEvent_t *evs, int k)
 {
-    if (!evs) return GPGA_OK;
+    if (!evs || !marked(h, k)) return GPGA_OK;
     GPGA_CUDA(cudaEventRecordWithFlags(evs[k], h->stream, cudaEventRecordExternal));
     return GPGA_OK;
 }
@@ -288,7 +298,7 @@ int enqueue_start(gpga_ga *h, const double *C)
     GPGA_CUDA(cudaMemcpyAsync(h->C64, C, nn, cudaMemcpyDeviceToDevice, h->stream));
     GPGA_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
     GPGA_CUDA(cudaMemsetAsync(h->rank, 0, (size_t)h->P * sizeof(int), h->stream));
-    GPGA_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
+    GPGA_CUDA(cudaMemsetAsync(h->ticket, 0, TICKETS * sizeof(unsigned), h->stream));
     GPGA_CUDA(cudaMemsetAsync(h->diag, 0, sizeof(int), h->stream));
     if (h->pairs)
         GPGA_CUDA(cudaMemsetAsync(h->pairs, 0, ((size_t)h->prm.max_gens + 1) * sizeof(unsigned long long),
@@ -463,18 +473,19 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int P = p->P, E = p->elite, M = P - E;
-    const size_t total = (size_t)P * (2 * sizeof(uint64_t) + 3 * sizeof(int32_t)) + 2048;
+    const size_t total = (size_t)P * (2 * sizeof(uint64_t) + 3 * sizeof(int32_t)) + 2048 +
+                         TICKETS * sizeof(unsigned);
     char *ws = nullptr;
     GPGA_CUDA(cudaMallocAsync((void **)&ws, total, s));
     Carver c(ws);
     uint64_t *rpre = c.take<uint64_t>(P);
     uint64_t *wpre = c.take<uint64_t>(P);
     int *rank = c.take<int>(P);
-    unsigned *ticket = c.take<unsigned>(1);
+    unsigned *ticket = c.take<unsigned>(TICKETS);
     int32_t *pm_ = perm ? perm : c.take<int32_t>(P);
     do {
         if (cudaMemsetAsync(rank, 0, (size_t)P * sizeof(int), s) != cudaSuccess ||
-            cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess) {
+            cudaMemsetAsync(ticket, 0, TICKETS * sizeof(unsigned), s) != cudaSuccess) {
             rc = set_error(GPGA_ERR_CUDA, "ga_evolve: memset failed");
             break;
         }
@@ -681,7 +692,8 @@ GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count)
         for (int e = 0; e < 4; ++e) {
             float t = 0.f;
             const int stage_end = e == 3 ? 4 : e + 1;
-            GPGA_CUDA(cudaEventElapsedTime(&t, evs[k][e], evs[k][stage_end]));
+            if (marked(h, e) && marked(h, stage_end))
+                GPGA_CUDA(cudaEventElapsedTime(&t, evs[k][e], evs[k][stage_end]));
             ms[k * 4 + e] = t;
         }
     if (count) *count = n;

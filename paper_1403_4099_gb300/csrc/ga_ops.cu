@@ -103,6 +103,7 @@ __global__ void state_init_kernel(DevState *st, unsigned long long *ts0, uint32_
     st->done = 0;
     st->best_idx = 0;
     st->err = 0;
+    st->lsum = 0;
     st->best = 0.0;
     st->mean = 0.0;
     if (ts0) {
@@ -144,10 +145,11 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 // memory (bitonic) and counts, for each key i of chunk x, the fitter keys of
 // chunk y by binary search; integer atomics sum the counts, so the ranks are
 // exact and order-independent (P^2/256 log 256 comparisons instead of P^2).
-// The CTA that arrives last (ticket; nobody waits) then holds every rank: it
-// scatters perm[rank_i] = i, zeroes rank for the next use, and does "evaluate
-// state and statistics" (best, mean), the record of the best configuration
-// and the device clock, "determine if termination criteria are met", and for
+// Tickets (no CTA ever waits): the last CTA of column x holds the final ranks
+// of chunk x and scatters perm[rank_i] = i (zeroing rank for the next use) and
+// its share of the mean; the last such column finisher does "evaluate state
+// and statistics" (best, mean), the record of the best configuration and the
+// device clock, "determine if termination criteria are met", and for
 // proportional scaling the weights by rank with their inclusive prefix.
 // Stateful use: g = st->gen + gen_off.
 // ---------------------------------------------------------------------------
@@ -166,7 +168,6 @@ __global__ void __launch_bounds__(RANK_CHUNK)
     __shared__ unsigned long long sk[RANK_CHUNK];
     __shared__ int si[RANK_CHUNK];
     __shared__ int s_last;
-    __shared__ double s_red[RANK_CHUNK / 32];
     __shared__ uint64_t s_part[RANK_CHUNK];
     const int tid = threadIdx.x, nt = blockDim.x;
     {
@@ -206,41 +207,58 @@ __global__ void __launch_bounds__(RANK_CHUNK)
             if (lo) atomicAdd(&rank[i], lo);
         }
     }
+    // column ticket: the last of the nc CTAs of column x holds the final ranks
+    // of chunk x, scatters them into perm and adds its share of the mean
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    if (tid == 0) s_last = atomicAdd(&ticket[1 + blockIdx.x], 1u) == gridDim.y - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (tid == 0) *ticket = 0u;
-    for (int i = tid; i < P; i += nt) {
-        perm[__ldcg(rank + i)] = i;
-        rank[i] = 0;
+    {
+        const int i = blockIdx.x * RANK_CHUNK + tid;
+        if (i < P) {
+            perm[__ldcg(rank + i)] = i;
+            rank[i] = 0;
+        }
+        if (tid == 0) ticket[1 + blockIdx.x] = 0u;
+        if (st) {
+            // population mean in fixed point 2^-30 (exact integer sum; non-finite
+            // fitness left out)
+            long long f = 0;
+            if (i < P) {
+                const double v = L[i];
+                if (isfinite(v)) f = __double2ll_rn(v * 1073741824.0);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+            if ((tid & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&st->lsum),
+                                           (unsigned long long)f);
+        }
     }
-    __threadfence_block();
+    // global ticket: the last column finisher does the generation's bookkeeping
+    __threadfence();
     __syncthreads();
-    const int bidx = perm[0];
+    if (tid == 0) s_last = atomicAdd(&ticket[0], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) ticket[0] = 0u;
+    const int bidx = __ldcg(perm);
     if (st) {
         const int g = st->gen + cfg.gen_off;
-        double part = 0.0;
-        for (int k = tid; k < P; k += nt) part += L[k];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = part;
         if (cfg.record && ring) {
             const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
             for (int j = tid; j < cfg.N; j += nt) ring[(size_t)g * cfg.N + j] = src[j];
         }
-        __syncthreads();
         if (tid == 0) {
-            double m = 0.0;
-            for (int w = 0; w < (nt >> 5); ++w) m += s_red[w];
             double best = L[bidx];
             if (isnan(best)) best = -INFINITY;
             st->gen = g;
             st->best = best;
             st->best_idx = bidx;
-            st->mean = m / (double)P;
+            st->mean = (double)__ldcg(&st->lsum) * 9.313225746154785e-10 / (double)P;
+            st->lsum = 0;
             hist[g] = best;
             int done = g >= cfg.max_gens;
             if (!done && cfg.tol >= 0.0 && cfg.stall_gens > 0 && g >= cfg.stall_gens) {
@@ -269,7 +287,7 @@ __global__ void __launch_bounds__(RANK_CHUNK)
     for (int r = lo; r < hi; ++r) {
         uint64_t w = 1;
         if (lmax > 0.0) {
-            double x = L[perm[r]];
+            double x = L[__ldcg(perm + r)];
             if (!(x > 0.0)) x = 0.0;
             w = (uint64_t)floor(__dmul_rn(__ddiv_rn(x, lmax), 4294967296.0));
         }

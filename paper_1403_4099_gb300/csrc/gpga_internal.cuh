@@ -73,6 +73,7 @@ struct DevState {
     double best;  // its L
     double mean;  // population mean L
     uint32_t k0, k1; // Philox key (the run's seed), read by the graphed kernels
+    long long lsum;  // fixed-point (2^-30) sum of the generation's fitness, for the mean
 };
 
 // label storage traits: the handle stores labels as uint16 (N <= 65535), the
@@ -333,8 +334,10 @@ template <typename LabT>
 int launch_init_uniform(LabT *pop, int ldp, int P, int N, int K0, uint32_t k0, uint32_t k1,
                         cudaStream_t s);
 
-// rank (counting, grid) + finalize (perm, stats, termination, records, PROP
-// prefix); rank[] and *ticket must be zero on entry and are left zero
+// rank (chunked sort + search, grid) + finalize (perm, stats, termination,
+// records, PROP prefix); rank[] and ticket[0 .. 1 + P/256] must be zero on
+// entry and are left zero
+constexpr int TICKETS = 2 + GPGA_MAX_P / 256;
 template <typename LabT>
 int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *perm,
                   uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,
