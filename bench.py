@@ -253,6 +253,21 @@ def run_gpu(args, ranks):
                 "peak_source": f"{SMS} SMs x {ALU_LANES} FP32/INT32 lanes x "
                                f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max clock)",
                 "algorithmic_ops_per_launch": ops, "launch_ms": main_ms}
+    elif form == gpga.FORM_TENSOR:
+        # issued tcgen05 work: column tiles of 128 clusters x row tiles of 256 x
+        # K = Np, two MMAs (D_hi, D_lo) of 2 M N K FLOPs each
+        Np = (N + 63) // 64 * 64
+        NTt = min(256, Np)
+        cols = float(np.mean(hist["clusters"][1:])) if len(hist["clusters"]) > 1 else 0.0
+        n_ct = int(np.ceil(cols / 128.0))
+        flops = n_ct * int(np.ceil(Np / NTt)) * 2 * 2.0 * 128 * NTt * Np
+        t = main_ms / 1e3
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "kernel": "tc_mma (with column prep)", "achieved": flops / t / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                "peak_source": f"bf16_tflops_sustained ({pk_kind})",
+                "issued_mma_flops_per_launch": flops, "columns_per_launch": cols,
+                "launch_ms": main_ms}
     elif form == gpga.FORM_GATHER:
         pairs = hist["pairs"]
         roof = gather_roofline(main_ms, pk, pk_kind,
@@ -299,6 +314,9 @@ def run_gpu(args, ranks):
                        "generations_per_step": G, "form": args.form, "init": "uniform",
                        "l2": "flushed between steps (256 MB memset outside the step events)"},
             "generations_per_s": gens_per_s,
+            "non_singleton_clusters_per_individual": {
+                "first_generation": float(hist["clusters"][0]) / P,
+                "last_generation": float(hist["clusters"][-1]) / P},
             "same_cluster_pairs_per_individual": {
                 "first_generation": float(hist["pairs"][0]) / P,
                 "last_generation": float(hist["pairs"][-1]) / P,

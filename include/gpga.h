@@ -193,15 +193,17 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation);
 
 /*
  * ga_history -- per-generation records kept when params.record != 0: best L
- * (FP64), best labels (int32, as stored), the device clock (ns, %globaltimer)
- * and the number of same-cluster gene pairs sum_s n_s (n_s - 1) / 2 summed over
- * the population (the work Eq. 6 needs), for generations 0..count-1,
+ * (FP64), best labels (int32, as stored), the device clock (ns, %globaltimer),
+ * the number of same-cluster gene pairs sum_s n_s (n_s - 1) / 2 summed over
+ * the population (the work Eq. 6 needs; gather, plain and tensor forms) and
+ * the number of non-singleton clusters summed over the population (tensor
+ * form: the columns of the contraction), for generations 0..count-1,
  * count <= cap. Host pointers (each optional). t_ns[0] is taken at the start
  * of ga_init / ga_reset, t_ns[1 + g] at the end of generation g (so t_ns holds
  * count + 1 values). Waits for the stream.
  */
 GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns,
-                        uint64_t *pairs, int cap, int *count);
+                        uint64_t *pairs, uint64_t *clusters, int cap, int *count);
 
 /*
  * ga_kernel_times -- stage durations (ms, CUDA events on the handle's stream) of

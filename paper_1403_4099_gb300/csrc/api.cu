@@ -115,6 +115,7 @@ struct gpga_ga {
     uint16_t *ring = nullptr;
     unsigned long long *ts = nullptr;
     unsigned long long *pairs = nullptr;
+    unsigned long long *clusters = nullptr;
     int32_t *mst_order = nullptr, *mst_from = nullptr;
     double *mst_w = nullptr;
     int *err = nullptr;
@@ -170,6 +171,7 @@ size_t carve(gpga_ga *h, char *base)
     h->ring = h->prm.record ? c.take<uint16_t>(G * N) : nullptr;
     h->ts = h->prm.record ? c.take<unsigned long long>(G + 1) : nullptr;
     h->pairs = h->prm.record ? c.take<unsigned long long>(G) : nullptr;
+    h->clusters = h->prm.record ? c.take<unsigned long long>(G) : nullptr;
     h->mst_order = c.take<int32_t>(N);
     h->mst_from = c.take<int32_t>(N);
     h->mst_w = c.take<double>(N);
@@ -196,16 +198,22 @@ int enqueue_score(gpga_ga *h, int sel_off, cudaEvent_t *evs = nullptr)
         if (!rc) rc = mark(h, evs, 3);
         return rc;
     }
-    if (tensor)
-        rc = tc_score<uint16_t>(&h->tc, h->Dhi, h->Dlo, h->Np, lab2, h->Np, sel_off, h->P, h->N,
-                                h->acc, h->st, h->stream);
-    else
+    if (tensor) { // columns + tcgen05 contraction, then the assembly
+        rc = tc_contract<uint16_t>(&h->tc, h->Dhi, h->Dlo, h->Np, lab2, h->Np, sel_off, h->P,
+                                   h->N, h->err, h->st, h->pairs, h->clusters, h->stream);
+        if (!rc) rc = mark(h, evs, 2);
+        if (!rc)
+            rc = tc_finish<uint16_t>(&h->tc, lab2, h->Np, sel_off, h->P, h->N, h->logtab, h->L,
+                                     h->err, h->st, h->stream);
+        if (!rc) rc = mark(h, evs, 3);
+        return rc;
+    }
         rc = launch_pair_plain<uint16_t>(h->D32, h->Np, lab2, h->Np, sel_off, h->P, h->N, h->acc,
                                          h->st, h->stream);
     if (!rc) rc = mark(h, evs, 2);
     if (!rc)
-        rc = launch_assemble<uint16_t>(lab2, h->Np, sel_off, h->acc, h->Np, h->D32, tensor, h->P,
-                                       h->N, h->logtab, h->L, h->err, h->st, h->pairs, h->stream);
+        rc = launch_assemble<uint16_t>(lab2, h->Np, sel_off, h->acc, h->Np, h->D32, 0, h->P, h->N,
+                                       h->logtab, h->L, h->err, h->st, h->pairs, h->stream);
     if (!rc) rc = mark(h, evs, 3);
     return rc;
 }
@@ -303,6 +311,9 @@ int enqueue_start(gpga_ga *h, const double *C)
     if (h->pairs)
         GPGA_CUDA(cudaMemsetAsync(h->pairs, 0, ((size_t)h->prm.max_gens + 1) * sizeof(unsigned long long),
                                   h->stream));
+    if (h->clusters)
+        GPGA_CUDA(cudaMemsetAsync(h->clusters, 0,
+                                  ((size_t)h->prm.max_gens + 1) * sizeof(unsigned long long), h->stream));
     int rc = launch_state_init(h->st, h->ts, h->k0, h->k1, h->stream);
     if (rc) return rc;
     rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->Dfix, h->logtab,
@@ -439,10 +450,9 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
             rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, Dfix, err + 1, logtab, L, err,
                                               nullptr, nullptr, s);
         } else if (form == GPGA_FORM_TENSOR) {
-            rc = tc_score<int32_t>(&tc, Dhi, Dlo, Np, lab2, ld, 0, P, N, acc, nullptr, s);
-            if (rc) break;
-            rc = launch_assemble<int32_t>(lab2, ld, 0, acc, Np, D32, 1, P, N, logtab, L, err,
-                                          nullptr, nullptr, s);
+            rc = tc_contract<int32_t>(&tc, Dhi, Dlo, Np, lab2, ld, 0, P, N, err, nullptr, nullptr,
+                                      nullptr, s);
+            if (!rc) rc = tc_finish<int32_t>(&tc, lab2, ld, 0, P, N, logtab, L, err, nullptr, s);
         } else {
             rc = launch_pair_plain<int32_t>(D32, Np, lab2, ld, 0, P, N, acc, nullptr, s);
             if (rc) break;
@@ -649,7 +659,7 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation)
 }
 
 GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns,
-                        uint64_t *pairs, int cap, int *count)
+                        uint64_t *pairs, uint64_t *clusters, int cap, int *count)
 {
     g_err[0] = 0;
     if (!h) return set_error(GPGA_ERR_ARG, "ga_history: NULL handle");
@@ -661,7 +671,7 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
     if (count) *count = n;
     if (n <= 0) return GPGA_OK;
     if (best_L) GPGA_CUDA(cudaMemcpy(best_L, h->hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
-    if (best_labels || t_ns || pairs) {
+    if (best_labels || t_ns || pairs || clusters) {
         if (!h->prm.record) return set_error(GPGA_ERR_STATE, "ga_history: run created with record = 0");
     }
     if (best_labels) {
@@ -675,6 +685,8 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
         if (e != cudaSuccess) return cuda_error(e, "ga_history copy", __FILE__, __LINE__);
     }
     if (pairs) GPGA_CUDA(cudaMemcpy(pairs, h->pairs, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (clusters)
+        GPGA_CUDA(cudaMemcpy(clusters, h->clusters, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (t_ns) GPGA_CUDA(cudaMemcpy(t_ns, h->ts, (size_t)(n + 1 > cap ? cap : n + 1) * sizeof(int64_t),
                                    cudaMemcpyDeviceToHost));
     return GPGA_OK;

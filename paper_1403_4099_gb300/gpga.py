@@ -82,7 +82,7 @@ def lib() -> ct.CDLL:
             "ga_reset": (i32, [vp, vp, ct.c_uint64]),
             "ga_step": (i32, [vp, i32, ct.POINTER(i32)]),
             "ga_best": (i32, [vp, vp, vp, ct.POINTER(i32)]),
-            "ga_history": (i32, [vp, vp, vp, vp, vp, i32, ct.POINTER(i32)]),
+            "ga_history": (i32, [vp, vp, vp, vp, vp, vp, i32, ct.POINTER(i32)]),
             "ga_kernel_times": (i32, [vp, vp, i32, ct.POINTER(i32)]),
             "ga_population": (i32, [vp, vp, vp]),
             "gpga_log_selftest": (i32, [vp, i32, vp, vp, vp]),
@@ -233,11 +233,14 @@ class GA:
             lab = np.zeros((cap, self.N), np.int32)
             ts = np.zeros(cap + 1, np.int64)
             pairs = np.zeros(cap, np.uint64)
+            clus = np.zeros(cap, np.uint64)
             _check(lib().ga_history(self._h, bl.ctypes.data, lab.ctypes.data, ts.ctypes.data,
-                                    pairs.ctypes.data, cap, ct.byref(n)))
+                                    pairs.ctypes.data, clus.ctypes.data, cap, ct.byref(n)))
             k = n.value
-            return dict(best_L=bl[:k], labels=lab[:k], t_ns=ts[:k + 1], pairs=pairs[:k])
-        _check(lib().ga_history(self._h, bl.ctypes.data, None, None, None, cap, ct.byref(n)))
+            return dict(best_L=bl[:k], labels=lab[:k], t_ns=ts[:k + 1], pairs=pairs[:k],
+                        clusters=clus[:k])
+        _check(lib().ga_history(self._h, bl.ctypes.data, None, None, None, None, cap,
+                                ct.byref(n)))
         return dict(best_L=bl[: n.value])
 
     def kernel_times(self):

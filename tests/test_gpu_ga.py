@@ -85,7 +85,7 @@ def test_threshold_init_bit_exact(g, orc):
         ga.close()
 
 
-@pytest.mark.parametrize("scaling,form", [(0, 0), (1, 0), (0, 2), (1, 2)])
+@pytest.mark.parametrize("scaling,form", [(0, 0), (1, 0), (0, 2), (1, 2), (0, 1)])
 def test_pipeline_generation_by_generation(g, orc, scaling, form):
     """Each device generation equals the oracle's operators applied to the
     device's own population and fitness (bit-exact), and the device fitness
@@ -135,7 +135,7 @@ def test_termination_and_noop_after_done(g, orc):
     ga.close()
 
 
-@pytest.mark.parametrize("form", [0, 2])
+@pytest.mark.parametrize("form", [0, 1, 2])
 def test_recovers_small16(g, orc, form):
     p = synth.small16()
     C = orc.pearson(p.R)

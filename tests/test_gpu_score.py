@@ -8,7 +8,7 @@ from gpu_util import assert_L_close, dev
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [0, 2]  # plain, gather
+FORMS = [0, 1, 2]  # plain, tensor, gather
 
 
 @pytest.fixture(scope="module")
@@ -104,8 +104,9 @@ def test_forms_agree(g, orc):
     C = orc.pearson(p.R)
     rng = np.random.default_rng(44)
     pop = synth.perturbed_population(rng, p.truth, 512, 0.02)
-    a, b = _score(g, pop, C, 0), _score(g, pop, C, 2)
+    a, b, t = _score(g, pop, C, 0), _score(g, pop, C, 2), _score(g, pop, C, 1)
     assert np.all(np.abs(a - b) <= 1e-4 + 1e-6 * np.abs(a))
+    assert np.all(np.abs(a - t) <= 1e-4 + 1e-6 * np.abs(a))
 
 
 def test_nonunit_diagonal_counts(g, orc):
