@@ -148,7 +148,9 @@ def gather_roofline(launch_ms, pk, pk_kind, pairs_per_gen):
     gbs = bytes_per_launch / t / 1e9
     peak = pk["hbm_gbs"]
     return {"bound": "hbm", "kernel": "gather_generation", "achieved": gbs, "peak": peak,
-            "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+            "unit": "GB/s", "frac": gbs / peak,
+            "traffic": profiled_traffic("gather_generation_n500_p4096",
+                                        source_hash("gather.cu", "gpga_internal.cuh")),
             "peak_source": f"hbm_gbs ({pk_kind})", "algorithmic_bytes_per_launch": bytes_per_launch,
             "same_cluster_pairs_per_launch": pairs_per_gen, "launch_ms": launch_ms}
 
@@ -247,7 +249,8 @@ def run_gpu(args, ranks):
         ops = float(P) * N * (N - 1)
         t = main_ms / 1e3
         peak = SMS * ALU_LANES * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        traffic = profiled_traffic("pair_plain_n500_p4096", source_hash("score.cu"))
+        traffic = profiled_traffic("pair_plain_n500_p4096",
+                                   source_hash("score.cu", "gpga_internal.cuh"))
         roof = {"bound": "alu", "kernel": "pair_plain", "achieved": ops / t / 1e12, "peak": peak,
                 "unit": "Tops/s", "frac": (ops / t / 1e12) / peak, "traffic": traffic,
                 "peak_source": f"{SMS} SMs x {ALU_LANES} FP32/INT32 lanes x "
@@ -264,7 +267,9 @@ def run_gpu(args, ranks):
         t = main_ms / 1e3
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "kernel": "tc_mma (with column prep)", "achieved": flops / t / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
+                "traffic": profiled_traffic("tc_mma_n500_p4096",
+                                            source_hash("score_tc.cu", "gpga_internal.cuh")),
                 "peak_source": f"bf16_tflops_sustained ({pk_kind})",
                 "issued_mma_flops_per_launch": flops, "columns_per_launch": cols,
                 "launch_ms": main_ms}

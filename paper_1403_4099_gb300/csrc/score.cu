@@ -355,8 +355,9 @@ template int launch_assemble<int32_t>(const int32_t *const *, int, int, const fl
 // ---------------------------------------------------------------------------
 // Final re-score of one configuration in FP64 straight from C (Eq. 5, 6, 8),
 // plus its canonical relabelling (first occurrence -> 0, 1, 2, ...). One CTA.
-// Row sums are sequential in j; cluster sums run over members in ascending i;
-// terms are added in first-occurrence order with compensation.
+// Row sums are sequential in j; cluster sums run over members in ascending i
+// (one thread per cluster); the terms are added in first-occurrence order with
+// compensation, as 32 contiguous runs whose partial sums are then added in order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void neu_add(double &s, double &c, double x)
 {
@@ -377,13 +378,28 @@ __global__ void __launch_bounds__(1024)
     extern __shared__ double sm_d[];
     double *rc = sm_d;          // N row sums of C over same-cluster columns
     double *rd = sm_d + N;      // N row sums of (1 - C)
-    int *li = reinterpret_cast<int *>(sm_d + 2 * N); // labels
+    double *term = sm_d + 2 * N; // per canonical cluster: its Eq. 8 term (0 for singletons)
+    int *li = reinterpret_cast<int *>(sm_d + 3 * N); // labels
     int *map = li + N;          // label -> canonical id
+    int *rep = map + N;         // canonical id -> label
+    __shared__ int s_k;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         li[i] = lab[i];
         map[i] = -1;
     }
     __syncthreads();
+    // canonical ids by first occurrence (integer work only)
+    if (threadIdx.x == 0) {
+        int next = 0;
+        for (int i = 0; i < N; ++i) {
+            const int s = li[i];
+            if (map[s] < 0) {
+                map[s] = next;
+                rep[next++] = s;
+            }
+        }
+        s_k = next;
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         double sc = 0.0, cc = 0.0, sd = 0.0, cd = 0.0;
         const int si = li[i];
@@ -397,42 +413,54 @@ __global__ void __launch_bounds__(1024)
         rd[i] = sd + cd;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int next = 0;
-        double acc = 0.0, comp = 0.0;
-        for (int i = 0; i < N; ++i) {
-            const int s = li[i];
-            if (map[s] >= 0) continue;
-            map[s] = next++;
-            // members of s are i and later indices with the same label
-            int n = 0;
-            double c = 0.0, cc = 0.0, d = 0.0, dc = 0.0;
-            for (int j = i; j < N; ++j) {
-                if (li[j] != s) continue;
-                ++n;
-                neu_add(c, cc, rc[j]);
-                neu_add(d, dc, rd[j]);
-            }
-            if (n >= 2) {
-                const double dn = (double)n;
-                double cs = c + cc, ds = d + dc;
-                const double eps = 9.094947017729282e-13;
-                if (!(cs >= dn * eps)) cs = dn * eps;
-                if (!(ds >= dn * (dn - 1.0) * eps)) ds = dn * (dn - 1.0) * eps;
-                const double term = 0.5 * (log(dn / cs) + (dn - 1.0) * log((dn * dn - dn) / ds));
-                neu_add(acc, comp, term);
-            }
+    const int K = s_k;
+    // one thread per cluster: member sums in ascending index, then its term
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int s = rep[k];
+        int n = 0;
+        double c = 0.0, cc = 0.0, d = 0.0, dc = 0.0;
+        for (int j = 0; j < N; ++j) {
+            if (li[j] != s) continue;
+            ++n;
+            neu_add(c, cc, rc[j]);
+            neu_add(d, dc, rd[j]);
         }
-        *L_out = acc + comp;
+        double t = 0.0;
+        if (n >= 2) {
+            const double dn = (double)n;
+            double cs = c + cc, ds = d + dc;
+            const double eps = 9.094947017729282e-13;
+            if (!(cs >= dn * eps)) cs = dn * eps;
+            if (!(ds >= dn * (dn - 1.0) * eps)) ds = dn * (dn - 1.0) * eps;
+            t = 0.5 * (log(dn / cs) + (dn - 1.0) * log((dn * dn - dn) / ds));
+        }
+        term[k] = t;
     }
     __syncthreads();
+    // terms in canonical order: each lane of warp 0 sums a contiguous run with
+    // compensation, then lane 0 adds the 32 partial sums in lane order
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int per = (K + 31) / 32;
+        const int lo = min(K, lane * per), hi = min(K, lo + per);
+        double a = 0.0, ac = 0.0;
+        for (int k = lo; k < hi; ++k) neu_add(a, ac, term[k]);
+        double acc = 0.0, comp = 0.0;
+        for (int l = 0; l < 32; ++l) {
+            const double pa = __shfl_sync(0xffffffffu, a, l);
+            const double pc = __shfl_sync(0xffffffffu, ac, l);
+            neu_add(acc, comp, pa);
+            neu_add(acc, comp, pc);
+        }
+        if (lane == 0) *L_out = acc + comp;
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) canon[i] = map[li[i]];
 }
 
 int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
                         const double *C, int N, int32_t *canon_out, double *L_out, cudaStream_t s)
 {
-    const size_t smem = (size_t)N * (2 * sizeof(double) + 2 * sizeof(int));
+    const size_t smem = (size_t)N * (3 * sizeof(double) + 3 * sizeof(int));
     rescore_kernel<<<1, 1024, smem, s>>>(pop0, pop1, ldp, st, C, N, canon_out, L_out);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
