@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recover", action="store_true")
+    ap.add_argument("--workload", default="planted", choices=["planted", "batched", "serving"],
+                    help="planted: the N=500 headline; batched: 256 sliding intraday windows "
+                         "in one fleet; serving: Poisson request stream")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -414,12 +419,195 @@ def run_recover(args, ranks, planted, dev, form):
             "threshold_init_with_prelude": None if ms is None else ms + corr_ms}
 
 
+# ---------------------------------------------------------------------------
+# Batched: 256 sliding windows (W=390, stride 30) of an N=400 intraday series
+# whose planted structure switches at the midpoint; run k works on a random
+# column subset of N_k ~ U{20..400}; P=1024; all runs in one fleet.
+# ---------------------------------------------------------------------------
+B_WINDOWS, B_W, B_STRIDE, B_N, B_P = 256, 390, 30, 400, 1024
+
+
+def run_batched(args, ranks):
+    import torch
+
+    from paper_1403_4099_gb300 import gpga, metrics, runtime, synth
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    runtime.init_dist(ranks, "nccl")
+    win = synth.intraday(B_N, B_WINDOWS, B_W, B_STRIDE, replicate=ranks.rank)
+    subs = synth.window_subsets(B_N, B_WINDOWS, 20, B_N, replicate=ranks.rank)
+    stream = torch.cuda.Stream(device=dev)
+    prm = gpga.default_params(P=B_P, elite=10, max_gens=400, stall_gens=50, tol=1e-5, pm=0.01,
+                              form=gpga.FORM_GATHER)
+    with torch.cuda.stream(stream):
+        R = torch.from_numpy(win.R).to(dev)
+        cols = [torch.from_numpy(s).to(dev) for s in subs]
+        Cs = [torch.empty((B_N, B_N), dtype=torch.float64, device=dev) for _ in range(B_WINDOWS)]
+        seeds = [9000 + k for k in range(B_WINDOWS)]
+
+        def job():
+            for k in range(B_WINDOWS):
+                gpga.cluster_corr(R[B_STRIDE * k: B_STRIDE * k + B_W], Cs[k], stream)
+            b = gpga.Batch(Cs, prm, seeds, cols=cols, stream=stream)
+            t_init = time.perf_counter()
+            while b.step(16) > 0:
+                pass
+            return b, t_init
+
+        b, _ = job()  # warm-up (builds, tunes, captures)
+        b.close()
+        stream.synchronize()
+        runtime.barrier(ranks)
+        times, gens_tot = [], []
+        for _ in range(max(1, args.steps // 10)):
+            t0 = time.perf_counter()
+            b, t_init = job()
+            stream.synchronize()
+            t1 = time.perf_counter()
+            g, done, best = b.status()
+            times.append((t1 - t0, t_init - t0))
+            gens_tot.append(g.copy())
+            last = b
+            if _ < max(1, args.steps // 10) - 1:
+                b.close()
+    secs = float(np.mean([t for t, _ in times]))
+    g = gens_tot[-1]
+    evals = float(B_P * np.sum(g + 1))
+    max_secs, total_evals = runtime.aggregate(ranks, secs, evals, device=dev)
+    tune = last.tuning()
+    aris_b, aris_a = [], []
+    for k in range(B_WINDOWS):
+        lab, L, gg = last.best(k)
+        lo, hi = B_STRIDE * k, B_STRIDE * k + B_W
+        if hi <= win.switch:
+            aris_b.append(metrics.ari(lab, win.truth_before[subs[k]]))
+        elif lo >= win.switch:
+            aris_a.append(metrics.ari(lab, win.truth_after[subs[k]]))
+    last.close()
+    if ranks.rank == 0:
+        line = {"metric": "windows/s (256 sliding intraday windows, N_k in [20,400], P=1024, "
+                          "each run to 400 generations or stall)",
+                "value": B_WINDOWS * ranks.world / max_secs, "unit": "windows/s",
+                "n_gpus": ranks.world, "steps": len(times), "warmup": 1,
+                "ms_per_step": 1e3 * max_secs, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "intraday_n400_w390_s30_x256_p1024", "P": B_P,
+                           "N_range": [20, B_N], "windows": B_WINDOWS, "form": "gather"},
+                "evals_per_s": total_evals / max_secs,
+                "generations": {"mean": float(np.mean(g)), "min": int(g.min()), "max": int(g.max())},
+                "init_ms": 1e3 * float(np.mean([t for _, t in times])),
+                "tuning": tune,
+                "ari_single_regime_windows": {
+                    "before_switch": {"n": len(aris_b), "mean": float(np.mean(aris_b)),
+                                      "min": float(np.min(aris_b))},
+                    "after_switch": {"n": len(aris_a), "mean": float(np.mean(aris_a)),
+                                     "min": float(np.min(aris_a))}}}
+        print(json.dumps(line), flush=True)
+    runtime.barrier(ranks)
+
+
+# ---------------------------------------------------------------------------
+# Serving: Poisson arrivals of correlation windows, N in {30, 100, 300, 1000}
+# (T = 4N returns, planted clusters), P=2048, each run to 300 generations or
+# stall (50, 1e-5); latency from arrival to the collected result.
+# ---------------------------------------------------------------------------
+S_NS, S_P, S_POOL = (30, 100, 300, 1000), 2048, 8
+
+
+def run_serving(args, ranks):
+    import torch
+
+    from paper_1403_4099_gb300 import gpga, runtime, synth
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    runtime.init_dist(ranks, "nccl")
+    rng = np.random.default_rng(synth.seed_for(5, 900 + ranks.rank))
+    pool = {}
+    for n in S_NS:
+        pool[n] = []
+        for r in range(S_POOL):
+            pl = synth.serving_request(n, replicate=100 * ranks.rank + r)
+            C = gpga.cluster_corr(torch.from_numpy(pl.R).to(dev))
+            pool[n].append(C.cpu().numpy())
+    torch.cuda.synchronize()
+    prm = gpga.default_params(P=S_P, elite=10, max_gens=300, stall_gens=50, tol=1e-5, pm=0.01,
+                              form=gpga.FORM_GATHER)
+    dur, rate = args.serve_seconds, args.serve_rate
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * dur * 1.5) + 16))
+    arr = arr[arr < dur]
+    reqN = rng.choice(S_NS, size=arr.shape[0])
+    reqP = rng.integers(0, S_POOL, size=arr.shape[0])
+    stream = torch.cuda.Stream(device=dev)
+    srv = gpga.Server(prm, max_runs=1024, max_n=max(S_NS), stream=stream)
+    # warm-up request (tuning, graph capture)
+    wid = srv.submit(pool[S_NS[-1]][0], 1)
+    while srv.result(wid) is None:
+        srv.tick(8)
+    runtime.barrier(ranks)
+    lat, qs, gens, active_hist = [], [], [], []
+    pending = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    done_n = 0
+    while done_n < arr.shape[0]:
+        now = time.perf_counter() - t0
+        while nxt < arr.shape[0] and arr[nxt] <= now:
+            i = srv.submit(pool[int(reqN[nxt])][int(reqP[nxt])], 10_000 + nxt)
+            pending[i] = nxt
+            nxt += 1
+        a, q = srv.tick(8)
+        active_hist.append(a)
+        tnow = time.perf_counter() - t0
+        for i in list(pending):
+            r = srv.result(i)
+            if r is not None:
+                k = pending.pop(i)
+                lat.append(tnow - arr[k])
+                qs.append(r[3][0])
+                gens.append(r[2])
+                done_n += 1
+        if a == 0 and q == 0 and nxt < arr.shape[0]:
+            time.sleep(max(0.0, min(0.001, arr[nxt] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat_ms = 1e3 * np.array(lat)
+    n_done = len(lat)
+    max_wall, total = runtime.aggregate(ranks, wall, float(n_done), device=dev)
+    evals = float(S_P * np.sum(np.array(gens) + 1))
+    if ranks.rank == 0:
+        line = {"metric": "windows/s (Poisson stream, N in {30,100,300,1000}, P=2048, "
+                          "<=300 generations or stall)",
+                "value": total / max_wall, "unit": "windows/s", "n_gpus": ranks.world,
+                "steps": 1, "warmup": 1, "ms_per_step": 1e3 * max_wall,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "serving_poisson", "rate_per_s": rate, "seconds": dur,
+                           "requests": int(arr.shape[0]), "P": S_P, "Ns": list(S_NS)},
+                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                               "p99": float(np.percentile(lat_ms, 99)),
+                               "max": float(lat_ms.max())},
+                "queue_ms_mean": 1e3 * float(np.mean(qs)),
+                "evals_per_s": evals / wall,
+                "generations_mean": float(np.mean(gens)),
+                "active_runs": {"mean": float(np.mean(active_hist)), "max": int(max(active_hist))},
+                "launch_shape": {"warps_per_cta": st["warps_per_cta"], "ctas": st["ctas"]}}
+        print(json.dumps(line), flush=True)
+    runtime.barrier(ranks)
+
+
 def main():
     args = parse()
     from paper_1403_4099_gb300 import runtime
     ranks = runtime.ranks_from_env()
     if args.impl == "reference":
         run_reference(args, ranks)
+        return
+    if args.workload == "batched":
+        run_batched(args, ranks)
+        return
+    if args.workload == "serving":
+        run_serving(args, ranks)
         return
     run_gpu(args, ranks)
 

@@ -21,13 +21,17 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   - Layouts are row-major. Labels are int32 in [0, N) (0-based form of the
  *     paper's 1..K labels, Eq. 9, with K = N).
- *   - The library allocates device memory only in ga_init (owned by the handle,
- *     released by ga_free) and, for cluster_corr and ga_score, stream-ordered
- *     scratch (cudaMallocAsync / cudaFreeAsync) inside the call.
+ *   - The library allocates device memory only in ga_init and ga_batch_init
+ *     (owned by the handle, released by ga_free / ga_batch_free), in
+ *     serve_create and at each admission of a request (stream-ordered, freed
+ *     when the request retires or by serve_free) and, for cluster_corr and
+ *     ga_score, stream-ordered scratch (cudaMallocAsync / cudaFreeAsync)
+ *     inside the call.
  */
 #ifndef GPGA_H
 #define GPGA_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -257,6 +261,106 @@ GPGA_API int ga_score_noalloc(const int32_t *labels, int P, int N, int ld, const
 
 /* ga_free -- release the handle and all its device memory (NULL is a no-op). */
 GPGA_API int ga_free(gpga_ga *h);
+
+/* ------------------------------------------------------------------------
+ * Batch: many independent GA runs (e.g. one per sliding window of a returns
+ * series, each window's C being the input of one run as in Sec. 4) advanced
+ * together. Each run is exactly the single-run gather form with its own C, N
+ * and seed: same parameters as ga_init (p->form must be GPGA_FORM_GATHER;
+ * record and profile must be 0), and bit-for-bit the same result as ga_init +
+ * ga_step on that run alone. One generation of all runs is two kernel
+ * launches, captured in a CUDA graph; the launch shape of the fused
+ * generation kernel (warps per CTA, CTAs) is chosen at init by timing the
+ * candidates on the runs themselves.
+ * ------------------------------------------------------------------------ */
+typedef struct gpga_batch gpga_batch;
+
+/*
+ * ga_batch_init -- create `runs` runs and score their initial populations.
+ * C[k]: device pointer (host array of `runs` pointers) to run k's correlation
+ *   matrix, FP64 row-major with leading dimension ldc[k] (ldc NULL: N[k]).
+ * cols: NULL, or host array of `runs` device pointers; cols[k] (if not NULL)
+ *   holds N[k] int32 row/column indices into C[k], and run k works on the
+ *   submatrix C[k][cols[k], cols[k]] (a column subset of a larger window).
+ *   The indices are not checked on the device: each must lie in [0, ldc[k])
+ *   and C[k] must have that many rows.
+ * N[k] in [2, GPGA_MAX_N]; seeds[k] is run k's Philox key. The inputs are
+ * copied: the caller may free them after the call returns.
+ * Errors: GPGA_ERR_ARG (bad sizes, NULL arrays, unsupported options),
+ * GPGA_ERR_OOM, GPGA_ERR_CUDA. Blocks until initialisation and the launch-shape
+ * tuning have finished.
+ */
+GPGA_API int ga_batch_init(int runs, const double *const *C, const int *ldc,
+                           const int32_t *const *cols, const int *N, const gpga_params *p,
+                           const uint64_t *seeds, void *stream, gpga_batch **out);
+
+/* ga_batch_step -- advance every run that has not terminated by up to
+ * `generations` generations (terminated runs do no work). active (optional,
+ * host): number of runs not yet terminated, read after a synchronisation. */
+GPGA_API int ga_batch_step(gpga_batch *h, int generations, int *active);
+
+/* ga_batch_status -- per run (host arrays of length runs, each optional): the
+ * generation scored last, the termination flag, the best L of that
+ * generation. Synchronises the stream. */
+GPGA_API int ga_batch_status(gpga_batch *h, int32_t *generation, int32_t *done, double *best);
+
+/* ga_batch_best -- as ga_best for run `run`: canonical labels (N[run] int32),
+ * L re-scored in FP64, generation; host or device pointers. */
+GPGA_API int ga_batch_best(gpga_batch *h, int run, int32_t *labels, double *L, int *generation);
+
+/* ga_batch_tuning -- the launch shape the tuner chose and its time per
+ * generation launch in ms (each output optional). */
+GPGA_API int ga_batch_tuning(gpga_batch *h, int *warps_per_cta, int *ctas, float *ms);
+
+/* ga_batch_free -- release the batch and all its device memory (NULL: no-op). */
+GPGA_API int ga_batch_free(gpga_batch *h);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over a fleet of runs. A request is one
+ * correlation window (host N x N FP64 C, copied at submission) with its own
+ * seed; it waits in a FIFO queue until a run slot and device memory are free
+ * (admission by memory: the run's whole footprint must fit the budget and
+ * leave the reserve free), then runs on the device, its population resident
+ * across generations, alongside every other admitted request, until it
+ * terminates (max_gens or the stall rule). Its result is the same as that of
+ * ga_init + ga_step + ga_best on its C alone. Single-threaded: one host
+ * thread drives a server.
+ * ------------------------------------------------------------------------ */
+typedef struct gpga_server gpga_server;
+
+/* serve_create -- max_runs concurrent runs of N <= max_n; mem_budget: bytes
+ * of run memory the server may hold (0: free device memory less a reserve of
+ * min(1 GiB, 10%)). Parameters as ga_batch_init. */
+GPGA_API int serve_create(const gpga_params *p, int max_runs, int max_n, size_t mem_budget,
+                          void *stream, gpga_server **out);
+
+/* serve_submit -- queue one request: C host pointer, N x N FP64 row-major
+ * (copied), 2 <= N <= max_n; *id receives the request's id. No GPU work. */
+GPGA_API int serve_submit(gpga_server *h, const double *C, int N, uint64_t seed, long long *id);
+
+/* serve_tick -- one turn of the loop: wait for the previous turn's work,
+ * retire terminated runs (FP64 re-score, results to the host, memory freed),
+ * admit queued requests while slots and memory allow, then launch
+ * `generations` generations of every admitted run and return without waiting
+ * for them. active/queued (optional): runs on the device and requests
+ * waiting after admission. */
+GPGA_API int serve_tick(gpga_server *h, int generations, int *active, int *queued);
+
+/* serve_result -- 1 and the result if request `id` has finished (labels:
+ * host, N int32 canonical; L; generation; times: host, 2 doubles = seconds
+ * queued before admission and seconds from admission to retirement; each
+ * optional), and the result is then released; 0 if it is still queued or
+ * running; GPGA_ERR_ARG for an unknown or already collected id. */
+GPGA_API int serve_result(gpga_server *h, long long id, int32_t *labels, double *L,
+                          int *generation, double *times);
+
+/* serve_stats -- run memory in use, the budget, requests completed so far,
+ * and the generation kernel's launch shape (each optional). */
+GPGA_API int serve_stats(gpga_server *h, size_t *bytes_in_use, size_t *budget,
+                         long long *completed, int *warps_per_cta, int *ctas);
+
+/* serve_free -- release the server, its queue, results and device memory. */
+GPGA_API int serve_free(gpga_server *h);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ int cuda_error(cudaError_t e, const char *what, const char *file, int line)
     return set_error(code, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
-static bool is_device_ptr(const void *p)
+bool is_device_ptr(const void *p)
 {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -41,7 +41,7 @@ static bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static int check_params(const gpga_params *p, int N)
+int check_params(const gpga_params *p, int N)
 {
     if (!p) return set_error(GPGA_ERR_ARG, "params is NULL");
     if (N < 2 || N > GPGA_MAX_N) return set_error(GPGA_ERR_ARG, "N=%d outside [2, %d]", N, GPGA_MAX_N);

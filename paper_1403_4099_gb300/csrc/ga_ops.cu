@@ -155,20 +155,29 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 // ---------------------------------------------------------------------------
 constexpr int RANK_CHUNK = 256;
 
+struct SelectSmem {
+    unsigned long long sk[RANK_CHUNK];
+    int si[RANK_CHUNK];
+    uint64_t s_part[RANK_CHUNK];
+    int s_last;
+};
+
+// the body of one CTA (blockIdx.x, blockIdx.y) of the selection grid of one run
 template <typename LabT>
-__global__ void __launch_bounds__(RANK_CHUNK)
-    select_kernel(const double *__restrict__ L, SelectCfg cfg, int *__restrict__ rank,
-                  int32_t *__restrict__ perm, uint64_t *__restrict__ work_prefix,
-                  unsigned *__restrict__ ticket, DevState *st, double *__restrict__ hist,
-                  const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
-                  unsigned long long *__restrict__ ts)
+__device__ __forceinline__ void select_cta(const double *__restrict__ L, const SelectCfg &cfg,
+                                           int *__restrict__ rank, int32_t *__restrict__ perm,
+                                           uint64_t *__restrict__ work_prefix,
+                                           unsigned *__restrict__ ticket, DevState *st,
+                                           double *__restrict__ hist, const LabT *pop0,
+                                           const LabT *pop1, LabT *__restrict__ ring,
+                                           unsigned long long *__restrict__ ts, SelectSmem &sm)
 {
     if (st && st->done) return;
     const int P = cfg.P;
-    __shared__ unsigned long long sk[RANK_CHUNK];
-    __shared__ int si[RANK_CHUNK];
-    __shared__ int s_last;
-    __shared__ uint64_t s_part[RANK_CHUNK];
+    unsigned long long *sk = sm.sk;
+    int *si = sm.si;
+    int &s_last = sm.s_last;
+    uint64_t *s_part = sm.s_part;
     const int tid = threadIdx.x, nt = blockDim.x;
     {
         const int jy = blockIdx.y * RANK_CHUNK + tid;
@@ -306,6 +315,51 @@ __global__ void __launch_bounds__(RANK_CHUNK)
     }
     __syncthreads();
     for (int r = lo; r < hi; ++r) work_prefix[r] += s_part[tid];
+}
+
+template <typename LabT>
+__global__ void __launch_bounds__(RANK_CHUNK)
+    select_kernel(const double *__restrict__ L, SelectCfg cfg, int *__restrict__ rank,
+                  int32_t *__restrict__ perm, uint64_t *__restrict__ work_prefix,
+                  unsigned *__restrict__ ticket, DevState *st, double *__restrict__ hist,
+                  const LabT *pop0, const LabT *pop1, LabT *__restrict__ ring,
+                  unsigned long long *__restrict__ ts)
+{
+    __shared__ SelectSmem sm;
+    select_cta<LabT>(L, cfg, rank, perm, work_prefix, ticket, st, hist, pop0, pop1, ring, ts, sm);
+}
+
+// Selection of every active run of a fleet: CTA (x, y, z) plays CTA (x, y) of
+// the runs at table positions z, z + gridDim.z, ... < hdr->nruns in turn (the
+// per-run tickets never make a CTA wait, so the order is free).
+__global__ void __launch_bounds__(RANK_CHUNK)
+    fleet_select_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
+                        SelectCfg cfg)
+{
+    __shared__ SelectSmem sm;
+    const int nruns = hdr->nruns;
+    for (int z = blockIdx.z; z < nruns; z += gridDim.z) {
+        const FleetRun &r = runs[z];
+        SelectCfg c = cfg;
+        c.N = r.N;
+        c.ldp = r.Np;
+        select_cta<uint16_t>(r.L, c, r.rank, r.perm, r.work_prefix, r.ticket, r.st, r.hist,
+                             r.pop0, r.pop1, nullptr, nullptr, sm);
+        __syncthreads(); // shared memory is reused by the next run
+    }
+}
+
+int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectCfg &cfg,
+                        int cap, cudaStream_t s)
+{
+    const int nc = (cfg.P + RANK_CHUNK - 1) / RANK_CHUNK;
+    // at most ~4096 CTAs in flight, the rest of the runs taken in turn
+    int z = 4096 / (nc * nc);
+    if (z < 1) z = 1;
+    if (z > cap) z = cap;
+    fleet_select_kernel<<<dim3(nc, nc, z), RANK_CHUNK, 0, s>>>(runs, hdr, cfg);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
 }
 
 template <typename LabT>

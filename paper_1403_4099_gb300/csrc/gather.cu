@@ -206,26 +206,17 @@ __global__ void __launch_bounds__(256)
 // the evolve kernel does (elite copy, or SUS parents + crossover + mutation)
 // into global memory and its shared slice, then scores it.
 // ---------------------------------------------------------------------------
+// one slot of the next population (all lanes of the warp call)
 template <typename LabT>
-__global__ void __launch_bounds__(256)
-    gather_generation_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1,
-                             EvolveCfg cfg, const int32_t *__restrict__ perm,
-                             const uint64_t *__restrict__ prefix, int Np,
-                             const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
-                             const double *__restrict__ logtab,
-                             double *__restrict__ L, const DevState *__restrict__ st,
-                             unsigned long long *__restrict__ pairs)
+__device__ __forceinline__ void generation_slot(const LabT *cur, LabT *nxt, const EvolveCfg &cfg,
+                                                int g, uint32_t k0, uint32_t k1, int slot,
+                                                const int32_t *__restrict__ perm,
+                                                const uint64_t *__restrict__ prefix, int Np,
+                                                const int32_t *__restrict__ Dfix, int diag,
+                                                const double *__restrict__ logtab,
+                                                double *__restrict__ L, const GatherSlice &sl,
+                                                int lane, unsigned long long *pairs_out)
 {
-    if (st->done) return;
-    const int g = st->gen;
-    const uint32_t k0 = st->k0, k1 = st->k1;
-    const LabT *cur = (g & 1) ? pop1 : pop0;
-    LabT *nxt = (g & 1) ? next1 : next0;
-    extern __shared__ unsigned char smem_g[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int slot = blockIdx.x * nw + warp;
-    if (slot >= cfg.P) return;
-    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
     const int N = cfg.N, ldp = cfg.ldp;
     LabT *dst = nxt + (size_t)slot * ldp;
     if (slot < cfg.E) {
@@ -241,10 +232,67 @@ __global__ void __launch_bounds__(256)
                           lane);
     }
     __syncwarp();
-    const double v = gather_score_warp(sl, N, Np, Dfix, *diag_flag,
+    const double v = gather_score_warp(sl, N, Np, Dfix, diag,
                                        reinterpret_cast<const long long *>(logtab), kfix_of(logtab),
-                                       lane, pairs ? pairs + g + 1 : nullptr);
+                                       lane, pairs_out);
     if (lane == 0) L[slot] = v;
+}
+
+template <typename LabT>
+__global__ void __launch_bounds__(256)
+    gather_generation_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1,
+                             EvolveCfg cfg, const int32_t *__restrict__ perm,
+                             const uint64_t *__restrict__ prefix, int Np,
+                             const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
+                             const double *__restrict__ logtab,
+                             double *__restrict__ L, const DevState *__restrict__ st,
+                             unsigned long long *__restrict__ pairs)
+{
+    if (st->done) return;
+    const int g = st->gen;
+    const LabT *cur = (g & 1) ? pop1 : pop0;
+    LabT *nxt = (g & 1) ? next1 : next0;
+    extern __shared__ unsigned char smem_g[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int slot = blockIdx.x * nw + warp;
+    if (slot >= cfg.P) return;
+    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
+    generation_slot<LabT>(cur, nxt, cfg, g, st->k0, st->k1, slot, perm, prefix, Np, Dfix,
+                          *diag_flag, logtab, L, sl, lane, pairs ? pairs + g + 1 : nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Fleet generation: work item i is slot i mod P of the run at table position
+// i / P (the table is ordered by decreasing N, so the costly runs start
+// first); the CTAs stride over the items. Runs whose state is done are
+// skipped. Per slot the work is exactly that of gather_generation_kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512)
+    fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
+                            EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
+                            const double *__restrict__ logtab, int Np_max, int prop)
+{
+    extern __shared__ unsigned char smem_g[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max);
+    const int nitems = hdr->nitems, P = base.P;
+    for (int item = blockIdx.x * nw + warp; item < nitems; item += gridDim.x * nw) {
+        const int ri = item / P, slot = item - ri * P;
+        const FleetRun &r = runs[ri];
+        const DevState *st = r.st;
+        if (st->done) continue;
+        const int g = st->gen;
+        EvolveCfg cfg = base;
+        cfg.N = r.N;
+        cfg.ldp = r.Np;
+        const uint16_t *cur = (g & 1) ? r.pop1 : r.pop0;
+        uint16_t *nxt = (g & 1) ? r.pop0 : r.pop1;
+        const uint64_t *prefix = prop ? r.work_prefix : rank_prefix;
+        const GatherSlice sl = gather_slice(slice, r.Np);
+        generation_slot<uint16_t>(cur, nxt, cfg, g, st->k0, st->k1, slot, r.perm, prefix, r.Np,
+                                  r.Dfix, *r.diag, logtab, r.L, sl, lane, nullptr);
+        __syncwarp();
+    }
 }
 
 static int warps_for(int Np)
@@ -288,6 +336,33 @@ int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const 
     return GPGA_OK;
 }
 
+int fleet_max_warps(int Np_max)
+{
+    int nw = 16;
+    while (nw > 1 && nw * gather_slice_bytes(Np_max) > (size_t)200 * 1024) nw >>= 1;
+    return nw;
+}
+
+int fleet_ctas_per_sm(int Np_max, int warps, int *out)
+{
+    GPGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        out, fleet_generation_kernel, 32 * warps, warps * gather_slice_bytes(Np_max)));
+    return GPGA_OK;
+}
+
+int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
+                            const uint64_t *rank_prefix, const double *logtab, int Np_max,
+                            int warps, int ctas, int prop, cudaStream_t s)
+{
+    if (warps < 1 || warps > 16 || ctas < 1)
+        return set_error(GPGA_ERR_ARG, "fleet generation: %d warps x %d CTAs", warps, ctas);
+    const size_t smem = warps * gather_slice_bytes(Np_max);
+    fleet_generation_kernel<<<ctas, 32 * warps, smem, s>>>(runs, hdr, cfg, rank_prefix, logtab,
+                                                           Np_max, prop);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
 template int launch_gather_score<uint16_t>(const uint16_t *const *, int, int, int, int, int,
                                            const int32_t *, const int *, const double *, double *,
                                            int *, const DevState *, unsigned long long *,
@@ -308,6 +383,7 @@ int prepare_gather_kernels(int maxsmem)
     if (int rc = raise_smem(gather_score_kernel<uint16_t>, maxsmem)) return rc;
     if (int rc = raise_smem(gather_score_kernel<int32_t>, maxsmem)) return rc;
     if (int rc = raise_smem(gather_generation_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(fleet_generation_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }
 

@@ -290,6 +290,13 @@ int launch_assemble(const LabT *const *lab2, int ldl, int sel_off, const float *
                     double *L, int *err, const DevState *st, unsigned long long *pairs,
                     cudaStream_t s);
 
+// the log tables alone (length logtab_len(N)), as launch_prep_d writes them
+int launch_logtab(double *logtab, int N, cudaStream_t s);
+// one fleet run: C (ld ldc, optional column subset cols[0..N)) -> dense C64
+// (N x N) and Dfix (Np x Np) with its diagonal flag (zeroed by the caller)
+int launch_fleet_prep(const double *C, int ldc, const int32_t *cols, int N, int Np, double *C64,
+                      int32_t *Dfix, int *diag_flag, cudaStream_t s);
+
 int launch_log_selftest(const double *x, int n, double *yt, double *yc, cudaStream_t s);
 
 int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
@@ -308,6 +315,9 @@ template <typename F> inline int raise_smem(F *f, int maxsmem)
 
 // one-time per-device raise of the dynamic shared-memory limit of the kernels
 // that need more than 48 KB (outside any stream capture)
+int prepare_device();
+bool is_device_ptr(const void *p);
+int check_params(const gpga_params *p, int N);
 int prepare_score_kernels(int maxsmem);
 int prepare_ga_kernels(int maxsmem);
 int prepare_init_kernels(int maxsmem);
@@ -333,6 +343,31 @@ int rank_prefix_table(uint64_t *prefix, int P, cudaStream_t s);
 template <typename LabT>
 int launch_init_uniform(LabT *pop, int ldp, int P, int N, int K0, uint32_t k0, uint32_t k1,
                         cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Fleet: many independent GA runs (each its own C, N, population, state and
+// Philox key) advanced together, one launch per step for all of them. The
+// descriptor table lives in device memory and is read by the graphed kernels,
+// so the set of runs can change between graph launches.
+// ---------------------------------------------------------------------------
+struct FleetRun {
+    int N, Np;               // genes, padded row length of pop and Dfix
+    uint16_t *pop0, *pop1;   // P x Np label buffers (ping-pong by generation parity)
+    const int32_t *Dfix;     // Np x Np fixed-point D
+    const int *diag;         // nonzero if some D_ii != 0
+    double *L;               // P fitness values
+    int32_t *perm;           // P: index by rank
+    int *rank;               // P: zero between launches
+    unsigned *ticket;        // TICKETS: zero between launches
+    uint64_t *work_prefix;   // P: proportional-scaling prefix
+    DevState *st;            // the run's state
+    double *hist;            // max_gens + 1 best values
+};
+
+struct FleetHdr {
+    int nruns;  // active descriptors 0 .. nruns-1
+    int nitems; // nruns * P work items of the generation kernel
+};
 
 // rank (chunked sort + search, grid) + finalize (perm, stats, termination,
 // records, PROP prefix); rank[] and ticket[0 .. 1 + P/256] must be zero on
@@ -497,6 +532,20 @@ int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const 
 
 int launch_state_init(DevState *st, unsigned long long *ts0, uint32_t k0, uint32_t k1,
                       cudaStream_t s);
+
+// fleet launches: selection of every active run (grid nc x nc x cap), and the
+// fused generation over all (run, slot) items, `warps` warps per CTA, `ctas`
+// CTAs striding over the items; smem slices sized for Np_max; prop: the runs
+// use proportional scaling (their own work prefix), else the shared rank table
+int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectCfg &cfg,
+                        int cap, cudaStream_t s);
+int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
+                            const uint64_t *rank_prefix, const double *logtab, int Np_max,
+                            int warps, int ctas, int prop, cudaStream_t s);
+// largest warps per CTA whose shared-memory slices fit, and the resident CTAs
+// per SM of the fleet generation kernel at that shape
+int fleet_max_warps(int Np_max);
+int fleet_ctas_per_sm(int Np_max, int warps, int *out);
 
 // threshold initialisation (init.cu)
 int launch_mst(const double *C, int N, int32_t *edge_u, int32_t *edge_v, double *edge_w,

@@ -33,6 +33,33 @@ __device__ __forceinline__ void log_tab_entry(int k, long long *out)
     out[1] = __double2ll_rn(-log(v) * 4611686018427387904.0);
 }
 
+// the log tables (threads tid of nt): log_q62()'s table, then the per-size
+// constant of the assembly, K[n] = 1/2 (log n + (n - 1) log(n (n - 1))), in
+// fixed point 2^-44, n = 0..N
+__device__ __forceinline__ void fill_logtab(double *logtab, int N, int tid, int nt)
+{
+    for (int k = tid; k < LOG_TAB; k += nt)
+        log_tab_entry(k, reinterpret_cast<long long *>(logtab) + 2 * k);
+    long long *kfix = reinterpret_cast<long long *>(logtab + 2 * LOG_TAB);
+    for (int n = tid; n <= N; n += nt) {
+        double v = 0.0;
+        if (n >= 2) {
+            const double dn = (double)n;
+            v = 0.5 * (log(dn) + (dn - 1.0) * (log(dn) + log(dn - 1.0)));
+        }
+        kfix[n] = __double2ll_rn(v * 17592186044416.0); // 2^44
+    }
+}
+
+// D 2^30 rounded, saturated to the int32 range (D in [-2, 2))
+__device__ __forceinline__ int32_t dfix_of(double d)
+{
+    double v = rint(d * 1073741824.0);
+    if (v > 2147483647.0) v = 2147483647.0;
+    if (v < -2147483648.0) v = -2147483648.0;
+    return (int32_t)v;
+}
+
 // ---------------------------------------------------------------------------
 // D forms: D32 = fp32(1 - (C + C^T)/2), Dhi = bf16(D), Dlo = bf16(D - Dhi),
 // Dfix = int32(D 2^30), all Np x Np, zero outside N x N; and the log tables.
@@ -54,13 +81,7 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
         const float df = (float)d;
         D32[idx] = df;
         if (diag_flag && i == j && df != 0.f) *diag_flag = 1;
-        if (Dfix) {
-            // D 2^30 rounded, saturated to the int32 range (D in [-2, 2))
-            double v = rint(d * 1073741824.0);
-            if (v > 2147483647.0) v = 2147483647.0;
-            if (v < -2147483648.0) v = -2147483648.0;
-            Dfix[idx] = (int32_t)v;
-        }
+        if (Dfix) Dfix[idx] = dfix_of(d);
         if (Dhi) {
             const __nv_bfloat16 hi = __double2bfloat16(d);
             const double rem = d - (double)__bfloat162float(hi);
@@ -68,22 +89,56 @@ __global__ void prep_d_kernel(const double *__restrict__ C, int N, int ldc, int 
             Dlo[idx] = __double2bfloat16(rem);
         }
     }
-    if (logtab) {
-        // table of log_q62(), then the per-size constant of the assembly,
-        // K[n] = 1/2 (log n + (n - 1) log(n (n - 1))), in fixed point 2^-44
-        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-        for (int k = tid; k < LOG_TAB; k += nt)
-            log_tab_entry(k, reinterpret_cast<long long *>(logtab) + 2 * k);
-        long long *kfix = reinterpret_cast<long long *>(logtab + 2 * LOG_TAB);
-        for (int n = tid; n <= N; n += nt) {
-            double v = 0.0;
-            if (n >= 2) {
-                const double dn = (double)n;
-                v = 0.5 * (log(dn) + (dn - 1.0) * (log(dn) + log(dn - 1.0)));
-            }
-            kfix[n] = __double2ll_rn(v * 17592186044416.0); // 2^44
+    if (logtab)
+        fill_logtab(logtab, N, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void logtab_kernel(double *__restrict__ logtab, int N)
+{
+    fill_logtab(logtab, N, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+int launch_logtab(double *logtab, int N, cudaStream_t s)
+{
+    logtab_kernel<<<(N + 1 + 255) / 256 + 1, 256, 0, s>>>(logtab, N);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+// One fleet run's inputs: C gathered through the optional column subset into
+// a dense N x N copy (for the final re-score; C64 == nullptr when C already is
+// that copy), and the fixed-point D of the gather form with its diagonal
+// flag, element for element as prep_d_kernel.
+__global__ void fleet_prep_kernel(const double *__restrict__ C, int ldc,
+                                  const int32_t *__restrict__ cols, int N, int Np,
+                                  double *__restrict__ C64, int32_t *__restrict__ Dfix,
+                                  int *__restrict__ diag_flag)
+{
+    const size_t total = (size_t)Np * Np;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / Np), j = (int)(idx - (size_t)i * Np);
+        double d = 0.0;
+        if (i < N && j < N) {
+            const int ci = cols ? cols[i] : i, cj = cols ? cols[j] : j;
+            const double cij = C[(size_t)ci * ldc + cj], cji = C[(size_t)cj * ldc + ci];
+            if (C64) C64[(size_t)i * N + j] = cij;
+            d = 1.0 - 0.5 * (cij + cji);
         }
+        if (diag_flag && i == j && (float)d != 0.f) *diag_flag = 1;
+        Dfix[idx] = dfix_of(d);
     }
+}
+
+int launch_fleet_prep(const double *C, int ldc, const int32_t *cols, int N, int Np, double *C64,
+                      int32_t *Dfix, int *diag_flag, cudaStream_t s)
+{
+    const size_t total = (size_t)Np * Np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    fleet_prep_kernel<<<blocks, 256, 0, s>>>(C, ldc, cols, N, Np, C64, Dfix, diag_flag);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
 }
 
 int launch_prep_d(const double *C, int N, int ldc, int Np, float *D32, __nv_bfloat16 *Dhi,

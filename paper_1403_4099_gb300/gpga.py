@@ -24,7 +24,10 @@ MAX_N, MAX_P = 4096, 16384
 
 EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score", "ga_evolve",
            "ga_init", "ga_reset", "ga_step", "ga_best", "ga_history", "ga_kernel_times",
-           "ga_population", "gpga_log_selftest", "ga_score_noalloc", "ga_free"]
+           "ga_population", "gpga_log_selftest", "ga_score_noalloc", "ga_free",
+           "ga_batch_init", "ga_batch_step", "ga_batch_status", "ga_batch_best",
+           "ga_batch_tuning", "ga_batch_free", "serve_create", "serve_submit", "serve_tick",
+           "serve_result", "serve_stats", "serve_free"]
 
 
 class GpgaError(RuntimeError):
@@ -88,6 +91,22 @@ def lib() -> ct.CDLL:
             "gpga_log_selftest": (i32, [vp, i32, vp, vp, vp]),
             "ga_score_noalloc": (i32, [vp, i32, i32, i32, vp, vp, vp]),
             "ga_free": (i32, [vp]),
+            "ga_batch_init": (i32, [i32, vp, vp, vp, vp, ct.POINTER(Params), vp, vp,
+                                    ct.POINTER(vp)]),
+            "ga_batch_step": (i32, [vp, i32, ct.POINTER(i32)]),
+            "ga_batch_status": (i32, [vp, vp, vp, vp]),
+            "ga_batch_best": (i32, [vp, i32, vp, vp, ct.POINTER(i32)]),
+            "ga_batch_tuning": (i32, [vp, ct.POINTER(i32), ct.POINTER(i32),
+                                      ct.POINTER(ct.c_float)]),
+            "ga_batch_free": (i32, [vp]),
+            "serve_create": (i32, [ct.POINTER(Params), i32, i32, ct.c_size_t, vp,
+                                   ct.POINTER(vp)]),
+            "serve_submit": (i32, [vp, vp, i32, ct.c_uint64, ct.POINTER(ct.c_longlong)]),
+            "serve_tick": (i32, [vp, i32, ct.POINTER(i32), ct.POINTER(i32)]),
+            "serve_result": (i32, [vp, ct.c_longlong, vp, vp, ct.POINTER(i32), vp]),
+            "serve_stats": (i32, [vp, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
+                                  ct.POINTER(ct.c_longlong), ct.POINTER(i32), ct.POINTER(i32)]),
+            "serve_free": (i32, [vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -275,3 +294,130 @@ def _ptr(x):
     if isinstance(x, np.ndarray):
         return ct.c_void_p(x.ctypes.data)
     return ct.c_void_p(x.data_ptr())
+
+
+class Batch:
+    """Independent runs advanced together (ga_batch_*). Cs: list of device FP64
+    correlation matrices; cols: optional list of device int32 index vectors
+    (run k then works on Cs[k][cols[k]][:, cols[k]]); seeds: one per run."""
+
+    def __init__(self, Cs, params: Params, seeds, cols=None, stream=None):
+        R = len(Cs)
+        if len(seeds) != R or (cols is not None and len(cols) != R):
+            raise ValueError("Cs, seeds and cols must have the same length")
+        self.R = R
+        self.params = params
+        ptrs = (ct.c_void_p * R)(*[_dev(C, "float64").value for C in Cs])
+        ldc = (ct.c_int * R)(*[int(C.shape[1]) for C in Cs])
+        if cols is not None:
+            self.N = [int(c.shape[0]) for c in cols]
+            cptr = (ct.c_void_p * R)(*[_dev(c, "int32").value for c in cols])
+        else:
+            self.N = [int(C.shape[0]) for C in Cs]
+            cptr = None
+        Ns = (ct.c_int * R)(*self.N)
+        sd = (ct.c_uint64 * R)(*[int(s) for s in seeds])
+        h = ct.c_void_p()
+        _check(lib().ga_batch_init(R, ptrs, ldc, cptr, Ns, ct.byref(params), sd,
+                                   _stream_ptr(stream), ct.byref(h)))
+        self._h = h
+
+    def step(self, generations: int, wait: bool = True):
+        """Advance; returns the number of runs still active if wait."""
+        if wait:
+            a = ct.c_int()
+            _check(lib().ga_batch_step(self._h, int(generations), ct.byref(a)))
+            return a.value
+        _check(lib().ga_batch_step(self._h, int(generations), None))
+        return None
+
+    def status(self):
+        g = np.zeros(self.R, np.int32)
+        d = np.zeros(self.R, np.int32)
+        b = np.zeros(self.R, np.float64)
+        _check(lib().ga_batch_status(self._h, g.ctypes.data, d.ctypes.data, b.ctypes.data))
+        return g, d.astype(bool), b
+
+    def best(self, run: int):
+        lab = np.zeros(self.N[run], np.int32)
+        Lb = np.zeros(1, np.float64)
+        g = ct.c_int()
+        _check(lib().ga_batch_best(self._h, int(run), lab.ctypes.data, Lb.ctypes.data,
+                                   ct.byref(g)))
+        return lab, float(Lb[0]), g.value
+
+    def tuning(self):
+        w, c, ms = ct.c_int(), ct.c_int(), ct.c_float()
+        _check(lib().ga_batch_tuning(self._h, ct.byref(w), ct.byref(c), ct.byref(ms)))
+        return dict(warps_per_cta=w.value, ctas=c.value, ms=float(ms.value))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ga_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving loop (serve_*): submit host correlation windows, tick, collect."""
+
+    def __init__(self, params: Params, max_runs: int, max_n: int, mem_budget: int = 0,
+                 stream=None):
+        self.params = params
+        self.max_n = max_n
+        self._n = {}
+        h = ct.c_void_p()
+        _check(lib().serve_create(ct.byref(params), int(max_runs), int(max_n),
+                                  ct.c_size_t(int(mem_budget)), _stream_ptr(stream), ct.byref(h)))
+        self._h = h
+
+    def submit(self, C: np.ndarray, seed: int) -> int:
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        i = ct.c_longlong()
+        _check(lib().serve_submit(self._h, C.ctypes.data, int(C.shape[0]), ct.c_uint64(seed),
+                                  ct.byref(i)))
+        self._n[i.value] = int(C.shape[0])
+        return i.value
+
+    def tick(self, generations: int):
+        a, q = ct.c_int(), ct.c_int()
+        _check(lib().serve_tick(self._h, int(generations), ct.byref(a), ct.byref(q)))
+        return a.value, q.value
+
+    def result(self, rid: int):
+        """None while pending, else (labels, L, generation, (queued_s, run_s))."""
+        lab = np.zeros(self._n.get(rid, 1), np.int32)  # unknown ids: the library reports
+        L = ct.c_double()
+        g = ct.c_int()
+        t = np.zeros(2, np.float64)
+        rc = lib().serve_result(self._h, ct.c_longlong(rid), lab.ctypes.data, ct.byref(L),
+                                ct.byref(g), t.ctypes.data)
+        if rc == 0:
+            return None
+        if rc < 0:
+            _check(rc)
+        self._n.pop(rid, None)
+        return lab, L.value, g.value, (float(t[0]), float(t[1]))
+
+    def stats(self):
+        u, b, c, w, k = ct.c_size_t(), ct.c_size_t(), ct.c_longlong(), ct.c_int(), ct.c_int()
+        _check(lib().serve_stats(self._h, ct.byref(u), ct.byref(b), ct.byref(c), ct.byref(w),
+                                 ct.byref(k)))
+        return dict(bytes_in_use=u.value, budget=b.value, completed=c.value,
+                    warps_per_cta=w.value, ctas=k.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().serve_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -148,3 +148,44 @@ def perturbed_population(rng: np.random.Generator, truth: np.ndarray, P: int, fl
     mask = rng.random((P, N)) < flip
     pop[mask] = rng.integers(0, N, size=int(mask.sum()), dtype=np.int64).astype(np.int32)
     return pop
+
+
+@dataclass
+class Intraday:
+    R: np.ndarray          # T x N float64 one-minute returns
+    truth_before: np.ndarray  # N int32 labels of the first regime (noise: singletons)
+    truth_after: np.ndarray   # N int32 labels of the second regime
+    switch: int            # first minute of the second regime
+
+
+def intraday(N: int = 400, windows: int = 256, W: int = 390, stride: int = 30,
+             k_before: int = 12, k_after: int = 9, replicate: int = 0) -> Intraday:
+    """An intraday series of W + (windows - 1) stride one-minute returns over N
+    stocks whose planted structure switches at the midpoint: k_before clusters
+    before, a fresh draw of k_after clusters after (g ~ U[0.2, 0.8], market
+    loading 0.3, 10% singleton noise series in each regime)."""
+    rng = np.random.default_rng(seed_for(4, replicate))
+    T = W + (windows - 1) * stride
+    sw = T // 2
+    n_noise = int(round(0.1 * N))
+    parts = []
+    truths = []
+    for k, T_part in ((k_before, sw), (k_after, T - sw)):
+        sizes = dirichlet_sizes(rng, N - n_noise, k)
+        g = rng.uniform(0.2, 0.8, size=k)
+        pl = planted_returns(rng, T_part, sizes, g, n_noise=n_noise, beta=0.3)
+        parts.append(pl.R)
+        truths.append(pl.truth)
+    return Intraday(np.ascontiguousarray(np.vstack(parts)), truths[0], truths[1], sw)
+
+
+def window_subsets(N: int, windows: int, nmin: int = 20, nmax: int | None = None,
+                   replicate: int = 0) -> list:
+    """Per window a sorted random column subset of size N_k ~ U{nmin..nmax}."""
+    rng = np.random.default_rng(seed_for(4, 500 + replicate))
+    nmax = N if nmax is None else nmax
+    out = []
+    for _ in range(windows):
+        n = int(rng.integers(nmin, nmax + 1))
+        out.append(np.sort(rng.choice(N, size=n, replace=False)).astype(np.int32))
+    return out
