@@ -34,6 +34,7 @@ WORKLOAD = "planted_n500_t5000_p4096"
 METRIC = "fitness evals/s (N=500, P=4096; step = Pearson prelude + init + G generations)"
 SMS = 152
 ALU_LANES = 128
+GRAPH_GENS = 8  # generations per captured graph in ga_step
 
 
 def parse():
@@ -266,7 +267,8 @@ def run_gpu(args, ranks):
         # K = Np, two MMAs (D_hi, D_lo) of 2 M N K FLOPs each
         Np = (N + 63) // 64 * 64
         NTt = min(256, Np)
-        cols = float(np.mean(hist["clusters"][1:])) if len(hist["clusters"]) > 1 else 0.0
+        tg = G if G % GRAPH_GENS else G - GRAPH_GENS + 1  # the timed generation
+        cols = float(hist["clusters"][tg]) if tg < len(hist["clusters"]) else 0.0
         n_ct = int(np.ceil(cols / 128.0))
         flops = n_ct * int(np.ceil(Np / NTt)) * 2 * 2.0 * 128 * NTt * Np
         t = main_ms / 1e3
@@ -279,9 +281,12 @@ def run_gpu(args, ranks):
                 "issued_mma_flops_per_launch": flops, "columns_per_launch": cols,
                 "launch_ms": main_ms}
     elif form == gpga.FORM_GATHER:
+        # the timed launch is the first generation of the step's last graph
+        # launch (graphs of GRAPH_GENS generations, then single generations)
+        tg = G if G % GRAPH_GENS else G - GRAPH_GENS + 1
         pairs = hist["pairs"]
-        roof = gather_roofline(main_ms, pk, pk_kind,
-                               float(np.mean(pairs[1:])) if len(pairs) > 1 else 0.0)
+        roof = gather_roofline(main_ms, pk, pk_kind, float(pairs[tg]) if tg < len(pairs) else 0.0)
+        roof["timed_generation"] = int(tg)
     else:
         roof = None  # filled by the tensor form
 
@@ -591,7 +596,12 @@ def run_serving(args, ranks):
                 "evals_per_s": evals / wall,
                 "generations_mean": float(np.mean(gens)),
                 "active_runs": {"mean": float(np.mean(active_hist)), "max": int(max(active_hist))},
-                "launch_shape": {"warps_per_cta": st["warps_per_cta"], "ctas": st["ctas"]}}
+                "launch_shape": {"warps_per_cta": st["warps_per_cta"], "ctas": st["ctas"]},
+                "ticks": st["ticks"], "generations_per_tick": 8,
+                "host_s": {"waiting_for_gpu": st["host_wait_s"], "tick_work": st["host_work_s"]},
+                "gpu_generation_graphs_s": st["gpu_ms"] / 1e3,
+                "individual_generations_per_gpu_s": (st["item_gens"] / (st["gpu_ms"] / 1e3)
+                                                     if st["gpu_ms"] > 0 else None)}
         print(json.dumps(line), flush=True)
     runtime.barrier(ranks)
 

@@ -214,9 +214,10 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
  * the generations run by the most recent graph launch of ga_step, available
  * when params.profile != 0. Row g of ms (count x 4, count <= cap) holds
  * [evolve (gather form: the fused generation kernel), pair accumulation
- * (plain) or contraction (tensor), assembly, selection]; with profile = 1 only
- * the dominant kernel's entry is measured (the others are 0). Waits for the
- * stream. GPGA_ERR_STATE without profile.
+ * (plain) or contraction (tensor), assembly, selection]. With profile = 1 only
+ * the first generation of each graph launch is timed, and only its dominant
+ * kernel (the other entries are 0; count is 1); with profile = 2 every stage
+ * of every generation. Waits for the stream. GPGA_ERR_STATE without profile.
  */
 GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count);
 
@@ -338,12 +339,15 @@ GPGA_API int serve_create(const gpga_params *p, int max_runs, int max_n, size_t 
  * (copied), 2 <= N <= max_n; *id receives the request's id. No GPU work. */
 GPGA_API int serve_submit(gpga_server *h, const double *C, int N, uint64_t seed, long long *id);
 
-/* serve_tick -- one turn of the loop: wait for the previous turn's work,
- * retire terminated runs (FP64 re-score, results to the host, memory freed),
- * admit queued requests while slots and memory allow, then launch
- * `generations` generations of every admitted run and return without waiting
- * for them. active/queued (optional): runs on the device and requests
- * waiting after admission. */
+/* serve_tick -- one turn k of the loop: wait until the GPU has finished
+ * turn k-2, collect the results copied out at turn k-1, retire the runs turn
+ * k-2 left terminated (FP64 re-score and copy-out enqueued, memory freed in
+ * stream order), admit queued requests while slots and memory allow, then
+ * enqueue `generations` generations of every admitted run and return without
+ * waiting for them: the GPU works on turn k-1 while the host prepares turn k.
+ * A result is collected two or three turns after its run terminates.
+ * active/queued (optional): runs in this turn's table and requests still
+ * waiting. */
 GPGA_API int serve_tick(gpga_server *h, int generations, int *active, int *queued);
 
 /* serve_result -- 1 and the result if request `id` has finished (labels:
@@ -355,9 +359,12 @@ GPGA_API int serve_result(gpga_server *h, long long id, int32_t *labels, double 
                           int *generation, double *times);
 
 /* serve_stats -- run memory in use, the budget, requests completed so far,
- * and the generation kernel's launch shape (each optional). */
+ * the generation kernel's launch shape, and timing (host, 6 doubles: ticks,
+ * host seconds waiting for the GPU, host seconds of tick work, GPU ms of the
+ * generation graphs of ticks already waited for, fleet generations launched,
+ * sum over those generations of the work items); each optional. */
 GPGA_API int serve_stats(gpga_server *h, size_t *bytes_in_use, size_t *budget,
-                         long long *completed, int *warps_per_cta, int *ctas);
+                         long long *completed, int *warps_per_cta, int *ctas, double *timing);
 
 /* serve_free -- release the server, its queue, results and device memory. */
 GPGA_API int serve_free(gpga_server *h);

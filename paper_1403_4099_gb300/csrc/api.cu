@@ -350,8 +350,13 @@ int build_graph(gpga_ga *h, int gens, cudaGraphExec_t *out)
     }
     GPGA_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = GPGA_OK;
+    // profile 1 times the dominant kernel of the graph's first generation only
+    // (each event node costs about 2 us of the step); profile 2 every stage of
+    // every generation
     for (int k = 0; k < gens && rc == GPGA_OK; ++k)
-        rc = enqueue_generation(h, h->prm.profile ? evs[k] : nullptr);
+        rc = enqueue_generation(h, (h->prm.profile >= 2 || (h->prm.profile == 1 && k == 0))
+                                       ? evs[k]
+                                       : nullptr);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -698,7 +703,8 @@ GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count)
     if (!h || !ms) return set_error(GPGA_ERR_ARG, "ga_kernel_times: NULL argument");
     if (!h->prm.profile) return set_error(GPGA_ERR_STATE, "ga_kernel_times: run created with profile = 0");
     GPGA_CUDA(cudaStreamSynchronize(h->stream));
-    const int n = h->last_graph < cap ? h->last_graph : cap;
+    const int timed = h->prm.profile >= 2 ? h->last_graph : (h->last_graph ? 1 : 0);
+    const int n = timed < cap ? timed : cap;
     cudaEvent_t(*evs)[gpga_ga::NEV] = h->last_graph == 1 ? h->ev1 : h->evU;
     for (int k = 0; k < n; ++k)
         for (int e = 0; e < 4; ++e) {

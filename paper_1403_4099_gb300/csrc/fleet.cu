@@ -57,7 +57,7 @@ struct RunMem {
 
 struct Slot {
     bool used = false;
-    bool stepped = false; // part of the table when the last status copy was taken
+    long long since = -1; // first tick whose run table holds this run (-1: not yet)
     int N = 0;
     uint64_t seed = 0;
     long long id = -1;
@@ -80,14 +80,18 @@ struct Fleet {
     FleetRun *d_runs = nullptr;
     FleetHdr *d_hdr = nullptr;
     DevState *d_st = nullptr;      // cap states, indexed by slot
-    FleetRun *h_runs = nullptr;    // pinned mirrors
-    FleetHdr *h_hdr = nullptr;
-    DevState *h_st = nullptr;
+    // pinned mirrors, two of each: a serving tick fills one while the copies
+    // of the previous tick may still read the other
+    FleetRun *h_runs[2] = {nullptr, nullptr};
+    FleetHdr *h_hdr[2] = {nullptr, nullptr};
+    DevState *h_st[2] = {nullptr, nullptr};
     std::vector<Slot> slots;
-    int nactive = 0;
+    int nactive = 0, nitems = 0;
     int warps = 0, ctas = 0;
     float tune_ms = 0.f;
-    bool flat = false;
+    bool flat_ok = false;    // a grid sized to the items is allowed (fixed set of runs)
+    long long tune_items = 0; // work items when the shape was last tuned
+    bool retune = false;      // tune again when the items double
     cudaGraphExec_t gU = nullptr, g1 = nullptr;
     int U = 8;
 };
@@ -169,9 +173,11 @@ static void fleet_destroy(Fleet *f)
         if (s.m.block) cudaFreeAsync(s.m.block, f->stream);
     if (f->shared) cudaFreeAsync(f->shared, f->stream);
     if (f->stream) cudaStreamSynchronize(f->stream);
-    if (f->h_runs) cudaFreeHost(f->h_runs);
-    if (f->h_hdr) cudaFreeHost(f->h_hdr);
-    if (f->h_st) cudaFreeHost(f->h_st);
+    for (int b = 0; b < 2; ++b) {
+        if (f->h_runs[b]) cudaFreeHost(f->h_runs[b]);
+        if (f->h_hdr[b]) cudaFreeHost(f->h_hdr[b]);
+        if (f->h_st[b]) cudaFreeHost(f->h_st[b]);
+    }
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
     delete f;
 }
@@ -229,15 +235,17 @@ static int fleet_create(const gpga_params *p, int cap, int Nmax, void *stream, F
             f->d_st = ds;
         }
     }
-    if (cudaMallocHost((void **)&f->h_runs, (size_t)cap * sizeof(FleetRun)) != cudaSuccess ||
-        cudaMallocHost((void **)&f->h_hdr, sizeof(FleetHdr)) != cudaSuccess ||
-        cudaMallocHost((void **)&f->h_st, (size_t)cap * sizeof(DevState)) != cudaSuccess) {
-        fleet_destroy(f);
-        return set_error(GPGA_ERR_OOM, "fleet: pinned host allocation");
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMallocHost((void **)&f->h_runs[b], (size_t)cap * sizeof(FleetRun)) != cudaSuccess ||
+            cudaMallocHost((void **)&f->h_hdr[b], sizeof(FleetHdr)) != cudaSuccess ||
+            cudaMallocHost((void **)&f->h_st[b], (size_t)cap * sizeof(DevState)) != cudaSuccess) {
+            fleet_destroy(f);
+            return set_error(GPGA_ERR_OOM, "fleet: pinned host allocation");
+        }
+        memset(f->h_st[b], 0, (size_t)cap * sizeof(DevState));
+        f->h_hdr[b]->nruns = 0;
+        f->h_hdr[b]->nitems = 0;
     }
-    memset(f->h_st, 0, (size_t)cap * sizeof(DevState));
-    f->h_hdr->nruns = 0;
-    f->h_hdr->nitems = 0;
     rc = rank_prefix_table(f->rank_prefix, f->P, f->stream);
     if (!rc) rc = launch_logtab(f->logtab, Nmax, f->stream);
     if (!rc && cudaMemsetAsync(f->d_hdr, 0, sizeof(FleetHdr), f->stream) != cudaSuccess)
@@ -313,24 +321,27 @@ static void fleet_release_run(Fleet *f, int slot)
     s = Slot{};
 }
 
-// the run table: used slots by decreasing N (ties by slot), and the header
-static int fleet_upload(Fleet *f)
+// the run table: used slots by decreasing N (ties by slot), and the header,
+// from pinned mirror `b`; runs entering the table are stamped with `tick`
+static int fleet_upload(Fleet *f, int b, long long tick)
 {
     std::vector<int> order;
     for (int i = 0; i < f->cap; ++i)
         if (f->slots[i].used) order.push_back(i);
     std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return f->slots[a].N > f->slots[b].N; });
-    for (size_t k = 0; k < order.size(); ++k) f->h_runs[k] = f->slots[order[k]].m.d;
+                     [&](int a, int c) { return f->slots[a].N > f->slots[c].N; });
+    for (size_t k = 0; k < order.size(); ++k) f->h_runs[b][k] = f->slots[order[k]].m.d;
     f->nactive = (int)order.size();
-    f->h_hdr->nruns = f->nactive;
-    f->h_hdr->nitems = f->nactive * f->P;
+    f->nitems = f->nactive * f->P;
+    f->h_hdr[b]->nruns = f->nactive;
+    f->h_hdr[b]->nitems = f->nitems;
     if (f->nactive)
-        GPGA_CUDA(cudaMemcpyAsync(f->d_runs, f->h_runs, (size_t)f->nactive * sizeof(FleetRun),
+        GPGA_CUDA(cudaMemcpyAsync(f->d_runs, f->h_runs[b], (size_t)f->nactive * sizeof(FleetRun),
                                   cudaMemcpyHostToDevice, f->stream));
-    GPGA_CUDA(cudaMemcpyAsync(f->d_hdr, f->h_hdr, sizeof(FleetHdr), cudaMemcpyHostToDevice,
+    GPGA_CUDA(cudaMemcpyAsync(f->d_hdr, f->h_hdr[b], sizeof(FleetHdr), cudaMemcpyHostToDevice,
                               f->stream));
-    for (int i : order) f->slots[i].stepped = true;
+    for (int i : order)
+        if (f->slots[i].since < 0) f->slots[i].since = tick;
     return GPGA_OK;
 }
 
@@ -345,16 +356,15 @@ static int fleet_gen_launch(Fleet *f, int warps, int ctas)
 // generation kernel, timed on the fleet's current runs. The kernel is
 // idempotent between selections (it rewrites the next population and its
 // fitness from the same parents and Philox counters), so the trials leave the
-// runs' results unchanged. flat_ok: also try one warp per work item (a grid
-// that depends on the number of items, for a fixed set of runs).
-static int fleet_tune(Fleet *f, bool flat_ok)
+// runs' results unchanged. Shapes: 1, 2 or 4 waves of resident CTAs striding
+// over the items and, when f->flat_ok (a fixed set of runs), one warp per item.
+static int fleet_tune(Fleet *f)
 {
     int sms = 0;
     GPGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->dev));
     const int wmax = fleet_max_warps(f->Np_max);
     struct Cand {
         int warps, ctas;
-        bool flat;
     };
     std::vector<Cand> cands;
     for (int w = 2; w <= wmax; w <<= 1) {
@@ -362,25 +372,26 @@ static int fleet_tune(Fleet *f, bool flat_ok)
         int rc = fleet_ctas_per_sm(f->Np_max, w, &occ);
         if (rc) return rc;
         if (occ < 1) continue;
-        cands.push_back({w, sms * occ, false});
-        if (flat_ok && f->h_hdr->nitems > 0) {
-            const int flat = (f->h_hdr->nitems + w - 1) / w;
-            if (flat > sms * occ) cands.push_back({w, flat, true});
-        }
+        const int flat = (f->nitems + w - 1) / w;
+        for (int waves = 1; waves <= 4; waves <<= 1)
+            if (waves == 1 || sms * occ * waves < flat) cands.push_back({w, sms * occ * waves});
+        if (f->flat_ok && flat > sms * occ) cands.push_back({w, flat});
     }
     if (cands.empty()) return set_error(GPGA_ERR_ARG, "fleet: no launch shape fits N=%d", f->Nmax);
+    if (f->nactive == 0) { // nothing to time: the widest one-wave shape
+        for (const Cand &c : cands)
+            if (c.ctas <= sms * 64) {
+                f->warps = c.warps;
+                f->ctas = c.ctas;
+            }
+        return GPGA_OK;
+    }
     cudaEvent_t e0, e1;
     GPGA_CUDA(cudaEventCreate(&e0));
     GPGA_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int rc = GPGA_OK;
     for (const Cand &c : cands) {
-        if (f->nactive == 0) { // nothing to time: take the largest persistent shape
-            f->warps = c.warps;
-            f->ctas = c.ctas;
-            f->flat = false;
-            continue;
-        }
         rc = fleet_gen_launch(f, c.warps, c.ctas); // warm-up
         if (rc) break;
         cudaEventRecord(e0, f->stream);
@@ -398,12 +409,12 @@ static int fleet_tune(Fleet *f, bool flat_ok)
             best = ms;
             f->warps = c.warps;
             f->ctas = c.ctas;
-            f->flat = c.flat;
             f->tune_ms = ms;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    f->tune_items = f->nitems;
     return rc;
 }
 
@@ -433,9 +444,12 @@ static int fleet_step(Fleet *f, int generations)
 {
     if (generations <= 0 || f->nactive == 0) return GPGA_OK;
     int rc;
-    if (!f->warps) {
-        rc = fleet_tune(f, false);
+    if (!f->warps || (f->retune && f->nitems > 2 * f->tune_items)) {
+        rc = fleet_tune(f);
         if (rc) return rc;
+        if (f->gU) cudaGraphExecDestroy(f->gU);
+        if (f->g1) cudaGraphExecDestroy(f->g1);
+        f->gU = f->g1 = nullptr;
     }
     if (generations >= f->U && !f->gU) {
         rc = fleet_graph(f, f->U, &f->gU);
@@ -453,7 +467,7 @@ static int fleet_step(Fleet *f, int generations)
 
 static int fleet_status(Fleet *f)
 {
-    GPGA_CUDA(cudaMemcpyAsync(f->h_st, f->d_st, (size_t)f->cap * sizeof(DevState),
+    GPGA_CUDA(cudaMemcpyAsync(f->h_st[0], f->d_st, (size_t)f->cap * sizeof(DevState),
                               cudaMemcpyDeviceToHost, f->stream));
     GPGA_CUDA(cudaStreamSynchronize(f->stream));
     return GPGA_OK;
@@ -508,8 +522,9 @@ GPGA_API int ga_batch_init(int runs, const double *const *C, const int *ldc,
         f->slots[k].seed = seeds[k];
         rc = fleet_start(f, k, C[k], ldc ? ldc[k] : N[k], cols ? cols[k] : nullptr, N[k], seeds[k]);
     }
-    if (!rc) rc = fleet_upload(f);
-    if (!rc) rc = fleet_tune(f, true);
+    f->flat_ok = true;
+    if (!rc) rc = fleet_upload(f, 0, 0);
+    if (!rc) rc = fleet_tune(f);
     if (!rc) rc = fleet_status(f);
     if (rc) {
         fleet_destroy(f);
@@ -536,7 +551,7 @@ GPGA_API int ga_batch_step(gpga_batch *h, int generations, int *active)
         rc = fleet_status(h->f);
         if (rc) return rc;
         int a = 0;
-        for (int k = 0; k < h->runs; ++k) a += h->f->h_st[k].done ? 0 : 1;
+        for (int k = 0; k < h->runs; ++k) a += h->f->h_st[0][k].done ? 0 : 1;
         *active = a;
     }
     return GPGA_OK;
@@ -548,7 +563,7 @@ GPGA_API int ga_batch_status(gpga_batch *h, int32_t *generation, int32_t *done, 
     int rc = fleet_status(h->f);
     if (rc) return rc;
     for (int k = 0; k < h->runs; ++k) {
-        const DevState &s = h->f->h_st[k];
+        const DevState &s = h->f->h_st[0][k];
         if (generation) generation[k] = s.gen;
         if (done) done[k] = s.done;
         if (best) best[k] = s.best;
@@ -576,7 +591,7 @@ GPGA_API int ga_batch_best(gpga_batch *h, int run, int32_t *labels, double *L, i
                                   f->stream));
     rc = fleet_status(f);
     if (rc) return rc;
-    if (generation) *generation = f->h_st[run].gen;
+    if (generation) *generation = f->h_st[0][run].gen;
     return GPGA_OK;
 }
 
@@ -601,6 +616,14 @@ GPGA_API int ga_batch_free(gpga_batch *h)
 
 // ---------------------------------------------------------------------------
 // serving
+//
+// A tick k, on the host: wait until the GPU has finished tick k-2 (its status
+// copy), collect the results copied out at tick k-1, retire the runs that
+// tick k-2 left terminated (FP64 re-score and copy-out enqueued, memory freed
+// in stream order), admit queued requests, upload the run table and launch the
+// generations of tick k, then the status copy. The GPU runs tick k-1 while the
+// host prepares tick k, so it never waits for the host; results come back two
+// to three ticks after their run terminates.
 // ---------------------------------------------------------------------------
 struct gpga_server {
     Fleet *f = nullptr;
@@ -609,6 +632,7 @@ struct gpga_server {
     size_t reserve = 0;    // device memory always left free
     long long next_id = 0;
     long long completed = 0;
+    long long tick = 0;
     struct Req {
         long long id;
         int N;
@@ -625,56 +649,92 @@ struct gpga_server {
     };
     std::unordered_map<long long, Result> results;
     std::unordered_map<long long, int> running; // id -> slot
+    // results in flight: copied at tick t into the pinned arena, collected at t+1
+    struct Out {
+        long long id;
+        int slot, N, gen;
+        std::chrono::steady_clock::time_point t_submit, t_admit;
+    };
+    std::vector<Out> out[2];
+    int32_t *arena_lab = nullptr; // pinned, cap x Nmax
+    double *arena_L = nullptr;    // pinned, cap
+    double *stage[2] = {nullptr, nullptr}; // pinned request matrices of a tick
+    size_t stage_cap[2] = {0, 0};
+    cudaEvent_t ev_status[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_g0[2] = {nullptr, nullptr}, ev_g1[2] = {nullptr, nullptr};
+    bool g_timed[2] = {false, false};
+    // counters
+    double gpu_ms = 0.0;          // device time of the generation graphs
+    long long gens = 0;           // fleet generations launched
+    long long item_gens = 0;      // sum over launched generations of the work items
+    double host_wait_s = 0.0, host_work_s = 0.0;
 };
 
 namespace {
 
-// retire the runs that were stepped and have terminated: FP64 re-score,
-// copy-out, free their memory
-int serve_retire(gpga_server *h)
+void serve_release(gpga_server *h)
+{
+    if (!h) return;
+    if (h->f) fleet_destroy(h->f); // synchronises the stream
+    for (int b = 0; b < 2; ++b) {
+        if (h->stage[b]) cudaFreeHost(h->stage[b]);
+        if (h->ev_status[b]) cudaEventDestroy(h->ev_status[b]);
+        if (h->ev_out[b]) cudaEventDestroy(h->ev_out[b]);
+        if (h->ev_g0[b]) cudaEventDestroy(h->ev_g0[b]);
+        if (h->ev_g1[b]) cudaEventDestroy(h->ev_g1[b]);
+    }
+    if (h->arena_lab) cudaFreeHost(h->arena_lab);
+    if (h->arena_L) cudaFreeHost(h->arena_L);
+    delete h;
+}
+
+// move the results copied out at the previous tick (its copies are complete)
+void serve_collect(gpga_server *h, int b)
+{
+    const auto now = std::chrono::steady_clock::now();
+    const int Nmax = h->f->Nmax;
+    for (const gpga_server::Out &o : h->out[b]) {
+        gpga_server::Result r;
+        r.labels.assign(h->arena_lab + (size_t)o.slot * Nmax, h->arena_lab + (size_t)o.slot * Nmax + o.N);
+        r.L = h->arena_L[o.slot];
+        r.gen = o.gen;
+        r.queue_s = std::chrono::duration<double>(o.t_admit - o.t_submit).count();
+        r.run_s = std::chrono::duration<double>(now - o.t_admit).count();
+        h->results[o.id] = std::move(r);
+        h->running.erase(o.id);
+        ++h->completed;
+    }
+    h->out[b].clear();
+}
+
+// retire the runs whose status (from tick `tick` - 2, mirror b) says done:
+// FP64 re-score, copy-out into the arena, memory freed in stream order
+int serve_retire(gpga_server *h, int b)
 {
     Fleet *f = h->f;
-    std::vector<int> fin;
-    for (int i = 0; i < f->cap; ++i)
-        if (f->slots[i].used && f->slots[i].stepped && f->h_st[i].done) fin.push_back(i);
-    if (fin.empty()) return GPGA_OK;
-    std::vector<std::vector<int32_t>> lab(fin.size());
-    std::vector<double> Lb(fin.size());
-    for (size_t k = 0; k < fin.size(); ++k) {
-        const int i = fin[k];
+    const int Nmax = f->Nmax;
+    for (int i = 0; i < f->cap; ++i) {
+        Slot &s = f->slots[i];
+        if (!s.used || s.since < 0 || s.since > h->tick - 2 || !f->h_st[b][i].done) continue;
         int rc = fleet_rescore(f, i);
         if (rc) return rc;
-        lab[k].resize(f->slots[i].N);
-        GPGA_CUDA(cudaMemcpyAsync(lab[k].data(), f->slots[i].m.canon,
-                                  (size_t)f->slots[i].N * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                  f->stream));
-        GPGA_CUDA(cudaMemcpyAsync(&Lb[k], f->slots[i].m.Lbest, sizeof(double),
+        GPGA_CUDA(cudaMemcpyAsync(h->arena_lab + (size_t)i * Nmax, s.m.canon,
+                                  (size_t)s.N * sizeof(int32_t), cudaMemcpyDeviceToHost, f->stream));
+        GPGA_CUDA(cudaMemcpyAsync(h->arena_L + i, s.m.Lbest, sizeof(double),
                                   cudaMemcpyDeviceToHost, f->stream));
-    }
-    GPGA_CUDA(cudaStreamSynchronize(f->stream));
-    const auto now = std::chrono::steady_clock::now();
-    for (size_t k = 0; k < fin.size(); ++k) {
-        const int i = fin[k];
-        Slot &s = f->slots[i];
-        gpga_server::Result r;
-        r.labels = std::move(lab[k]);
-        r.L = Lb[k];
-        r.gen = f->h_st[i].gen;
-        r.queue_s = std::chrono::duration<double>(s.t_admit - s.t_submit).count();
-        r.run_s = std::chrono::duration<double>(now - s.t_admit).count();
-        h->results[s.id] = std::move(r);
-        h->running.erase(s.id);
+        h->out[b].push_back({s.id, i, s.N, f->h_st[b][i].gen, s.t_submit, s.t_admit});
         h->in_use -= s.m.bytes;
-        ++h->completed;
         fleet_release_run(f, i);
-        memset(&f->h_st[i], 0, sizeof(DevState));
     }
     return GPGA_OK;
 }
 
-int serve_admit(gpga_server *h)
+int serve_admit(gpga_server *h, int b)
 {
     Fleet *f = h->f;
+    // matrices of this tick's admissions go through pinned staging buffer b
+    // (free: tick - 2, its last user, has finished)
+    size_t staged = 0;
     while (!h->queue.empty()) {
         gpga_server::Req &q = h->queue.front();
         int slot = -1;
@@ -689,17 +749,30 @@ int serve_admit(gpga_server *h)
         size_t free_b = 0, total_b = 0;
         GPGA_CUDA(cudaMemGetInfo(&free_b, &total_b));
         if (free_b < need + h->reserve) break;
+        const size_t nn = (size_t)q.N * q.N;
+        if (staged + nn > h->stage_cap[b]) {
+            if (staged) break; // this tick's buffer is full: admit the rest next tick
+            if (h->stage[b]) cudaFreeHost(h->stage[b]);
+            h->stage[b] = nullptr;
+            h->stage_cap[b] = 0;
+            const size_t want = std::max(nn, (size_t)1 << 24);
+            GPGA_CUDA(cudaMallocHost((void **)&h->stage[b], want * sizeof(double)));
+            h->stage_cap[b] = want;
+        }
+        double *src = h->stage[b] + staged;
+        memcpy(src, q.C.data(), nn * sizeof(double));
+        staged += nn;
         int rc = fleet_alloc_run(f, slot, q.N);
         if (rc) return rc;
         Slot &s = f->slots[slot];
         s.used = true;
-        s.stepped = false;
+        s.since = -1;
         s.seed = q.seed;
         s.id = q.id;
         s.t_submit = q.t_submit;
         s.t_admit = std::chrono::steady_clock::now();
-        GPGA_CUDA(cudaMemcpyAsync(s.m.C64, q.C.data(), (size_t)q.N * q.N * sizeof(double),
-                                  cudaMemcpyHostToDevice, f->stream));
+        GPGA_CUDA(cudaMemcpyAsync(s.m.C64, src, nn * sizeof(double), cudaMemcpyHostToDevice,
+                                  f->stream));
         rc = fleet_start(f, slot, nullptr, q.N, nullptr, q.N, q.seed);
         if (rc) return rc;
         h->in_use += need;
@@ -718,20 +791,32 @@ GPGA_API int serve_create(const gpga_params *p, int max_runs, int max_n, size_t 
 {
     if (!out) return set_error(GPGA_ERR_ARG, "serve_create: out is NULL");
     *out = nullptr;
-    Fleet *f = nullptr;
-    int rc = fleet_create(p, max_runs, max_n, stream, &f);
-    if (rc) return rc;
     gpga_server *h = new (std::nothrow) gpga_server;
-    if (!h) {
-        fleet_destroy(f);
-        return set_error(GPGA_ERR_OOM, "serve_create: host allocation");
+    if (!h) return set_error(GPGA_ERR_OOM, "serve_create: host allocation");
+    int rc = fleet_create(p, max_runs, max_n, stream, &h->f);
+    if (rc) {
+        h->f = nullptr;
+        serve_release(h);
+        return rc;
     }
-    h->f = f;
+    h->f->retune = true;
+    const int Nmax = h->f->Nmax;
+    bool ok = cudaMallocHost((void **)&h->arena_lab, (size_t)max_runs * Nmax * sizeof(int32_t)) ==
+                  cudaSuccess &&
+              cudaMallocHost((void **)&h->arena_L, (size_t)max_runs * sizeof(double)) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaEventCreateWithFlags(&h->ev_status[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_out[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&h->ev_g0[b]) == cudaSuccess &&
+             cudaEventCreate(&h->ev_g1[b]) == cudaSuccess;
+    if (!ok) {
+        serve_release(h);
+        return set_error(GPGA_ERR_OOM, "serve_create: pinned memory or events");
+    }
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) {
-        fleet_destroy(f);
-        delete h;
+        serve_release(h);
         return cuda_error(e, "serve_create: cudaMemGetInfo", __FILE__, __LINE__);
     }
     h->reserve = std::min<size_t>((size_t)1 << 30, free_b / 10);
@@ -765,14 +850,41 @@ GPGA_API int serve_tick(gpga_server *h, int generations, int *active, int *queue
     if (!h) return set_error(GPGA_ERR_ARG, "serve_tick: NULL handle");
     if (generations < 0) return set_error(GPGA_ERR_ARG, "serve_tick: generations < 0");
     Fleet *f = h->f;
-    GPGA_CUDA(cudaStreamSynchronize(f->stream)); // last tick's graphs and status copy
-    int rc = serve_retire(h);
-    if (!rc) rc = serve_admit(h);
-    if (!rc) rc = fleet_upload(f);
-    if (!rc) rc = fleet_step(f, generations);
+    const int b = (int)(h->tick & 1), pb = b ^ 1;
+    const auto t0 = std::chrono::steady_clock::now();
+    // tick - 2 finished (its status is in mirror b); tick - 1's copy-out landed
+    if (h->tick >= 2) GPGA_CUDA(cudaEventSynchronize(h->ev_status[b]));
+    if (h->tick >= 1) GPGA_CUDA(cudaEventSynchronize(h->ev_out[pb]));
+    const auto t1 = std::chrono::steady_clock::now();
+    if (h->g_timed[b]) { // tick - 2's generation graphs
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_g0[b], h->ev_g1[b]) == cudaSuccess) h->gpu_ms += ms;
+        h->g_timed[b] = false;
+    }
+    serve_collect(h, pb);
+    int rc = h->tick >= 2 ? serve_retire(h, b) : GPGA_OK;
+    if (!rc) GPGA_CUDA(cudaEventRecord(h->ev_out[b], f->stream));
+    if (!rc) rc = serve_admit(h, b);
+    if (!rc) rc = fleet_upload(f, b, h->tick);
     if (rc) return rc;
-    GPGA_CUDA(cudaMemcpyAsync(f->h_st, f->d_st, (size_t)f->cap * sizeof(DevState),
+    if (generations > 0 && f->nactive > 0) {
+        // (the first launch, and the first after the work doubled, tunes the
+        // launch shape and waits for the GPU)
+        GPGA_CUDA(cudaEventRecord(h->ev_g0[b], f->stream));
+        rc = fleet_step(f, generations);
+        if (rc) return rc;
+        GPGA_CUDA(cudaEventRecord(h->ev_g1[b], f->stream));
+        h->g_timed[b] = true;
+        h->gens += generations;
+        h->item_gens += (long long)generations * f->nitems;
+    }
+    GPGA_CUDA(cudaMemcpyAsync(f->h_st[b], f->d_st, (size_t)f->cap * sizeof(DevState),
                               cudaMemcpyDeviceToHost, f->stream));
+    GPGA_CUDA(cudaEventRecord(h->ev_status[b], f->stream));
+    ++h->tick;
+    const auto t2 = std::chrono::steady_clock::now();
+    h->host_wait_s += std::chrono::duration<double>(t1 - t0).count();
+    h->host_work_s += std::chrono::duration<double>(t2 - t1).count();
     if (active) *active = f->nactive;
     if (queued) *queued = (int)h->queue.size();
     return GPGA_OK;
@@ -802,7 +914,7 @@ GPGA_API int serve_result(gpga_server *h, long long id, int32_t *labels, double 
 }
 
 GPGA_API int serve_stats(gpga_server *h, size_t *bytes_in_use, size_t *budget,
-                         long long *completed, int *warps_per_cta, int *ctas)
+                         long long *completed, int *warps_per_cta, int *ctas, double *timing)
 {
     if (!h) return set_error(GPGA_ERR_ARG, "serve_stats: NULL handle");
     if (bytes_in_use) *bytes_in_use = h->in_use;
@@ -810,14 +922,20 @@ GPGA_API int serve_stats(gpga_server *h, size_t *bytes_in_use, size_t *budget,
     if (completed) *completed = h->completed;
     if (warps_per_cta) *warps_per_cta = h->f->warps;
     if (ctas) *ctas = h->f->ctas;
+    if (timing) {
+        timing[0] = (double)h->tick;
+        timing[1] = h->host_wait_s;
+        timing[2] = h->host_work_s;
+        timing[3] = h->gpu_ms;
+        timing[4] = (double)h->gens;
+        timing[5] = (double)h->item_gens;
+    }
     return GPGA_OK;
 }
 
 GPGA_API int serve_free(gpga_server *h)
 {
-    if (!h) return GPGA_OK;
-    fleet_destroy(h->f);
-    delete h;
+    serve_release(h);
     return GPGA_OK;
 }
 

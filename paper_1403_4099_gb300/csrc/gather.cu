@@ -8,8 +8,8 @@
 // sweep. D is read as int32 fixed point (2^-30), so every cluster sum is an
 // exact integer sum: independent of the order of the members, which are
 // therefore scattered with plain atomics, and deterministic. One warp per
-// individual; labels, counts and members live in that warp's slice of shared
-// memory. A cluster of at most 8 members is summed by one lane, a larger one by
+// individual; labels, counts and members live in that warp's 8 N-byte slice of
+// shared memory. A cluster of at most 8 members is summed by one lane, a larger one by
 // the whole warp. Eq. 8 then follows in the one-log product form.
 #include <math.h>
 
@@ -17,22 +17,26 @@
 
 namespace gpga {
 
-// per-warp shared-memory slice for Np padded genes (12 Np bytes)
+// per-warp shared-memory slice for Np padded genes (8 Np bytes). Counts and
+// fill pointers are 16-bit (N < 65536), two per 32-bit word (label 2w in the
+// low half of word w), updated with 32-bit shared-memory atomics: a half never
+// carries into its neighbour because no count or pointer exceeds N.
 struct GatherSlice {
-    int *cnt;      // Np: label counts, then the compacted clusters (start << 16 | n)
-    int *fill;     // Np: fill pointers (cluster ends after the scatter), then big clusters
-    uint16_t *lab; // Np: labels
-    uint16_t *mem; // Np: gene indices grouped by label
+    uint32_t *cnt;  // Np/2 words: label counts; later the list of big clusters
+    uint32_t *fill; // Np/2 words: cluster starts, cluster ends after the scatter
+    uint16_t *lab;  // Np: labels; after the scatter, the int32 list of
+                    // non-singleton clusters (start << 16 | n, at most N/2)
+    uint16_t *mem;  // Np: gene indices grouped by label
 };
 
-__host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 12; }
+__host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 8; }
 
 __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
 {
     GatherSlice s;
-    s.cnt = reinterpret_cast<int *>(base);
-    s.fill = s.cnt + Np;
-    s.lab = reinterpret_cast<uint16_t *>(s.fill + Np);
+    s.cnt = reinterpret_cast<uint32_t *>(base);
+    s.fill = s.cnt + Np / 2;
+    s.lab = reinterpret_cast<uint16_t *>(s.fill + Np / 2);
     s.mem = s.lab + Np;
     return s;
 }
@@ -52,47 +56,64 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
                                     unsigned long long *pairs_out)
 {
     const unsigned lt = (1u << lane) - 1u;
+    const int nwd = (N + 1) >> 1; // words holding the labels 0..N-1
     // histogram
-    for (int s = lane; s < N; s += 32) sl.cnt[s] = 0;
+    for (int w = lane; w < nwd; w += 32) sl.cnt[w] = 0u;
     __syncwarp();
-    for (int i = lane; i < N; i += 32) atomicAdd(&sl.cnt[sl.lab[i]], 1);
+    for (int i = lane; i < N; i += 32) {
+        const int s = sl.lab[i];
+        atomicAdd(&sl.cnt[s >> 1], 1u << ((s & 1) << 4));
+    }
     __syncwarp();
-    // exclusive scan of the counts -> fill (cluster starts), 32 labels at a time
+    // exclusive scan of the counts -> fill (cluster starts), 64 labels a step
     int carry = 0;
-    for (int base = 0; base < N; base += 32) {
-        const int s = base + lane;
-        const int c = s < N ? sl.cnt[s] : 0;
+    for (int base = 0; base < nwd; base += 32) {
+        const int w = base + lane;
+        const uint32_t c2 = w < nwd ? sl.cnt[w] : 0u;
+        const int c0 = (int)(c2 & 0xffffu), c = c0 + (int)(c2 >> 16);
         int v = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += t;
         }
-        if (s < N) sl.fill[s] = carry + v - c;
+        const int e = carry + v - c;
+        if (w < nwd) sl.fill[w] = (uint32_t)e | ((uint32_t)(e + c0) << 16);
         carry += __shfl_sync(0xffffffffu, v, 31);
     }
     __syncwarp();
     // scatter gene indices by label (order inside a cluster is irrelevant: the
-    // pair sums below are exact integer sums); fill[s] ends at cluster s's end
-    for (int i = lane; i < N; i += 32) sl.mem[atomicAdd(&sl.fill[sl.lab[i]], 1)] = (uint16_t)i;
-    __syncwarp();
-    // compact the non-singleton clusters in place: cnt[c] = start << 16 | n
-    int nlist = 0;
-    for (int base = 0; base < N; base += 32) {
-        const int s = base + lane;
-        int n = 0, st = 0;
-        if (s < N) {
-            n = sl.cnt[s];
-            st = sl.fill[s] - n;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, n >= 2);
-        __syncwarp();
-        if (n >= 2) sl.cnt[nlist + __popc(m & lt)] = (st << 16) | n;
-        nlist += __popc(m);
-        __syncwarp();
+    // pair sums below are exact integer sums); fill ends at each cluster's end
+    for (int i = lane; i < N; i += 32) {
+        const int s = sl.lab[i], sh = (s & 1) << 4;
+        const uint32_t old = atomicAdd(&sl.fill[s >> 1], 1u << sh);
+        sl.mem[(old >> sh) & 0xffffu] = (uint16_t)i;
     }
+    __syncwarp();
+    // list the non-singleton clusters in label order (the labels are dead now:
+    // the list takes their space)
+    int *list = reinterpret_cast<int *>(sl.lab);
+    int nlist = 0;
+    for (int base = 0; base < nwd; base += 32) {
+        const int w = base + lane;
+        uint32_t c2 = 0u, f2 = 0u;
+        if (w < nwd) {
+            c2 = sl.cnt[w];
+            f2 = sl.fill[w];
+        }
+        const int n0 = (int)(c2 & 0xffffu), n1 = (int)(c2 >> 16);
+        const int e0 = (int)(f2 & 0xffffu), e1 = (int)(f2 >> 16);
+        const bool k0 = n0 >= 2, k1 = n1 >= 2;
+        const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
+        int pos = nlist + __popc(m0 & lt) + __popc(m1 & lt);
+        if (k0) list[pos++] = ((e0 - n0) << 16) | n0;
+        if (k1) list[pos] = ((e1 - n1) << 16) | n1;
+        nlist += __popc(m0) + __popc(m1);
+    }
+    __syncwarp();
     // small clusters: one lane each, term in registers; big clusters: listed in
-    // fill[] for the whole warp. d_s = 2 sum_{a<b} Dfix + sum_a Dfix_aa.
+    // the (dead) count words for the whole warp. d_s = 2 sum_{a<b} Dfix + sum_a Dfix_aa.
+    int *big = reinterpret_cast<int *>(sl.cnt);
     LogProd acc;
     int nbig = 0;
     long long npairs = 0;
@@ -100,7 +121,7 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         const int c = base + lane;
         int v = 0, n = 0;
         if (c < nlist) {
-            v = sl.cnt[c];
+            v = list[c];
             n = v & 0xffff;
         }
         if (n >= 2 && n <= SMALL_CLUSTER) {
@@ -120,12 +141,12 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
             npairs += n * (n - 1) / 2;
         }
         const unsigned bm = __ballot_sync(0xffffffffu, n > SMALL_CLUSTER);
-        if (n > SMALL_CLUSTER) sl.fill[nbig + __popc(bm & lt)] = v;
+        if (n > SMALL_CLUSTER) big[nbig + __popc(bm & lt)] = v;
         nbig += __popc(bm);
     }
     __syncwarp();
     for (int q = 0; q < nbig; ++q) {
-        const int v = sl.fill[q];
+        const int v = big[q];
         const int st = v >> 16, n = v & 0xffff;
         long long sum = 0;
         // rows a over lanes, each lane summing D[m_a][m_b] for b > a

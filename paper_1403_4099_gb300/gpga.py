@@ -105,7 +105,8 @@ def lib() -> ct.CDLL:
             "serve_tick": (i32, [vp, i32, ct.POINTER(i32), ct.POINTER(i32)]),
             "serve_result": (i32, [vp, ct.c_longlong, vp, vp, ct.POINTER(i32), vp]),
             "serve_stats": (i32, [vp, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
-                                  ct.POINTER(ct.c_longlong), ct.POINTER(i32), ct.POINTER(i32)]),
+                                  ct.POINTER(ct.c_longlong), ct.POINTER(i32), ct.POINTER(i32),
+                                  vp]),
             "serve_free": (i32, [vp]),
         }
         for name, (res, args) in sigs.items():
@@ -406,10 +407,12 @@ class Server:
 
     def stats(self):
         u, b, c, w, k = ct.c_size_t(), ct.c_size_t(), ct.c_longlong(), ct.c_int(), ct.c_int()
+        t = np.zeros(6, np.float64)
         _check(lib().serve_stats(self._h, ct.byref(u), ct.byref(b), ct.byref(c), ct.byref(w),
-                                 ct.byref(k)))
+                                 ct.byref(k), t.ctypes.data))
         return dict(bytes_in_use=u.value, budget=b.value, completed=c.value,
-                    warps_per_cta=w.value, ctas=k.value)
+                    warps_per_cta=w.value, ctas=k.value, ticks=int(t[0]), host_wait_s=t[1],
+                    host_work_s=t[2], gpu_ms=t[3], generations=int(t[4]), item_gens=int(t[5]))
 
     def close(self):
         if getattr(self, "_h", None):
