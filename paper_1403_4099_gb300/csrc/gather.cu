@@ -45,6 +45,34 @@ __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
 // ones by the whole warp
 constexpr int SMALL_CLUSTER = 8;
 
+// d_s of one cluster of 3 <= n <= K members m[0..n): every pair load issued
+// at once (predicated on n), so one L2 round trip instead of n (n - 1) / 2
+template <int K>
+__device__ __forceinline__ long long small_cluster_sum(const uint16_t *m, int n,
+                                                       const int32_t *__restrict__ Dfix, int Np,
+                                                       int diag)
+{
+    int idx[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) idx[a] = a < n ? (int)m[a] : 0;
+    int32_t v[K * (K - 1) / 2];
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < K - 1; ++a)
+#pragma unroll
+        for (int b = a + 1; b < K; ++b, ++t)
+            v[t] = b < n ? __ldg(Dfix + (size_t)idx[a] * Np + idx[b]) : 0;
+    long long s = 0;
+#pragma unroll
+    for (int q = 0; q < K * (K - 1) / 2; ++q) s += v[q];
+    s *= 2;
+    if (diag)
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+            if (a < n) s += Dfix[(size_t)idx[a] * (Np + 1)];
+    return s;
+}
+
 // Score one configuration held in sl.lab[0..N) (labels < N, N < 65536).
 // Returns L on all lanes. Dfix: Np x Np int32, D = 1 - C in fixed point
 // 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. pairs_out (optional):
@@ -125,18 +153,17 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
             n = v & 0xffff;
         }
         if (n >= 2 && n <= SMALL_CLUSTER) {
-            const int st = v >> 16;
-            long long sum = 0;
-            for (int a = 0; a < n - 1; ++a) {
-                const int32_t *row = Dfix + (size_t)sl.mem[st + a] * Np;
-                for (int b = a + 1; b < n; ++b) sum += __ldg(row + sl.mem[st + b]);
+            const uint16_t *m = sl.mem + (v >> 16);
+            long long sum;
+            if (n == 2) {
+                const int i0 = m[0], i1 = m[1];
+                sum = 2ll * __ldg(Dfix + (size_t)i0 * Np + i1);
+                if (diag) sum += (long long)Dfix[(size_t)i0 * (Np + 1)] + Dfix[(size_t)i1 * (Np + 1)];
+            } else if (n <= 4) {
+                sum = small_cluster_sum<4>(m, n, Dfix, Np, diag);
+            } else {
+                sum = small_cluster_sum<SMALL_CLUSTER>(m, n, Dfix, Np, diag);
             }
-            sum *= 2;
-            if (diag)
-                for (int a = 0; a < n; ++a) {
-                    const int i = sl.mem[st + a];
-                    sum += Dfix[(size_t)i * Np + i];
-                }
             logprod_add(acc, n, sum, DFIX_BITS, kfix);
             npairs += n * (n - 1) / 2;
         }
@@ -145,27 +172,40 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         nbig += __popc(bm);
     }
     __syncwarp();
+    // big clusters one at a time, rows a over lanes, eight independent loads in
+    // flight per lane; the sums go to the (dead) fill words, then one lane per
+    // cluster adds its term
+    long long *bsum = reinterpret_cast<long long *>(sl.fill);
     for (int q = 0; q < nbig; ++q) {
         const int v = big[q];
-        const int st = v >> 16, n = v & 0xffff;
+        const uint16_t *m = sl.mem + (v >> 16);
+        const int n = v & 0xffff;
         long long sum = 0;
-        // rows a over lanes, each lane summing D[m_a][m_b] for b > a
         for (int a = lane; a < n - 1; a += 32) {
-            const int32_t *row = Dfix + (size_t)sl.mem[st + a] * Np;
-            for (int b = a + 1; b < n; ++b) sum += __ldg(row + sl.mem[st + b]);
+            const int32_t *row = Dfix + (size_t)m[a] * Np;
+            long long s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int b = a + 1;
+            for (; b + 8 <= n; b += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s[u] += __ldg(row + m[b + u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 7; ++u)
+                if (b + u < n) s[u] += __ldg(row + m[b + u]);
+            sum += ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
         }
         sum *= 2;
         if (diag)
-            for (int a = lane; a < n; a += 32) {
-                const int i = sl.mem[st + a];
-                sum += Dfix[(size_t)i * Np + i];
-            }
+            for (int a = lane; a < n; a += 32) sum += Dfix[(size_t)m[a] * (Np + 1)];
 #pragma unroll
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == (q & 31)) {
-            logprod_add(acc, n, sum, DFIX_BITS, kfix);
-            npairs += n * (n - 1) / 2;
-        }
+        if (lane == 0) bsum[q] = sum;
+    }
+    __syncwarp();
+    for (int q = lane; q < nbig; q += 32) {
+        const int n = big[q] & 0xffff;
+        logprod_add(acc, n, bsum[q], DFIX_BITS, kfix);
+        npairs += n * (n - 1) / 2;
     }
     if (pairs_out) {
 #pragma unroll
@@ -288,7 +328,7 @@ __global__ void __launch_bounds__(256)
 // first); the CTAs stride over the items. Runs whose state is done are
 // skipped. Per slot the work is exactly that of gather_generation_kernel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
     fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
                             EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
                             const double *__restrict__ logtab, int Np_max, int prop)

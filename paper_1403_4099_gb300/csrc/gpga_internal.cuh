@@ -432,18 +432,28 @@ __device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t
     return x;
 }
 
-__device__ __forceinline__ int sus_parent(int k, uint32_t u, uint64_t W, int M, int P,
-                                          double inv_md, const uint64_t *__restrict__ prefix,
-                                          const int32_t *__restrict__ perm)
+// Parent of SUS pointer k for each half-warp (lanes 0-15 and 16-31 may ask
+// for different k): the rank r with prefix[r-1] <= x_k < prefix[r], found by a
+// 16-ary search (each round the half-warp loads 16 evenly spaced prefix values
+// and counts those <= x_k: three dependent loads for P = 4096 instead of
+// twelve), then perm[r]. All lanes of the warp call; returns the half's parent.
+__device__ __forceinline__ int sus_parent_half(uint32_t k, uint32_t u, uint64_t W, int M, int P,
+                                               double inv_md,
+                                               const uint64_t *__restrict__ prefix,
+                                               const int32_t *__restrict__ perm, int lane)
 {
-    const uint64_t x = sus_pointer((uint32_t)k, u, W, (uint32_t)M, inv_md);
-    int lo = 0, hi = P - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(prefix + mid) > x)
-            hi = mid;
-        else
-            lo = mid + 1;
+    const uint64_t x = sus_pointer(k, u, W, (uint32_t)M, inv_md);
+    const int l = lane & 15;
+    const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
+    int top = 1;
+    while (top * 16 < P) top *= 16;
+    // invariant: the answer lies in [lo, lo + 16 step)
+    int lo = 0;
+    for (int step = top; step >= 1; step >>= 4) {
+        const int idx = lo + l * step;
+        const bool le = idx < P && __ldg(prefix + idx) <= x;
+        const int c = __popc(__ballot_sync(0xffffffffu, le) & half);
+        if (c) lo += (c - 1) * step + 1;
     }
     return perm[lo];
 }
@@ -453,22 +463,19 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
                                             int g, int k, uint32_t k0, uint32_t k1,
                                             const int32_t *__restrict__ perm,
                                             const uint64_t *__restrict__ prefix,
-                                            int32_t *__restrict__ parents_out, LabT *dst,
-                                            uint16_t *lab_s, int lane)
+                                            int32_t *__restrict__ parents_out,
+                                            LabT *__restrict__ dst, uint16_t *lab_s, int lane)
 {
     const int M = cfg.M;
-    int par = 0;
-    if (lane < 2) {
-        const uint64_t W = __ldg(prefix + cfg.P - 1);
-        const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
-        par = sus_parent(lane == 0 ? k : (k + M / 2) % M, su.x, W, M, cfg.P, cfg.inv_md, prefix,
-                         perm);
-    }
+    const uint64_t W = __ldg(prefix + cfg.P - 1);
+    const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
+    const int par = sus_parent_half(lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M), su.x, W,
+                                    M, cfg.P, cfg.inv_md, prefix, perm, lane);
     const int ia = __shfl_sync(0xffffffffu, par, 0);
-    const int ib = __shfl_sync(0xffffffffu, par, 1);
+    const int ib = __shfl_sync(0xffffffffu, par, 16);
     if (parents_out && lane == 0) parents_out[k] = ia;
-    const LabT *a = cur + (size_t)ia * ldp;
-    const LabT *b = cur + (size_t)ib * ldp;
+    const LabT *__restrict__ a = cur + (size_t)ia * ldp;
+    const LabT *__restrict__ b = cur + (size_t)ib * ldp;
     const U4 xw = philox((uint32_t)g, (uint32_t)k, 0u, STREAM_XOVER, k0, k1);
     int mode = 0, cut = N;
     int bq = 0, aq = 0;
@@ -484,6 +491,37 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
         }
     }
     const int npair = (N + 1) >> 1;
+    if constexpr (sizeof(LabT) == 2) {
+        // 16-bit labels: one 32-bit load per parent and gene pair (rows are
+        // 128-byte aligned); a padding gene (j = N for odd N) is written as 0
+        const uint32_t *__restrict__ a2 = reinterpret_cast<const uint32_t *>(a);
+        const uint32_t *__restrict__ b2 = reinterpret_cast<const uint32_t *>(b);
+        uint32_t *__restrict__ d2 = reinterpret_cast<uint32_t *>(dst);
+        uint32_t *s2 = reinterpret_cast<uint32_t *>(lab_s);
+#pragma unroll 4
+        for (int m = lane; m < npair; m += 32) {
+            const int j0 = 2 * m, j1 = 2 * m + 1;
+            const uint32_t av = __ldg(a2 + m), bv = __ldg(b2 + m);
+            const int a0 = (int)(av & 0xffffu), a1 = (int)(av >> 16);
+            const int b0 = (int)(bv & 0xffffu), b1 = (int)(bv >> 16);
+            int c0 = a0, c1 = a1;
+            if (mode == 1) {
+                if (j0 >= cut) c0 = b0;
+                if (j1 >= cut) c1 = b1;
+            } else if (mode == 2) {
+                if (b0 == bq) c0 = aq;
+                if (b1 == bq) c1 = aq;
+            }
+            const U4 mw = philox((uint32_t)g, (uint32_t)k, (uint32_t)m, STREAM_MUT, k0, k1);
+            if ((uint64_t)mw.x < cfg.thr_pm) c0 = draw_below(mw.y, (uint32_t)N);
+            if ((uint64_t)mw.z < cfg.thr_pm) c1 = draw_below(mw.w, (uint32_t)N);
+            if (j1 >= N) c1 = 0;
+            const uint32_t cv = (uint32_t)c0 | ((uint32_t)c1 << 16);
+            d2[m] = cv;
+            if (s2) s2[m] = cv;
+        }
+        return;
+    }
     for (int m = lane; m < npair; m += 32) {
         const int j0 = 2 * m, j1 = 2 * m + 1;
         int a0 = (int)a[j0], b0 = (int)b[j0];
