@@ -548,6 +548,66 @@ static void kb_merge(const int32_t *a, const int32_t *b, int N, int q, int32_t *
     for (int j = 0; j < N; ++j) child[j] = (b[j] == bq) ? aq : a[j];
 }
 
+/* Mutation by random replacement, each gene with probability P_m (Sec. 3.1,
+ * Table 3), drawn as geometric gaps between mutated genes instead of one test
+ * per gene (the same law). Genes are taken in blocks of 16 consecutive genes.
+ * Within a block, from position pos the next mutated gene is pos + G(u) with
+ *   G(u) = #{t in 1..16 : u < T_t},  T_t = min(floor((1 - P_m)^t 2^32), 2^32 - 1),
+ * so that P(none of the next t genes mutates) = T_t / 2^32 = (1 - P_m)^t; the
+ * gene takes the label draw(v, N), and the search goes on after it. The (u, v)
+ * pairs are words (0, 1) then (2, 3) of Philox(g, k, block + 65536 e, MUT) for
+ * e = 0, 1, ... (a block with more than two mutations uses further calls).
+ * (1 - P_m)^t is the FP64 product of t factors (1 - P_m), left to right.
+ * floor(P_m 2^32) = 0 means no mutation at all. */
+#define ORC_MUT_BLOCK 16
+
+static void mutation_gap_table(double pm, uint32_t T[ORC_MUT_BLOCK])
+{
+    const double r = 1.0 - pm;
+    double q = 1.0;
+    for (int t = 0; t < ORC_MUT_BLOCK; ++t) {
+        q = q * r; /* (1 - P_m)^(t + 1) */
+        double v = floor(q * 4294967296.0);
+        if (v > 4294967295.0) v = 4294967295.0;
+        T[t] = (uint32_t)v;
+    }
+}
+
+static int mutation_gap(uint32_t u, const uint32_t T[ORC_MUT_BLOCK])
+{
+    int s = 0;
+    for (int t = 0; t < ORC_MUT_BLOCK; ++t)
+        if (u < T[t]) ++s;
+    return s;
+}
+
+static void mutate_child(int32_t *child, int N, uint64_t seed, int32_t g, int k,
+                         const uint32_t T[ORC_MUT_BLOCK])
+{
+    for (int blk = 0; blk * ORC_MUT_BLOCK < N; ++blk) {
+        const int base = blk * ORC_MUT_BLOCK;
+        const int len = N - base < ORC_MUT_BLOCK ? N - base : ORC_MUT_BLOCK;
+        int pos = 0;
+        for (uint32_t e = 0;; ++e) {
+            uint32_t w[4];
+            philox_draw(seed, (uint32_t)g, (uint32_t)k, (uint32_t)blk + 65536u * e,
+                        ORC_STREAM_MUT, w);
+            int done = 0;
+            for (int h = 0; h < 2 && !done; ++h) {
+                pos += mutation_gap(w[2 * h], T);
+                if (pos >= len) {
+                    done = 1;
+                    break;
+                }
+                child[base + pos] = label_draw(w[2 * h + 1], N);
+                ++pos;
+                if (pos >= len) done = 1;
+            }
+            if (done) break;
+        }
+    }
+}
+
 /* One generation of Algorithm 1 after scoring: isolate fittest, elitism,
  * scaling, SUS selection, crossover (P_c; cluster merge with P_kb, else one-point),
  * random-replacement mutation per gene (P_m), replacement. Draws for parent
@@ -555,8 +615,8 @@ static void kb_merge(const int32_t *a, const int32_t *b, int N, int q, int32_t *
  *   SUS offset   u = word 0 of Philox(g, 0, 0, SUS)
  *   child k      words of Philox(g, k, 0, XOVER): x crossover?, y merge?,
  *                z anchor q = draw(z, N) or cut = 1 + draw(z, N - 1)
- *   gene j       Philox(g, k, j/2, MUT): words (0,1) for even j, (2,3) for odd
- *                j: fire if first < thr(P_m), new label = draw(second, N)
+ *   mutation     per block of 16 genes (see mutate_child): gaps between
+ *                mutated genes from Philox(g, k, block + 65536 e, MUT)
  * Pairing: a = parent[k], b = parent[(k + M/2) mod M]. Elites fill slots
  * 0..E-1 in rank order, unchanged; child k fills slot E + k.
  * Optional outputs: perm (P ranks), parents (M indices). */
@@ -589,6 +649,8 @@ int orc_ga_evolve(const int32_t *pop, const double *L, const orc_ga_params *prm,
     const uint64_t thr_pc = orc_threshold(prm->pc);
     const uint64_t thr_pkb = orc_threshold(prm->pkb);
     const uint64_t thr_pm = orc_threshold(prm->pm);
+    uint32_t gaps[ORC_MUT_BLOCK];
+    mutation_gap_table(prm->pm, gaps);
 
     for (int e = 0; e < E; ++e)
         memcpy(next + (size_t)e * N, pop + (size_t)perm[e] * N, (size_t)N * sizeof(int32_t));
@@ -608,13 +670,7 @@ int orc_ga_evolve(const int32_t *pop, const double *L, const orc_ga_params *prm,
                 for (int j = cut; j < N; ++j) child[j] = b[j];
             }
         }
-        for (int j = 0; j < N; ++j) {
-            uint32_t mw[4];
-            philox_draw(seed, (uint32_t)g, (uint32_t)k, (uint32_t)(j / 2), ORC_STREAM_MUT, mw);
-            uint32_t fire = (j & 1) ? mw[2] : mw[0];
-            uint32_t val = (j & 1) ? mw[3] : mw[1];
-            if ((uint64_t)fire < thr_pm) child[j] = label_draw(val, N);
-        }
+        if (thr_pm) mutate_child(child, N, seed, g, k, gaps);
     }
     if (perm_out) memcpy(perm_out, perm, (size_t)P * sizeof(int32_t));
     if (parents_out) memcpy(parents_out, par, (size_t)M * sizeof(int32_t));

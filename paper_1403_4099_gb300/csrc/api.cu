@@ -272,7 +272,7 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs)
     e.ldp = h->Np;
     e.thr_pc = prob_threshold(h->prm.pc);
     e.thr_pkb = prob_threshold(h->prm.pkb);
-    e.thr_pm = prob_threshold(h->prm.pm);
+    set_mutation(&e, h->prm.pm);
     e.inv_md = 1.0 / ((double)h->M * 4294967296.0);
     e.k0 = h->k0;
     e.k1 = h->k1;
@@ -531,7 +531,7 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
         e.ldp = N;
         e.thr_pc = prob_threshold(p->pc);
         e.thr_pkb = prob_threshold(p->pkb);
-        e.thr_pm = prob_threshold(p->pm);
+        set_mutation(&e, p->pm);
         e.inv_md = 1.0 / ((double)M * 4294967296.0);
         e.k0 = sc.k0;
         e.k1 = sc.k1;

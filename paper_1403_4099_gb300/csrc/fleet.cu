@@ -156,7 +156,7 @@ static EvolveCfg fleet_evolve_cfg(const Fleet *f)
     e.ldp = 0;
     e.thr_pc = prob_threshold(f->prm.pc);
     e.thr_pkb = prob_threshold(f->prm.pkb);
-    e.thr_pm = prob_threshold(f->prm.pm);
+    set_mutation(&e, f->prm.pm);
     e.inv_md = 1.0 / ((double)f->M * 4294967296.0);
     e.k0 = 0;
     e.k1 = 0;

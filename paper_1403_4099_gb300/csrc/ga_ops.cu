@@ -17,6 +17,19 @@ uint64_t prob_threshold(double p)
     return (uint64_t)floor(p * 4294967296.0);
 }
 
+void set_mutation(EvolveCfg *cfg, double pm)
+{
+    cfg->thr_pm = prob_threshold(pm);
+    // (1 - P_m)^t as a running FP64 product, t = 1..MUT_BLOCK, scaled to 32 bits
+    const double keep = 1.0 - pm;
+    double run = 1.0;
+    for (int t = 0; t < MUT_BLOCK; ++t) {
+        run *= keep;
+        const double v = floor(run * 4294967296.0);
+        cfg->gap[t] = v >= 4294967295.0 ? 0xffffffffu : (uint32_t)v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // "Create initial population": gene j of individual p uniform in [0, K0) from
 // word j mod 4 of Philox(0, p, j / 4, INIT). One thread per 4 genes.
@@ -141,10 +154,11 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 // ---------------------------------------------------------------------------
 // "Isolate fittest individuals" and the per-generation bookkeeping, one launch.
 // rank_i = #{j : (L_j, j) fitter than (L_i, i)} (key descending, index
-// ascending; NaN as -inf). CTA (x, y) sorts the 256 keys of chunk y in shared
-// memory (bitonic) and counts, for each key i of chunk x, the fitter keys of
-// chunk y by binary search; integer atomics sum the counts, so the ranks are
-// exact and order-independent (P^2/256 log 256 comparisons instead of P^2).
+// ascending; NaN as -inf). CTA (x, y) loads the 256 keys of chunk y into
+// shared memory and counts, for each key i of chunk x, the fitter keys of
+// chunk y (256 comparisons per thread, broadcast reads, no barrier between
+// them); integer atomics sum the counts, so the ranks are exact and
+// order-independent.
 // Tickets (no CTA ever waits): the last CTA of column x holds the final ranks
 // of chunk x and scatters perm[rank_i] = i (zeroing rank for the next use) and
 // its share of the mean; the last such column finisher does "evaluate state
@@ -180,40 +194,20 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
     uint64_t *s_part = sm.s_part;
     const int tid = threadIdx.x, nt = blockDim.x;
     {
+        // chunk y into shared memory (padding: key 0 with an index above every
+        // real one, fitter than no real key), then every key i of chunk x counts
+        // its fitter keys of chunk y one by one (broadcast reads, no barrier)
         const int jy = blockIdx.y * RANK_CHUNK + tid;
-        sk[tid] = jy < P ? order_key(L[jy]) : 0ull; // padding below every real key
+        sk[tid] = jy < P ? order_key(L[jy]) : 0ull;
         si[tid] = jy < P ? jy : 0x7fffffff;
-        __syncthreads();
-        for (int k = 2; k <= RANK_CHUNK; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                if (tid < RANK_CHUNK / 2) {
-                    const int i = ((tid & ~(j - 1)) << 1) | (tid & (j - 1));
-                    const int l = i + j;
-                    const unsigned long long ki = sk[i], kl = sk[l];
-                    const int ii = si[i], il = si[l];
-                    const bool up = (i & k) == 0;
-                    if (up ? fitter(kl, il, ki, ii) : fitter(ki, ii, kl, il)) {
-                        sk[i] = kl;
-                        sk[l] = ki;
-                        si[i] = il;
-                        si[l] = ii;
-                    }
-                }
-                __syncthreads();
-            }
-        }
         const int i = blockIdx.x * RANK_CHUNK + tid;
+        const unsigned long long ki = i < P ? order_key(L[i]) : 0ull;
+        __syncthreads();
         if (i < P) {
-            const unsigned long long ki = order_key(L[i]);
-            int lo = 0, hi = RANK_CHUNK; // fitter keys form a prefix of the sorted chunk
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (fitter(sk[mid], si[mid], ki, i))
-                    lo = mid + 1;
-                else
-                    hi = mid;
-            }
-            if (lo) atomicAdd(&rank[i], lo);
+            int cnt = 0;
+#pragma unroll 8
+            for (int j = 0; j < RANK_CHUNK; ++j) cnt += fitter(sk[j], si[j], ki, i);
+            if (cnt) atomicAdd(&rank[i], cnt);
         }
     }
     // column ticket: the last of the nc CTAs of column x holds the final ranks

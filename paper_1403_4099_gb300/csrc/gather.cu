@@ -139,12 +139,17 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         nlist += __popc(m0) + __popc(m1);
     }
     __syncwarp();
-    // small clusters: one lane each, term in registers; big clusters: listed in
-    // the (dead) count words for the whole warp. d_s = 2 sum_{a<b} Dfix + sum_a Dfix_aa.
-    int *big = reinterpret_cast<int *>(sl.cnt);
-    LogProd acc;
+    // Pair sums first, then the terms: the sums of the clusters hold no
+    // dependency on one another, so a lane's loads of successive clusters
+    // overlap instead of waiting behind each cluster's log-product step.
+    // csum (int64 per listed cluster) fills the dead count and fill words from
+    // the front, the list of big clusters (n > 8) from the back:
+    // 8 nlist + 4 nbig <= 4 N bytes.
+    long long *csum = reinterpret_cast<long long *>(sl.cnt);
+    int *big_end = reinterpret_cast<int *>(sl.fill + Np / 2);
     int nbig = 0;
-    long long npairs = 0;
+    long long ksum = 0; // sum of K(n_s) in 2^-44, loaded alongside the pair sums
+    // small clusters: one lane each, all pair loads of the cluster at once
     for (int base = 0; base < nlist; base += 32) {
         const int c = base + lane;
         int v = 0, n = 0;
@@ -154,30 +159,19 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         }
         if (n >= 2 && n <= SMALL_CLUSTER) {
             const uint16_t *m = sl.mem + (v >> 16);
-            long long sum;
-            if (n == 2) {
-                const int i0 = m[0], i1 = m[1];
-                sum = 2ll * __ldg(Dfix + (size_t)i0 * Np + i1);
-                if (diag) sum += (long long)Dfix[(size_t)i0 * (Np + 1)] + Dfix[(size_t)i1 * (Np + 1)];
-            } else if (n <= 4) {
-                sum = small_cluster_sum<4>(m, n, Dfix, Np, diag);
-            } else {
-                sum = small_cluster_sum<SMALL_CLUSTER>(m, n, Dfix, Np, diag);
-            }
-            logprod_add(acc, n, sum, DFIX_BITS, kfix);
-            npairs += n * (n - 1) / 2;
+            ksum += __ldg(kfix + n);
+            csum[c] = n <= 4 ? small_cluster_sum<4>(m, n, Dfix, Np, diag)
+                             : small_cluster_sum<SMALL_CLUSTER>(m, n, Dfix, Np, diag);
         }
         const unsigned bm = __ballot_sync(0xffffffffu, n > SMALL_CLUSTER);
-        if (n > SMALL_CLUSTER) big[nbig + __popc(bm & lt)] = v;
+        if (n > SMALL_CLUSTER) big_end[-1 - (nbig + __popc(bm & lt))] = c;
         nbig += __popc(bm);
     }
     __syncwarp();
-    // big clusters one at a time, rows a over lanes, eight independent loads in
-    // flight per lane; the sums go to the (dead) fill words, then one lane per
-    // cluster adds its term
-    long long *bsum = reinterpret_cast<long long *>(sl.fill);
+    // big clusters one at a time, rows a over lanes, eight loads in flight per lane
     for (int q = 0; q < nbig; ++q) {
-        const int v = big[q];
+        const int c = big_end[-1 - q];
+        const int v = list[c];
         const uint16_t *m = sl.mem + (v >> 16);
         const int n = v & 0xffff;
         long long sum = 0;
@@ -199,12 +193,19 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
             for (int a = lane; a < n; a += 32) sum += Dfix[(size_t)m[a] * (Np + 1)];
 #pragma unroll
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) bsum[q] = sum;
+        if (lane == 0) {
+            csum[c] = sum;
+            ksum += __ldg(kfix + n);
+        }
     }
     __syncwarp();
-    for (int q = lane; q < nbig; q += 32) {
-        const int n = big[q] & 0xffff;
-        logprod_add(acc, n, bsum[q], DFIX_BITS, kfix);
+    // the terms, one lane per cluster (a running mantissa product per lane)
+    LogProd acc;
+    acc.k = ksum;
+    long long npairs = 0;
+    for (int c = lane; c < nlist; c += 32) {
+        const int n = list[c] & 0xffff;
+        logprod_mul(acc, n, csum[c], DFIX_BITS);
         npairs += n * (n - 1) / 2;
     }
     if (pairs_out) {
@@ -222,7 +223,7 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
 // st->gen + sel_off).
 // ---------------------------------------------------------------------------
 template <typename LabT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     gather_score_kernel(const LabT *lab0, const LabT *lab1, int ldl, int sel_off, int P, int N,
                         int Np, const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
                         const double *__restrict__ logtab, double *__restrict__ L,
@@ -300,7 +301,7 @@ __device__ __forceinline__ void generation_slot(const LabT *cur, LabT *nxt, cons
 }
 
 template <typename LabT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     gather_generation_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1,
                              EvolveCfg cfg, const int32_t *__restrict__ perm,
                              const uint64_t *__restrict__ prefix, int Np,

@@ -179,8 +179,9 @@ __device__ __forceinline__ void mant_mul(unsigned long long &m, long long &e, un
     }
 }
 
-__device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int fix_bits,
-                                            const long long *__restrict__ kfix)
+// the product part of logprod_add: c d^(n-1) into the running mantissa
+// product (the caller sums K(n) itself)
+__device__ __forceinline__ void logprod_mul(LogProd &a, int n, long long df, int fix_bits)
 {
     long long cf = (((long long)n * n) << fix_bits) - df;
     const int sh = 40 - fix_bits; // fix_bits <= 40
@@ -203,6 +204,12 @@ __device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int
         mant_mul(md, ed, md, ed);
     }
     a.e -= (long long)fix_bits * n; // c and the n - 1 factors d each carried 2^b
+}
+
+__device__ __forceinline__ void logprod_add(LogProd &a, int n, long long df, int fix_bits,
+                                            const long long *__restrict__ kfix)
+{
+    logprod_mul(a, n, df, fix_bits);
     a.k += kfix[n];
 }
 
@@ -378,13 +385,22 @@ int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *per
                   uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,
                   const LabT *const *pop2, LabT *ring, unsigned long long *ts, cudaStream_t s);
 
+// mutation gaps: genes in blocks of MUT_BLOCK; gap[t] = min(floor((1 - P_m)^(t+1)
+// 2^32), 2^32 - 1), the probability (times 2^32) that the next t + 1 genes
+// keep their labels
+constexpr int MUT_BLOCK = 16;
+
 struct EvolveCfg {
     int P, E, M, N, ldp;
     double inv_md; // 1 / (M 2^32), for the SUS pointer estimate
     uint64_t thr_pc, thr_pkb, thr_pm;
     uint32_t k0, k1;
     int gen; // stateless generation (when st == nullptr)
+    uint32_t gap[MUT_BLOCK];
 };
+
+// fill cfg->thr_pm and cfg->gap for mutation probability pm (host)
+void set_mutation(EvolveCfg *cfg, double pm);
 
 // prefix: inclusive prefix of the scaled weights by rank (RANK: the fixed
 // table; PROP: the work prefix written by finalize); parents_out optional
@@ -458,6 +474,57 @@ __device__ __forceinline__ int sus_parent_half(uint32_t k, uint32_t u, uint64_t 
     return perm[lo];
 }
 
+// number of genes the next mutation skips for word u: #{t : u < gap[t]}
+__device__ __forceinline__ int mutation_skip(uint32_t u, const EvolveCfg &cfg)
+{
+    int s = 0;
+#pragma unroll
+    for (int t = 0; t < MUT_BLOCK; ++t) s += u < cfg.gap[t] ? 1 : 0;
+    return s;
+}
+
+// "Apply genetic operator: mutation" (random replacement, each gene with
+// probability P_m), drawn as geometric gaps: lane handles the blocks of
+// MUT_BLOCK genes b = lane, lane + 32, ...; from position pos the next
+// mutated gene is pos + skip(u) and takes label draw(v, N), with (u, v) the
+// words (x, y) then (z, w) of Philox(g, k, b + 65536 e, MUT), e = 0, 1, ...
+// The crossover result must already be in dst / lab_s (all lanes, synced here).
+template <typename LabT>
+__device__ __forceinline__ void mutate_child(const EvolveCfg &cfg, int N, int g, int k,
+                                             uint32_t k0, uint32_t k1, LabT *dst,
+                                             uint16_t *lab_s, int lane)
+{
+    __syncwarp();
+    if (!cfg.thr_pm) return;
+    const int nblk = (N + MUT_BLOCK - 1) / MUT_BLOCK;
+    for (int blk = lane; blk < nblk; blk += 32) {
+        const int base = blk * MUT_BLOCK;
+        const int len = min(MUT_BLOCK, N - base);
+        int pos = 0;
+        for (uint32_t e = 0;; ++e) {
+            const U4 w = philox((uint32_t)g, (uint32_t)k, (uint32_t)blk + 65536u * e, STREAM_MUT,
+                                k0, k1);
+            pos += mutation_skip(w.x, cfg);
+            if (pos >= len) break;
+            {
+                const int v = draw_below(w.y, (uint32_t)N);
+                dst[base + pos] = (LabT)v;
+                if (lab_s) lab_s[base + pos] = (uint16_t)v;
+            }
+            if (++pos >= len) break;
+            pos += mutation_skip(w.z, cfg);
+            if (pos >= len) break;
+            {
+                const int v = draw_below(w.w, (uint32_t)N);
+                dst[base + pos] = (LabT)v;
+                if (lab_s) lab_s[base + pos] = (uint16_t)v;
+            }
+            if (++pos >= len) break;
+        }
+    }
+    __syncwarp();
+}
+
 template <typename LabT>
 __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, const EvolveCfg &cfg,
                                             int g, int k, uint32_t k0, uint32_t k1,
@@ -512,14 +579,12 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
                 if (b0 == bq) c0 = aq;
                 if (b1 == bq) c1 = aq;
             }
-            const U4 mw = philox((uint32_t)g, (uint32_t)k, (uint32_t)m, STREAM_MUT, k0, k1);
-            if ((uint64_t)mw.x < cfg.thr_pm) c0 = draw_below(mw.y, (uint32_t)N);
-            if ((uint64_t)mw.z < cfg.thr_pm) c1 = draw_below(mw.w, (uint32_t)N);
             if (j1 >= N) c1 = 0;
             const uint32_t cv = (uint32_t)c0 | ((uint32_t)c1 << 16);
             d2[m] = cv;
             if (s2) s2[m] = cv;
         }
+        mutate_child<LabT>(cfg, N, g, k, k0, k1, dst, lab_s, lane);
         return;
     }
     for (int m = lane; m < npair; m += 32) {
@@ -538,9 +603,6 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
             if (b0 == bq) c0 = aq;
             if (b1 == bq) c1 = aq;
         }
-        const U4 mw = philox((uint32_t)g, (uint32_t)k, (uint32_t)m, STREAM_MUT, k0, k1);
-        if ((uint64_t)mw.x < cfg.thr_pm) c0 = draw_below(mw.y, (uint32_t)N);
-        if ((uint64_t)mw.z < cfg.thr_pm) c1 = draw_below(mw.w, (uint32_t)N);
         dst[j0] = (LabT)c0;
         if (lab_s) lab_s[j0] = (uint16_t)c0;
         if (j1 < N) {
@@ -548,6 +610,7 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
             if (lab_s) lab_s[j1] = (uint16_t)c1;
         }
     }
+    mutate_child<LabT>(cfg, N, g, k, k0, k1, dst, lab_s, lane);
 }
 
 template <typename LabT>

@@ -222,3 +222,53 @@ def test_prim_order_is_a_maximum_spanning_tree(orc):
         tot += max(C[order[k], order[:k]])
     mst = sp.minimum_spanning_tree(-(C - np.eye(30)) + 10.0)  # shift keeps weights positive
     assert abs((-(mst.sum() - 10.0 * 29)) - tot) < 1e-9
+
+
+def _mutation_indicator(orc, P, N, pm, seed=21, labels=False):
+    """Per gene: did mutation change it? (pc = 0, no elites: child = parent + mutation)."""
+    rng = np.random.default_rng(seed)
+    pop = rng.integers(0, N, (P, N)).astype(np.int32)
+    L = rng.standard_normal(P)
+    prm = orc.params(P, N, elite=0, pc=0.0, pm=pm)
+    nxt, perm, par = orc.ga_evolve(pop, L, prm, seed=seed, g=5)
+    assert nxt.min() >= 0 and nxt.max() < N
+    x = nxt != pop[par]
+    return (x, nxt[x]) if labels else x
+
+
+def test_mutation_law_is_independent_per_gene(orc):
+    """Mutation is drawn as geometric gaps inside blocks of 16 genes; the law must
+    still be one independent Bernoulli(P_m) per gene: every position (first,
+    middle and last of a block, and of the short last block) mutates at the same
+    rate, neighbours are uncorrelated, and the count per child has the binomial
+    variance. A lost step after a mutated gene, a gap counted from the wrong
+    position or a block offset error shows up as a position bias or a
+    correlation."""
+    P, N, pm = 6000, 37, 0.25
+    x, new = _mutation_indicator(orc, P, N, pm, labels=True)
+    x = x.astype(np.float64)
+    # the new labels are uniform on [0, N) and independent of the gap draws
+    # (a label taken from the gap word would crowd the top of the range)
+    hist = np.bincount(new, minlength=N)
+    e = new.size / N
+    assert np.all(np.abs(hist - e) < 6 * math.sqrt(e)), hist
+    assert abs(new.mean() - (N - 1) / 2) < 6 * math.sqrt((N * N - 1) / 12 / new.size)
+    p = pm * (1 - 1 / N)  # a redrawn label equals the old one with probability 1/N
+    sd = math.sqrt(p * (1 - p) / P)
+    rates = x.mean(axis=0)
+    assert np.all(np.abs(rates - p) < 5 * sd), rates
+    for j in range(N - 1):  # neighbours, across block boundaries too (15|16, 31|32)
+        c = np.corrcoef(x[:, j], x[:, j + 1])[0, 1]
+        assert abs(c) < 5 / math.sqrt(P), (j, c)
+    counts = x.sum(axis=1)
+    assert abs(counts.var() - N * p * (1 - p)) < 0.1 * N * p * (1 - p)
+
+
+def test_mutation_extremes(orc):
+    """P_m = 1 replaces every gene (a block then needs eight Philox calls);
+    P_m below 2^-32 replaces none."""
+    P, N = 400, 50
+    x = _mutation_indicator(orc, P, N, 1.0)
+    frac = x.mean()
+    assert abs(frac - (1 - 1 / N)) < 5 * math.sqrt((1 / N) * (1 - 1 / N) / (P * N))
+    assert not _mutation_indicator(orc, P, N, 1e-12).any()
