@@ -154,11 +154,10 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 // ---------------------------------------------------------------------------
 // "Isolate fittest individuals" and the per-generation bookkeeping, one launch.
 // rank_i = #{j : (L_j, j) fitter than (L_i, i)} (key descending, index
-// ascending; NaN as -inf). CTA (x, y) loads the 256 keys of chunk y into
-// shared memory and counts, for each key i of chunk x, the fitter keys of
-// chunk y (256 comparisons per thread, broadcast reads, no barrier between
-// them); integer atomics sum the counts, so the ranks are exact and
-// order-independent.
+// ascending; NaN as -inf). CTA (x, y) sorts the 256 keys of chunk y
+// (bitonic, shuffles below distance 32, shared memory above) and counts, for
+// each key i of chunk x, the fitter keys of chunk y by binary search; integer
+// atomics sum the counts, so the ranks are exact and order-independent.
 // Tickets (no CTA ever waits): the last CTA of column x holds the final ranks
 // of chunk x and scatters perm[rank_i] = i (zeroing rank for the next use) and
 // its share of the mean; the last such column finisher does "evaluate state
@@ -194,20 +193,51 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
     uint64_t *s_part = sm.s_part;
     const int tid = threadIdx.x, nt = blockDim.x;
     {
-        // chunk y into shared memory (padding: key 0 with an index above every
-        // real one, fitter than no real key), then every key i of chunk x counts
-        // its fitter keys of chunk y one by one (broadcast reads, no barrier)
+        // chunk y sorted fitter-first by a bitonic network, one key per thread:
+        // exchanges at distance < 32 through warp shuffles, wider ones through
+        // shared memory (6 of the 36 stages); padding (key 0, index above every
+        // real one) sorts last and is fitter than no real key
         const int jy = blockIdx.y * RANK_CHUNK + tid;
-        sk[tid] = jy < P ? order_key(L[jy]) : 0ull;
-        si[tid] = jy < P ? jy : 0x7fffffff;
+        unsigned long long mk = jy < P ? order_key(L[jy]) : 0ull;
+        int mi = jy < P ? jy : 0x7fffffff;
         const int i = blockIdx.x * RANK_CHUNK + tid;
         const unsigned long long ki = i < P ? order_key(L[i]) : 0ull;
+        for (int k = 2; k <= RANK_CHUNK; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                unsigned long long pk;
+                int pi;
+                if (j >= 32) {
+                    sk[tid] = mk;
+                    si[tid] = mi;
+                    __syncthreads();
+                    pk = sk[tid ^ j];
+                    pi = si[tid ^ j];
+                    __syncthreads();
+                } else {
+                    pk = __shfl_xor_sync(0xffffffffu, mk, j);
+                    pi = __shfl_xor_sync(0xffffffffu, mi, j);
+                }
+                // the lower position of an ascending (fitter-first) block keeps
+                // the fitter key, and so on
+                const bool keep_fitter = ((tid & j) == 0) == ((tid & k) == 0);
+                const bool mine_fitter = fitter(mk, mi, pk, pi);
+                if (keep_fitter != mine_fitter) {
+                    mk = pk;
+                    mi = pi;
+                }
+            }
+        }
+        sk[tid] = mk;
+        si[tid] = mi;
         __syncthreads();
         if (i < P) {
-            int cnt = 0;
-#pragma unroll 8
-            for (int j = 0; j < RANK_CHUNK; ++j) cnt += fitter(sk[j], si[j], ki, i);
-            if (cnt) atomicAdd(&rank[i], cnt);
+            // fitter keys of chunk y form a prefix of the sorted chunk
+            int pos = 0;
+#pragma unroll
+            for (int step = RANK_CHUNK / 2; step; step >>= 1)
+                if (fitter(sk[pos + step - 1], si[pos + step - 1], ki, i)) pos += step;
+            if (fitter(sk[pos], si[pos], ki, i)) ++pos; // pos = RANK_CHUNK - 1 case
+            if (pos) atomicAdd(&rank[i], pos);
         }
     }
     // column ticket: the last of the nc CTAs of column x holds the final ranks

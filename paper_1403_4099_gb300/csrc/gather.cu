@@ -199,15 +199,22 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         }
     }
     __syncwarp();
-    // the terms, one lane per cluster (a running mantissa product per lane)
-    LogProd acc;
+    // the terms, one lane per cluster: two running mantissa products per lane
+    // (alternate clusters), so two independent multiply chains overlap
+    LogProd acc, acc2;
     acc.k = ksum;
     long long npairs = 0;
-    for (int c = lane; c < nlist; c += 32) {
+    for (int c = lane; c < nlist; c += 64) {
         const int n = list[c] & 0xffff;
         logprod_mul(acc, n, csum[c], DFIX_BITS);
         npairs += n * (n - 1) / 2;
+        if (c + 32 < nlist) {
+            const int n2 = list[c + 32] & 0xffff;
+            logprod_mul(acc2, n2, csum[c + 32], DFIX_BITS);
+            npairs += n2 * (n2 - 1) / 2;
+        }
     }
+    mant_mul(acc.m, acc.e, acc2.m, acc2.e); // (adds acc2's exponent too)
     if (pairs_out) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
