@@ -17,16 +17,21 @@
 
 namespace gpga {
 
-// per-warp shared-memory slice for Np padded genes (8 Np bytes). Counts and
-// fill pointers are 16-bit (N < 65536), two per 32-bit word (label 2w in the
-// low half of word w), updated with 32-bit shared-memory atomics: a half never
-// carries into its neighbour because no count or pointer exceeds N.
+// per-warp shared-memory slice for Np padded genes (8 Np bytes), in order:
+//   list  (2 Np bytes) int32 list of the non-singleton clusters, label order,
+//         (start << 16 | n), at most N/2 entries;
+//   cnt   (2 Np bytes) label counts, then cluster starts, then cluster ends;
+//   lab   (2 Np bytes) labels;
+//   mem   (2 Np bytes) gene indices grouped by label.
+// Counts and starts are 16-bit (N < 65536), two per 32-bit word (label 2w in
+// the low half of word w), updated with 32-bit shared-memory atomics: a half
+// never carries into its neighbour because no count or start exceeds N. After
+// the scatter, cnt and lab (contiguous) are dead and hold the pair sums.
 struct GatherSlice {
-    uint32_t *cnt;  // Np/2 words: label counts; later the list of big clusters
-    uint32_t *fill; // Np/2 words: cluster starts, cluster ends after the scatter
-    uint16_t *lab;  // Np: labels; after the scatter, the int32 list of
-                    // non-singleton clusters (start << 16 | n, at most N/2)
-    uint16_t *mem;  // Np: gene indices grouped by label
+    int *list;
+    uint32_t *cnt;
+    uint16_t *lab;
+    uint16_t *mem;
 };
 
 __host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 8; }
@@ -34,10 +39,10 @@ __host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np
 __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
 {
     GatherSlice s;
-    s.cnt = reinterpret_cast<uint32_t *>(base);
-    s.fill = s.cnt + Np / 2;
-    s.lab = reinterpret_cast<uint16_t *>(s.fill + Np / 2);
-    s.mem = s.lab + Np;
+    s.list = reinterpret_cast<int *>(base);
+    s.cnt = reinterpret_cast<uint32_t *>(base + (size_t)2 * Np);
+    s.lab = reinterpret_cast<uint16_t *>(base + (size_t)4 * Np);
+    s.mem = reinterpret_cast<uint16_t *>(base + (size_t)6 * Np);
     return s;
 }
 
@@ -93,60 +98,67 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         atomicAdd(&sl.cnt[s >> 1], 1u << ((s & 1) << 4));
     }
     __syncwarp();
-    // exclusive scan of the counts -> fill (cluster starts), 64 labels a step
-    int carry = 0;
-    for (int base = 0; base < nwd; base += 32) {
-        const int w = base + lane;
-        const uint32_t c2 = w < nwd ? sl.cnt[w] : 0u;
-        const int c0 = (int)(c2 & 0xffffu), c = c0 + (int)(c2 >> 16);
-        int v = c;
+    // cluster starts (exclusive scan of the counts, written over the counts)
+    // and the list of non-singleton clusters, in one pass: lane l takes the 4
+    // consecutive count words 4 l .. 4 l + 3 of each 128-word chunk
+    int nlist = 0;
+    {
+        int carry = 0;
+        for (int cb = 0; cb < nwd; cb += 128) {
+            const int w0 = cb + 4 * lane;
+            uint32_t c2[4];
+            int tot = 0, nns = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
+            for (int q = 0; q < 4; ++q) {
+                c2[q] = w0 + q < nwd ? sl.cnt[w0 + q] : 0u;
+                const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
+                tot += x0 + x1;
+                nns += (x0 >= 2) + (x1 >= 2);
+            }
+            int it = tot, in = nns; // inclusive scans over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t1 = __shfl_up_sync(0xffffffffu, it, o);
+                const int t2 = __shfl_up_sync(0xffffffffu, in, o);
+                if (lane >= o) {
+                    it += t1;
+                    in += t2;
+                }
+            }
+            int run = carry + it - tot, li = nlist + in - nns;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (w0 + q < nwd) {
+                    const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
+                    sl.cnt[w0 + q] = (uint32_t)run | ((uint32_t)(run + x0) << 16);
+                    if (x0 >= 2) sl.list[li++] = (run << 16) | x0;
+                    run += x0;
+                    if (x1 >= 2) sl.list[li++] = (run << 16) | x1;
+                    run += x1;
+                }
+            }
+            carry += __shfl_sync(0xffffffffu, it, 31);
+            nlist += __shfl_sync(0xffffffffu, in, 31);
         }
-        const int e = carry + v - c;
-        if (w < nwd) sl.fill[w] = (uint32_t)e | ((uint32_t)(e + c0) << 16);
-        carry += __shfl_sync(0xffffffffu, v, 31);
     }
     __syncwarp();
     // scatter gene indices by label (order inside a cluster is irrelevant: the
-    // pair sums below are exact integer sums); fill ends at each cluster's end
+    // pair sums below are exact integer sums)
     for (int i = lane; i < N; i += 32) {
         const int s = sl.lab[i], sh = (s & 1) << 4;
-        const uint32_t old = atomicAdd(&sl.fill[s >> 1], 1u << sh);
+        const uint32_t old = atomicAdd(&sl.cnt[s >> 1], 1u << sh);
         sl.mem[(old >> sh) & 0xffffu] = (uint16_t)i;
     }
     __syncwarp();
-    // list the non-singleton clusters in label order (the labels are dead now:
-    // the list takes their space)
-    int *list = reinterpret_cast<int *>(sl.lab);
-    int nlist = 0;
-    for (int base = 0; base < nwd; base += 32) {
-        const int w = base + lane;
-        uint32_t c2 = 0u, f2 = 0u;
-        if (w < nwd) {
-            c2 = sl.cnt[w];
-            f2 = sl.fill[w];
-        }
-        const int n0 = (int)(c2 & 0xffffu), n1 = (int)(c2 >> 16);
-        const int e0 = (int)(f2 & 0xffffu), e1 = (int)(f2 >> 16);
-        const bool k0 = n0 >= 2, k1 = n1 >= 2;
-        const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
-        int pos = nlist + __popc(m0 & lt) + __popc(m1 & lt);
-        if (k0) list[pos++] = ((e0 - n0) << 16) | n0;
-        if (k1) list[pos] = ((e1 - n1) << 16) | n1;
-        nlist += __popc(m0) + __popc(m1);
-    }
-    __syncwarp();
+    const int *list = sl.list;
     // Pair sums first, then the terms: the sums of the clusters hold no
     // dependency on one another, so a lane's loads of successive clusters
     // overlap instead of waiting behind each cluster's log-product step.
-    // csum (int64 per listed cluster) fills the dead count and fill words from
-    // the front, the list of big clusters (n > 8) from the back:
-    // 8 nlist + 4 nbig <= 4 N bytes.
+    // csum (int64 per listed cluster) fills the dead count and label space
+    // (4 Np contiguous bytes) from the front, the list of big clusters (n > 8)
+    // from the back: 8 nlist + 4 nbig <= 4 N bytes.
     long long *csum = reinterpret_cast<long long *>(sl.cnt);
-    int *big_end = reinterpret_cast<int *>(sl.fill + Np / 2);
+    int *big_end = reinterpret_cast<int *>(sl.lab + Np);
     int nbig = 0;
     long long ksum = 0; // sum of K(n_s) in 2^-44, loaded alongside the pair sums
     // small clusters: one lane each, all pair loads of the cluster at once
@@ -364,10 +376,13 @@ __global__ void __launch_bounds__(512, 2)
     }
 }
 
+// warps per CTA of the single-run gather kernels: 4 (measured at N=500,
+// P=4096: 1024 CTAs of 4 warps spread over the SMs more evenly than 512 of 8,
+// 4% less time per generation), fewer if the slices do not fit
 static int warps_for(int Np)
 {
     const size_t per = gather_slice_bytes(Np);
-    int nw = 8;
+    int nw = 4;
     while (nw > 1 && nw * per > (size_t)200 * 1024) nw >>= 1;
     return nw;
 }

@@ -565,7 +565,7 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
         const uint32_t *__restrict__ b2 = reinterpret_cast<const uint32_t *>(b);
         uint32_t *__restrict__ d2 = reinterpret_cast<uint32_t *>(dst);
         uint32_t *s2 = reinterpret_cast<uint32_t *>(lab_s);
-#pragma unroll 4
+#pragma unroll 8
         for (int m = lane; m < npair; m += 32) {
             const int j0 = 2 * m, j1 = 2 * m + 1;
             const uint32_t av = __ldg(a2 + m), bv = __ldg(b2 + m);
