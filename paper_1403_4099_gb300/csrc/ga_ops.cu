@@ -158,12 +158,12 @@ __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned l
 // (bitonic, shuffles below distance 32, shared memory above) and counts, for
 // each key i of chunk x, the fitter keys of chunk y by binary search; integer
 // atomics sum the counts, so the ranks are exact and order-independent.
-// Tickets (no CTA ever waits): the last CTA of column x holds the final ranks
-// of chunk x and scatters perm[rank_i] = i (zeroing rank for the next use) and
-// its share of the mean; the last such column finisher does "evaluate state
-// and statistics" (best, mean), the record of the best configuration and the
-// device clock, "determine if termination criteria are met", and for
-// proportional scaling the weights by rank with their inclusive prefix.
+// Ticket (no CTA ever waits): the last CTA scatters perm[rank_i] = i (zeroing
+// rank for the next use) and does "evaluate state and statistics" (best; the
+// mean from the fixed-point sum the CTAs of row 0 add), the record of the best
+// configuration and the device clock, "determine if termination criteria are
+// met", and for proportional scaling the weights by rank with their inclusive
+// prefix.
 // Stateful use: g = st->gen + gen_off.
 // ---------------------------------------------------------------------------
 constexpr int RANK_CHUNK = 256;
@@ -240,64 +240,67 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
             if (pos) atomicAdd(&rank[i], pos);
         }
     }
-    // column ticket: the last of the nc CTAs of column x holds the final ranks
-    // of chunk x, scatters them into perm and adds its share of the mean
+    // the population mean in fixed point 2^-30 (exact integer sum, non-finite
+    // fitness left out): the CTAs of row y = 0 add chunk x's share
+    if (st && blockIdx.y == 0) {
+        const int i = blockIdx.x * RANK_CHUNK + tid;
+        long long f = 0;
+        if (i < P) {
+            const double v = L[i];
+            if (isfinite(v)) f = __double2ll_rn(v * 1073741824.0);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if ((tid & 31) == 0 && f)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st->lsum), (unsigned long long)f);
+    }
+    // ticket: the last of the nc x nc CTAs holds the final ranks, scatters
+    // perm[rank_i] = i (zeroing rank for the next use) and does the
+    // generation's bookkeeping
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&ticket[1 + blockIdx.x], 1u) == gridDim.y - 1;
+    if (tid == 0) s_last = atomicAdd(&ticket[0], 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    {
-        const int i = blockIdx.x * RANK_CHUNK + tid;
-        if (i < P) {
-            perm[__ldcg(rank + i)] = i;
-            rank[i] = 0;
-        }
-        if (tid == 0) ticket[1 + blockIdx.x] = 0u;
-        if (st) {
-            // population mean in fixed point 2^-30 (exact integer sum; non-finite
-            // fitness left out)
-            long long f = 0;
-            if (i < P) {
-                const double v = L[i];
-                if (isfinite(v)) f = __double2ll_rn(v * 1073741824.0);
-            }
+    const int g = st ? __ldcg(&st->gen) + cfg.gen_off : 0; // (loaded while perm is built)
+    for (int i0 = tid; i0 < P; i0 += 16 * nt) { // 16 rank loads in flight per thread
+        int r[16];
 #pragma unroll
-            for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-            if ((tid & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&st->lsum),
-                                           (unsigned long long)f);
+        for (int u = 0; u < 16; ++u) {
+            const int i = i0 + u * nt;
+            r[u] = i < P ? __ldcg(rank + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int i = i0 + u * nt;
+            if (i < P) {
+                perm[r[u]] = i;
+                rank[i] = 0;
+            }
         }
     }
-    // global ticket: the last column finisher does the generation's bookkeeping
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&ticket[0], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    __syncthreads(); // perm is visible to the whole CTA
     if (tid == 0) ticket[0] = 0u;
-    const int bidx = __ldcg(perm);
+    const int bidx = perm[0];
     if (st) {
-        const int g = st->gen + cfg.gen_off;
         if (cfg.record && ring) {
             const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
             for (int j = tid; j < cfg.N; j += nt) ring[(size_t)g * cfg.N + j] = src[j];
         }
         if (tid == 0) {
+            // the loads first (independent), then the decisions, the mean last
             double best = L[bidx];
+            const long long lsum = __ldcg(&st->lsum);
+            const bool stall = cfg.tol >= 0.0 && cfg.stall_gens > 0 && g >= cfg.stall_gens;
+            const double prev = stall ? hist[g - cfg.stall_gens] : 0.0;
             if (isnan(best)) best = -INFINITY;
             st->gen = g;
             st->best = best;
             st->best_idx = bidx;
-            st->mean = (double)__ldcg(&st->lsum) * 9.313225746154785e-10 / (double)P;
-            st->lsum = 0;
             hist[g] = best;
             int done = g >= cfg.max_gens;
-            if (!done && cfg.tol >= 0.0 && cfg.stall_gens > 0 && g >= cfg.stall_gens) {
-                const double prev = hist[g - cfg.stall_gens];
-                done = (best - prev) <= cfg.tol * fmax(1.0, fabs(best));
-            }
+            if (!done && stall) done = (best - prev) <= cfg.tol * fmax(1.0, fabs(best));
             if (cfg.record && ts) {
                 unsigned long long t;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -305,6 +308,8 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
             }
             st->done = done;
             s_last = done;
+            st->mean = (double)lsum * 9.313225746154785e-10 / (double)P;
+            st->lsum = 0;
         }
         __syncthreads();
         if (s_last) return;
