@@ -410,9 +410,11 @@ template int launch_assemble<int32_t>(const int32_t *const *, int, int, const fl
 // ---------------------------------------------------------------------------
 // Final re-score of one configuration in FP64 straight from C (Eq. 5, 6, 8),
 // plus its canonical relabelling (first occurrence -> 0, 1, 2, ...). One CTA.
-// Row sums are sequential in j; cluster sums run over members in ascending i
-// (one thread per cluster); the terms are added in first-occurrence order with
-// compensation, as 32 contiguous runs whose partial sums are then added in order.
+// Canonical ids from the first gene of each label (atomicMin) and a block scan;
+// row sums are sequential in j; cluster sums run over members in ascending i
+// (one thread per cluster); the terms, in canonical order, are summed with
+// compensation as 32 contiguous runs whose (sum, error) pairs are combined by
+// a two-sum butterfly (error of the total about one ulp).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void neu_add(double &s, double &c, double x)
 {
@@ -424,6 +426,15 @@ __device__ __forceinline__ void neu_add(double &s, double &c, double x)
     s = t;
 }
 
+// s + c += x exactly (Knuth's two-sum): the rounded sum and its error
+__device__ __forceinline__ void two_sum_add(double &s, double &c, double x)
+{
+    const double t = s + x;
+    const double bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
 __global__ void __launch_bounds__(1024)
     rescore_kernel(const uint16_t *pop0, const uint16_t *pop1, int ldp,
                    const DevState *__restrict__ st, const double *__restrict__ C, int N,
@@ -431,50 +442,73 @@ __global__ void __launch_bounds__(1024)
 {
     const uint16_t *lab = ((st->gen & 1) ? pop1 : pop0) + (size_t)st->best_idx * ldp;
     extern __shared__ double sm_d[];
-    double *rc = sm_d;          // N row sums of C over same-cluster columns
-    double *rd = sm_d + N;      // N row sums of (1 - C)
+    double *rc = sm_d;           // N row sums of C over same-cluster columns
+    double *rd = sm_d + N;       // N row sums of (1 - C)
     double *term = sm_d + 2 * N; // per canonical cluster: its Eq. 8 term (0 for singletons)
     int *li = reinterpret_cast<int *>(sm_d + 3 * N); // labels
-    int *map = li + N;          // label -> canonical id
-    int *rep = map + N;         // canonical id -> label
-    __shared__ int s_k;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    int *first = li + N;         // label -> first gene carrying it (N if none)
+    int *pos = first + N;        // gene -> canonical id of a first occurrence (scan)
+    __shared__ int s_part[32];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < N; i += nt) {
         li[i] = lab[i];
-        map[i] = -1;
+        first[i] = N;
     }
     __syncthreads();
-    // canonical ids by first occurrence (integer work only)
-    if (threadIdx.x == 0) {
-        int next = 0;
-        for (int i = 0; i < N; ++i) {
-            const int s = li[i];
-            if (map[s] < 0) {
-                map[s] = next;
-                rep[next++] = s;
-            }
-        }
-        s_k = next;
+    for (int i = tid; i < N; i += nt) atomicMin(&first[li[i]], i);
+    __syncthreads();
+    // canonical ids by first occurrence: exclusive scan of the first-occurrence
+    // flags over the genes (chunked: thread t scans genes t*chunk ..)
+    const int chunk = (N + nt - 1) / nt;
+    const int lo = min(N, tid * chunk), hi = min(N, lo + chunk);
+    int cnt = 0;
+    for (int i = lo; i < hi; ++i) cnt += first[li[i]] == i;
+    int v = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    if (lane == 31) s_part[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (nt >> 5) ? s_part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_part[lane] = w; // inclusive per warp
+    }
+    __syncthreads();
+    int run = v - cnt + (wid ? s_part[wid - 1] : 0);
+    for (int i = lo; i < hi; ++i) {
+        pos[i] = run;
+        if (first[li[i]] == i) ++run;
+    }
+    const int K = s_part[(nt >> 5) - 1];
+    __syncthreads();
+    // row sums over the gene's cluster, sequential in j
+    for (int i = tid; i < N; i += nt) {
         double sc = 0.0, cc = 0.0, sd = 0.0, cd = 0.0;
         const int si = li[i];
-        for (int j = 0; j < N; ++j) {
+        for (int j = first[si]; j < N; ++j) {
             if (li[j] != si) continue;
-            const double v = C[(size_t)i * N + j];
-            neu_add(sc, cc, v);
-            neu_add(sd, cd, 1.0 - v);
+            const double x = C[(size_t)i * N + j];
+            neu_add(sc, cc, x);
+            neu_add(sd, cd, 1.0 - x);
         }
         rc[i] = sc + cc;
         rd[i] = sd + cd;
     }
     __syncthreads();
-    const int K = s_k;
     // one thread per cluster: member sums in ascending index, then its term
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const int s = rep[k];
+    for (int i = tid; i < N; i += nt) {
+        const int s = li[i];
+        if (first[s] != i) continue; // i opens cluster s
         int n = 0;
         double c = 0.0, cc = 0.0, d = 0.0, dc = 0.0;
-        for (int j = 0; j < N; ++j) {
+        for (int j = i; j < N; ++j) {
             if (li[j] != s) continue;
             ++n;
             neu_add(c, cc, rc[j]);
@@ -489,27 +523,32 @@ __global__ void __launch_bounds__(1024)
             if (!(ds >= dn * (dn - 1.0) * eps)) ds = dn * (dn - 1.0) * eps;
             t = 0.5 * (log(dn / cs) + (dn - 1.0) * log((dn * dn - dn) / ds));
         }
-        term[k] = t;
+        term[pos[i]] = t;
     }
     __syncthreads();
-    // terms in canonical order: each lane of warp 0 sums a contiguous run with
-    // compensation, then lane 0 adds the 32 partial sums in lane order
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    // terms in canonical order: lane l of warp 0 sums a contiguous run with
+    // compensation, then the 32 (sum, error) pairs are combined by a two-sum
+    // butterfly
+    if (wid == 0) {
         const int per = (K + 31) / 32;
-        const int lo = min(K, lane * per), hi = min(K, lo + per);
-        double a = 0.0, ac = 0.0;
-        for (int k = lo; k < hi; ++k) neu_add(a, ac, term[k]);
-        double acc = 0.0, comp = 0.0;
-        for (int l = 0; l < 32; ++l) {
-            const double pa = __shfl_sync(0xffffffffu, a, l);
-            const double pc = __shfl_sync(0xffffffffu, ac, l);
-            neu_add(acc, comp, pa);
-            neu_add(acc, comp, pc);
+        const int a0 = min(K, lane * per), a1 = min(K, a0 + per);
+        double s = 0.0, c = 0.0;
+        for (int k = a0; k < a1; ++k) two_sum_add(s, c, term[k]);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            // the lower lane of each pair keeps the sum in lane order
+            const bool low = (lane & o) == 0;
+            double x = low ? s : s2, y = low ? s2 : s;
+            double e = low ? c + c2 : c2 + c;
+            two_sum_add(x, e, y);
+            s = x;
+            c = e;
         }
-        if (lane == 0) *L_out = acc + comp;
+        if (lane == 0) *L_out = s + c;
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) canon[i] = map[li[i]];
+    for (int i = tid; i < N; i += nt) canon[i] = pos[first[li[i]]];
 }
 
 int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
