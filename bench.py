@@ -269,7 +269,7 @@ def run_gpu(args, ranks):
         NTt = min(256, Np)
         tg = G if G % GRAPH_GENS else G - GRAPH_GENS + 1  # the timed generation
         cols = float(hist["clusters"][tg]) if tg < len(hist["clusters"]) else 0.0
-        n_ct = int(np.ceil(cols / 128.0))
+        n_ct = 2 * int(np.ceil(cols / 256.0))  # pairs of 128-column tiles per CTA
         flops = n_ct * int(np.ceil(Np / NTt)) * 2 * 2.0 * 128 * NTt * Np
         t = main_ms / 1e3
         peak = pk["bf16_tflops_sustained"]

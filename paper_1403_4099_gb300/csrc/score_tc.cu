@@ -29,15 +29,16 @@
 
 namespace gpga {
 
-constexpr int TC_M = 128;     // cluster columns per tile (MMA M)
+constexpr int TC_M = 128;     // cluster columns per accumulator (MMA M)
+constexpr int TC_ACC = 2;     // accumulators per CTA: 256 columns share every D tile
 constexpr int TC_NT = 256;    // rows of D per tile (MMA N, largest)
 constexpr int TC_KB = 64;     // genes per K-block: one 128-byte row of BF16
 constexpr int TC_THREADS = 128;
-constexpr int A_BYTES = TC_M * TC_KB * 2;           // 16 KB
-constexpr int B_BYTES = TC_NT * TC_KB * 2;          // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // 80 KB
+constexpr int A_BYTES = TC_M * TC_KB * 2;                     // 16 KB per accumulator
+constexpr int B_BYTES = TC_NT * TC_KB * 2;                    // 32 KB
+constexpr int STAGE_BYTES = TC_ACC * A_BYTES + 2 * B_BYTES;   // 96 KB
 constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024 + 256;
-constexpr int TC_TMEM_COLS = 256;
+constexpr int TC_TMEM_COLS = 512; // TC_ACC accumulators of TC_NT FP32 columns
 
 // ---------------------------------------------------------------------------
 // scratch layout
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t stage_addr[2] = {raw + pad, raw + pad + STAGE_BYTES};
 
     const int ncols = (int)*w.ncols;
-    const int nct = (ncols + TC_M - 1) / TC_M;
+    const int nct = (ncols + TC_ACC * TC_M - 1) / (TC_ACC * TC_M);
     const int nnt = (Np + NT - 1) / NT;
     const int units = nct * nnt;
     if ((int)blockIdx.x >= units) return;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int it = 0; // K-blocks issued by this CTA (stage = it & 1, use = it >> 1)
     for (int u = blockIdx.x; u < units && !s_abort; u += gridDim.x) {
         const int ct = u / nnt, nt = u - ct * nnt;
-        const int c0 = ct * TC_M, n0 = nt * NT;
+        const int c0 = ct * TC_ACC * TC_M, n0 = nt * NT;
         for (int kb = 0; kb < KB; ++kb, ++it) {
             const int s = it & 1;
             if (it >= 2) { // the MMAs that read this stage two K-blocks ago are done
@@ -285,15 +286,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             unsigned char *A = stage_ptr[s];
             const uint32_t Aaddr = stage_addr[s];
-            const uint32_t Bh = Aaddr + A_BYTES, Bl = Aaddr + A_BYTES + B_BYTES;
-            // one-hot rows from the membership bits (thread = column)
-            {
-                const int col = c0 + tid;
+            const uint32_t Bh = Aaddr + TC_ACC * A_BYTES, Bl = Bh + B_BYTES;
+            // one-hot rows from the membership bits (thread = column of each
+            // accumulator's tile)
+#pragma unroll
+            for (int acc = 0; acc < TC_ACC; ++acc) {
+                const int col = c0 + acc * TC_M + tid;
                 uint32_t w0 = 0u, w1 = 0u;
                 if (col < ncols) {
                     w0 = w.bits[(size_t)col * W + 2 * kb];
                     w1 = w.bits[(size_t)col * W + 2 * kb + 1];
                 }
+                unsigned char *Aa = A + acc * A_BYTES;
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {
                     const uint32_t byte = ((ch < 4 ? w0 : w1) >> (8 * (ch & 3))) & 0xffu;
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int h = 0; h < 4; ++h)
                         q[h] = ((byte >> (2 * h)) & 1u ? 0x3F80u : 0u) |
                                ((byte >> (2 * h + 1)) & 1u ? 0x3F800000u : 0u);
-                    *reinterpret_cast<uint4 *>(A + tid * 128 + ((ch ^ (tid & 7)) * 16)) =
+                    *reinterpret_cast<uint4 *>(Aa + tid * 128 + ((ch ^ (tid & 7)) * 16)) =
                         make_uint4(q[0], q[1], q[2], q[3]);
                 }
             }
@@ -323,9 +327,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                 for (int kk = 0; kk < TC_KB / 16; ++kk) {
-                    const uint64_t ad = sw128_desc(Aaddr + 32 * kk);
-                    mma_bf16(tmem, ad, sw128_desc(Bh + 32 * kk), idesc, (kb | kk) ? 1u : 0u);
-                    mma_bf16(tmem, ad, sw128_desc(Bl + 32 * kk), idesc, 1u);
+                    const uint64_t bh = sw128_desc(Bh + 32 * kk), bl = sw128_desc(Bl + 32 * kk);
+#pragma unroll
+                    for (int acc = 0; acc < TC_ACC; ++acc) {
+                        const uint64_t ad = sw128_desc(Aaddr + acc * A_BYTES + 32 * kk);
+                        const uint32_t t = tmem + (uint32_t)(acc * TC_NT);
+                        mma_bf16(t, ad, bh, idesc, (kb | kk) ? 1u : 0u);
+                        mma_bf16(t, ad, bl, idesc, 1u);
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&mbar[s]))
@@ -339,10 +348,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncthreads();
         if (s_abort) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        {
-            const int col = c0 + tid;
+#pragma unroll 1
+        for (int a2 = 0; a2 < TC_ACC; ++a2) {
+            const int col = c0 + a2 * TC_M + tid;
             float acc = 0.f;
-            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+            const uint32_t lane_base = ((uint32_t)(warp * 32) << 16) + (uint32_t)(a2 * TC_NT);
             for (int q = 0; q < NT / 32; ++q) {
                 uint32_t v[32];
                 asm volatile(
