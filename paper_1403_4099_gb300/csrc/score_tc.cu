@@ -277,6 +277,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int u = blockIdx.x; u < units && !s_abort; u += gridDim.x) {
         const int ct = u / nnt, nt = u - ct * nnt;
         const int c0 = ct * TC_ACC * TC_M, n0 = nt * NT;
+        // membership words of the current K-block, prefetched one block ahead
+        uint32_t bw[TC_ACC][2];
+#pragma unroll
+        for (int acc = 0; acc < TC_ACC; ++acc) {
+            const int col = c0 + acc * TC_M + tid;
+            bw[acc][0] = col < ncols ? w.bits[(size_t)col * W] : 0u;
+            bw[acc][1] = col < ncols ? w.bits[(size_t)col * W + 1] : 0u;
+        }
         for (int kb = 0; kb < KB; ++kb, ++it) {
             const int s = it & 1;
             if (it >= 2) { // the MMAs that read this stage two K-blocks ago are done
@@ -287,15 +295,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             unsigned char *A = stage_ptr[s];
             const uint32_t Aaddr = stage_addr[s];
             const uint32_t Bh = Aaddr + TC_ACC * A_BYTES, Bl = Bh + B_BYTES;
+            // D tiles first (their latency overlaps the one-hot build): rows n0..
+            // (N = NT), genes 64 kb.. of D_hi and D_lo
+            for (int q = tid; q < NT * 8; q += TC_THREADS) {
+                const int row = q >> 3, ch = q & 7;
+                const int gi = n0 + row;
+                const bool in = gi < Np;
+                const size_t off = (size_t)(in ? gi : 0) * Np + (size_t)kb * TC_KB + ch * 8;
+                const uint32_t dofs = row * 128 + ((ch ^ (row & 7)) * 16);
+                cp_async16(Bh + dofs, Dhi + off, in ? 16 : 0);
+                cp_async16(Bl + dofs, Dlo + off, in ? 16 : 0);
+            }
             // one-hot rows from the membership bits (thread = column of each
             // accumulator's tile)
 #pragma unroll
             for (int acc = 0; acc < TC_ACC; ++acc) {
                 const int col = c0 + acc * TC_M + tid;
-                uint32_t w0 = 0u, w1 = 0u;
-                if (col < ncols) {
-                    w0 = w.bits[(size_t)col * W + 2 * kb];
-                    w1 = w.bits[(size_t)col * W + 2 * kb + 1];
+                const uint32_t w0 = bw[acc][0], w1 = bw[acc][1];
+                if (kb + 1 < KB) {
+                    bw[acc][0] = col < ncols ? w.bits[(size_t)col * W + 2 * kb + 2] : 0u;
+                    bw[acc][1] = col < ncols ? w.bits[(size_t)col * W + 2 * kb + 3] : 0u;
                 }
                 unsigned char *Aa = A + acc * A_BYTES;
 #pragma unroll
@@ -309,16 +328,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     *reinterpret_cast<uint4 *>(Aa + tid * 128 + ((ch ^ (tid & 7)) * 16)) =
                         make_uint4(q[0], q[1], q[2], q[3]);
                 }
-            }
-            // D tiles: rows n0.. (N = NT), genes 64 kb.. of D_hi and D_lo
-            for (int q = tid; q < NT * 8; q += TC_THREADS) {
-                const int row = q >> 3, ch = q & 7;
-                const int gi = n0 + row;
-                const bool in = gi < Np;
-                const size_t off = (size_t)(in ? gi : 0) * Np + (size_t)kb * TC_KB + ch * 8;
-                const uint32_t dofs = row * 128 + ((ch ^ (row & 7)) * 16);
-                cp_async16(Bh + dofs, Dhi + off, in ? 16 : 0);
-                cp_async16(Bl + dofs, Dlo + off, in ? 16 : 0);
             }
             asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
