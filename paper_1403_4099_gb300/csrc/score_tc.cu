@@ -285,27 +285,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bw[acc][0] = col < ncols ? w.bits[(size_t)col * W] : 0u;
             bw[acc][1] = col < ncols ? w.bits[(size_t)col * W + 1] : 0u;
         }
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-            const int s = it & 1;
-            if (it >= 2) { // the MMAs that read this stage two K-blocks ago are done
-                if (tid == 0 && !mbar_wait(smem_u32(&mbar[s]), ((it - 2) >> 1) & 1)) s_abort = 1;
-                __syncthreads();
-                if (s_abort) break;
-            }
-            unsigned char *A = stage_ptr[s];
-            const uint32_t Aaddr = stage_addr[s];
-            const uint32_t Bh = Aaddr + TC_ACC * A_BYTES, Bl = Bh + B_BYTES;
-            // D tiles first (their latency overlaps the one-hot build): rows n0..
-            // (N = NT), genes 64 kb.. of D_hi and D_lo
+        // D tiles of K-block kb into stage s (all threads; one commit group)
+        auto copy_d = [&](int kb, int s) {
+            const uint32_t bh = stage_addr[s] + TC_ACC * A_BYTES, bl = bh + B_BYTES;
             for (int q = tid; q < NT * 8; q += TC_THREADS) {
                 const int row = q >> 3, ch = q & 7;
                 const int gi = n0 + row;
                 const bool in = gi < Np;
                 const size_t off = (size_t)(in ? gi : 0) * Np + (size_t)kb * TC_KB + ch * 8;
                 const uint32_t dofs = row * 128 + ((ch ^ (row & 7)) * 16);
-                cp_async16(Bh + dofs, Dhi + off, in ? 16 : 0);
-                cp_async16(Bl + dofs, Dlo + off, in ? 16 : 0);
+                cp_async16(bh + dofs, Dhi + off, in ? 16 : 0);
+                cp_async16(bl + dofs, Dlo + off, in ? 16 : 0);
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        // software pipeline over the K-blocks of this unit: the D tiles of block
+        // kb + 1 stream into the other stage while the MMAs of block kb run
+        // (every MMA of the previous unit is complete: its epilogue waited)
+        copy_d(0, it & 1);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+            const int s = it & 1;
+            unsigned char *A = stage_ptr[s];
+            const uint32_t Aaddr = stage_addr[s];
+            const uint32_t Bh = Aaddr + TC_ACC * A_BYTES, Bl = Bh + B_BYTES;
             // one-hot rows from the membership bits (thread = column of each
             // accumulator's tile)
 #pragma unroll
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         make_uint4(q[0], q[1], q[2], q[3]);
                 }
             }
-            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+            asm volatile("cp.async.wait_group 0;" ::: "memory"); // block kb's D tiles
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
@@ -348,6 +350,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&mbar[s]))
                              : "memory");
+            }
+            if (kb + 1 < KB) {
+                // the other stage is free once the MMAs of the previous block are done
+                if (it >= 1) {
+                    if (tid == 0 && !mbar_wait(smem_u32(&mbar[(it - 1) & 1]), ((it - 1) >> 1) & 1))
+                        s_abort = 1;
+                    __syncthreads();
+                    if (s_abort) {
+                        ++it;
+                        break;
+                    }
+                }
+                copy_d(kb + 1, s ^ 1);
             }
         }
         if (s_abort) break;
