@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recover", action="store_true")
-    ap.add_argument("--workload", default="planted", choices=["planted", "batched", "serving"],
+    ap.add_argument("--workload", default="planted",
+                    choices=["planted", "batched", "serving", "paper"],
                     help="planted: the N=500 headline; batched: 256 sliding intraday windows "
-                         "in one fleet; serving: Poisson request stream")
+                         "in one fleet; serving: Poisson request stream; paper: the paper's "
+                         "shapes (40-stock training set, 18-stock 1760-window stream, Table 3 "
+                         "parameters, a P_m x P_c sweep)")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
@@ -606,6 +609,102 @@ def run_serving(args, ranks):
     runtime.barrier(ranks)
 
 
+# ---------------------------------------------------------------------------
+# Paper-shaped workload (Sec. 4, Table 3): P = 1000, at most 400 generations,
+# P_c = 0.9, P_kb = 0.9, P_m = 0.1 per gene, tolerance 1e-5 over 50 stall
+# generations, 10 elites. (1) the 40-stock training set, (2) a P_m x P_c sweep
+# on it (8 seeds each), (3) the 18-stock stream of 1760 windows of 1800 bars
+# as one fleet.
+# ---------------------------------------------------------------------------
+def _table3(gpga, **kw):
+    base = dict(P=1000, elite=10, max_gens=400, stall_gens=50, tol=1e-5, pc=0.9, pkb=0.9,
+                pm=0.1, form=gpga.FORM_GATHER)
+    base.update(kw)
+    return gpga.default_params(**base)
+
+
+def run_paper(args, ranks):
+    import torch
+
+    from paper_1403_4099_gb300 import gpga, metrics, runtime, synth
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    runtime.init_dist(ranks, "nccl")
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        # (1) training set, one run with the history recorded
+        tr = synth.paper_training(replicate=ranks.rank)
+        C = gpga.cluster_corr(torch.from_numpy(tr.R).to(dev), stream=stream)
+        ga = gpga.GA(C, _table3(gpga, record=1), seed=21, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        while not ga.step(8, wait=True):
+            pass
+        e1.record(stream)
+        stream.synchronize()
+        h = ga.history()
+        lab, L, g = ga.best()
+        ga.close()
+        ari = [metrics.ari(l, tr.truth) for l in h["labels"]]
+        rec = next((k for k, a in enumerate(ari) if a >= 0.99), None)
+        out["training_40"] = {"generations": int(g), "final_ari": float(metrics.ari(lab, tr.truth)),
+                              "first_generation_ari_0.99": rec, "L": float(L),
+                              "ms": float(e0.elapsed_time(e1))}
+        # (2) sweep: 8 seeds per (P_m, P_c), each combination one batch
+        sweep = []
+        for pm in (0.01, 0.05, 0.1):
+            for pc in (0.6, 0.9):
+                b = gpga.Batch([C] * 8, _table3(gpga, pm=pm, pc=pc), [100 + k for k in range(8)],
+                               stream=stream)
+                while b.step(16) > 0:
+                    pass
+                gens, _, _ = b.status()
+                aris = [metrics.ari(b.best(k)[0], tr.truth) for k in range(8)]
+                b.close()
+                sweep.append({"pm": pm, "pc": pc, "recovered": int(sum(a >= 0.99 for a in aris)),
+                              "of": 8, "mean_ari": float(np.mean(aris)),
+                              "mean_generations": float(np.mean(gens))})
+        out["sweep_training_40"] = sweep
+        # (3) the stream: 1760 windows as one fleet
+        st = synth.paper_stream(replicate=ranks.rank)
+        R = torch.from_numpy(st.R).to(dev)
+        Cs = [torch.empty((18, 18), dtype=torch.float64, device=dev) for _ in range(st.windows)]
+        runtime.barrier(ranks)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for k in range(st.windows):
+            gpga.cluster_corr(R[k:k + st.W], Cs[k], stream)
+        b = gpga.Batch(Cs, _table3(gpga), [5000 + k for k in range(st.windows)], stream=stream)
+        while b.step(16) > 0:
+            pass
+        stream.synchronize()
+        secs = time.perf_counter() - t0
+        gens, _, _ = b.status()
+        sample = range(0, st.windows, 40)
+        aris = [metrics.ari(b.best(k)[0], st.truth) for k in sample]
+        b.close()
+    max_secs, total = runtime.aggregate(ranks, secs, float(st.windows), device=dev)
+    evals = float(1000 * np.sum(gens + 1))
+    if ranks.rank == 0:
+        line = {"metric": "windows/s (18-stock stream: 1760 windows of 1800 bars, Table 3 "
+                          "parameters, each run to 400 generations or stall)",
+                "value": total / max_secs, "unit": "windows/s", "n_gpus": ranks.world,
+                "steps": 1, "warmup": 0, "ms_per_step": 1e3 * max_secs,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "paper_stream_n18_w1800_x1760_p1000", "P": 1000,
+                           "max_gens": 400, "pm": 0.1, "pc": 0.9, "pkb": 0.9, "elite": 10},
+                "evals_per_s": evals / secs,
+                "generations": {"mean": float(np.mean(gens)), "min": int(gens.min()),
+                                "max": int(gens.max())},
+                "stream_ari_sampled": {"n": len(aris), "mean": float(np.mean(aris)),
+                                       "min": float(np.min(aris))},
+                **out}
+        print(json.dumps(line), flush=True)
+    runtime.barrier(ranks)
+
+
 def main():
     args = parse()
     from paper_1403_4099_gb300 import runtime
@@ -618,6 +717,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, ranks)
+        return
+    if args.workload == "paper":
+        run_paper(args, ranks)
         return
     run_gpu(args, ranks)
 

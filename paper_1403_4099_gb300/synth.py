@@ -189,3 +189,32 @@ def window_subsets(N: int, windows: int, nmin: int = 20, nmax: int | None = None
         n = int(rng.integers(nmin, nmax + 1))
         out.append(np.sort(rng.choice(N, size=n, replace=False)).astype(np.int32))
     return out
+
+
+# --- paper-shaped workloads (Sec. 4: a 40-stock training set with 4 planted
+# clusters; an 18-stock test stream, ~1800 bars per window, 1760 windows) ----
+
+def paper_training(replicate: int = 0, T: int = 1800, g: float = 0.5) -> Planted:
+    """40 simulated stocks in 4 disjoint planted clusters of 10 (no market mode,
+    no noise series); T and g are ours (the paper states neither)."""
+    rng = np.random.default_rng(seed_for(6, replicate))
+    return planted_returns(rng, T, [10, 10, 10, 10], g)
+
+
+@dataclass
+class Stream:
+    R: np.ndarray       # (W + windows - 1) x N returns
+    truth: np.ndarray   # N planted labels
+    W: int              # bars per window
+    windows: int        # window k covers bars [k, k + W)
+
+
+def paper_stream(N: int = 18, W: int = 1800, windows: int = 1760, replicate: int = 0) -> Stream:
+    """An 18-stock series of W + windows - 1 bars with 3 planted clusters of 6
+    (g ~ U[0.2, 0.8], market loading 0.3): the shape of the paper's test set,
+    1760 windows of about 1800 three-minute bars, each window one step later."""
+    rng = np.random.default_rng(seed_for(6, 100 + replicate))
+    k = 3
+    g = rng.uniform(0.2, 0.8, size=k)
+    pl = planted_returns(rng, W + windows - 1, [N // k] * k, g, beta=0.3)
+    return Stream(pl.R, pl.truth, W, windows)

@@ -272,3 +272,15 @@ def test_mutation_extremes(orc):
     frac = x.mean()
     assert abs(frac - (1 - 1 / N)) < 5 * math.sqrt((1 / N) * (1 - 1 / N) / (P * N))
     assert not _mutation_indicator(orc, P, N, 1e-12).any()
+
+
+def test_paper_shaped_inputs():
+    """The paper-shaped generators: 40 stocks in 4 clusters of 10; an 18-stock
+    series long enough for 1760 windows of 1800 bars with 3 clusters of 6."""
+    from paper_1403_4099_gb300 import synth
+    tr = synth.paper_training()
+    assert tr.R.shape == (1800, 40)
+    assert sorted(np.bincount(tr.truth).tolist()) == [10, 10, 10, 10]
+    st = synth.paper_stream()
+    assert st.R.shape == (1800 + 1760 - 1, 18) and st.W == 1800 and st.windows == 1760
+    assert sorted(np.bincount(st.truth).tolist()) == [6, 6, 6]
