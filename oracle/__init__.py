@@ -110,6 +110,8 @@ def _load():
             "orc_brute_force": (ct.c_int, [f64p, ct.c_int, i32p, ct.POINTER(ct.c_double),
                                            ct.POINTER(ct.c_int64)]),
             "orc_ari": (ct.c_double, [i32p, i32p, ct.c_int]),
+            "orc_cluster_mst": (ct.c_int, [i32p, ct.c_int, f64p, i32p, i32p, f64p,
+                                           ct.POINTER(ct.c_int32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -290,3 +292,17 @@ def brute_force(C):
 def ari(a, b) -> float:
     a = _i32(a)
     return float(_load().orc_ari(a, _i32(b), a.shape[0]))
+
+
+def cluster_mst(s, C):
+    """Per-cluster minimum spanning trees on d = sqrt(2 (1 - C)) (Kruskal):
+    (u, v, d) arrays, clusters in first-occurrence order, u < v."""
+    s = _i32(s)
+    N = s.shape[0]
+    eu = np.zeros(max(N, 1), np.int32)
+    ev = np.zeros(max(N, 1), np.int32)
+    ew = np.zeros(max(N, 1), np.float64)
+    n = ct.c_int32()
+    _check(_load().orc_cluster_mst(s, N, _f64(C), eu, ev, ew, ct.byref(n)), "cluster_mst")
+    k = n.value
+    return eu[:k], ev[:k], ew[:k]

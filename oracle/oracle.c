@@ -792,6 +792,82 @@ int orc_brute_force(const double *C, int N, int32_t *best, double *bestL, int64_
 /*   E   = sum_i C(a_i,2) sum_j C(b_j,2) / C(N,2).                              */
 /* The denominator vanishes only when both are all-singleton or both a single  */
 /* cluster, i.e. identical: 1 is returned. NaN on bad labels.                  */
+/* Minimum spanning tree of every cluster of configuration s (the trees the
+ * paper draws for the clusters it finds, Sec. 4), on the correlation distance
+ * d_ij = sqrt(2 (1 - C_ij)), by Kruskal's algorithm: the cluster's pairs
+ * i < j sorted by (d, i, j), each joining two components kept (union-find).
+ * Output, clusters in first-occurrence order, for each its n_s - 1 edges
+ * (u < v, d) in Kruskal order; *n_edges = N - number of clusters.
+ * Arrays eu, ev, ew hold at least N entries. */
+typedef struct {
+    double d;
+    int32_t u, v;
+} mst_edge;
+
+static int mst_edge_cmp(const void *a, const void *b)
+{
+    const mst_edge *x = (const mst_edge *)a, *y = (const mst_edge *)b;
+    if (x->d < y->d) return -1;
+    if (x->d > y->d) return 1;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    return 0;
+}
+
+int orc_cluster_mst(const int32_t *s, int N, const double *C, int32_t *eu, int32_t *ev,
+                    double *ew, int32_t *n_edges)
+{
+    if (!s || !C || !eu || !ev || !ew || !n_edges || N < 1) return ORC_ERR_ARG;
+    for (int i = 0; i < N; ++i)
+        if (s[i] < 0 || s[i] >= N) return ORC_ERR_ARG;
+    int32_t *seen = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    int32_t *mem = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int32_t *par = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    mst_edge *e = (mst_edge *)malloc(((size_t)N * (N - 1) / 2 + 1) * sizeof(mst_edge));
+    if (!seen || !mem || !par || !e) {
+        free(seen);
+        free(mem);
+        free(par);
+        free(e);
+        return ORC_ERR_OOM;
+    }
+    int out = 0;
+    for (int i = 0; i < N; ++i) {
+        const int32_t lab = s[i];
+        if (seen[lab]) continue;
+        seen[lab] = 1;
+        int n = 0;
+        for (int j = i; j < N; ++j)
+            if (s[j] == lab) mem[n++] = j;
+        size_t m = 0;
+        for (int a = 0; a < n; ++a)
+            for (int b = a + 1; b < n; ++b) {
+                const double c = C[(size_t)mem[a] * N + mem[b]];
+                e[m].d = sqrt(2.0 * (1.0 - c));
+                e[m].u = mem[a];
+                e[m].v = mem[b];
+                ++m;
+            }
+        qsort(e, m, sizeof(mst_edge), mst_edge_cmp);
+        for (int a = 0; a < n; ++a) par[mem[a]] = mem[a];
+        for (size_t k = 0; k < m; ++k) {
+            const int ru = uf_find(par, e[k].u), rv = uf_find(par, e[k].v);
+            if (ru == rv) continue;
+            par[ru] = rv;
+            eu[out] = e[k].u;
+            ev[out] = e[k].v;
+            ew[out] = e[k].d;
+            ++out;
+        }
+    }
+    *n_edges = out;
+    free(seen);
+    free(mem);
+    free(par);
+    free(e);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 double orc_ari(const int32_t *x, const int32_t *y, int N)
 {
