@@ -228,6 +228,23 @@ GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count);
 GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
 
 /*
+ * cluster_mst -- minimum spanning tree of every cluster of one configuration
+ * (the cluster trees the paper draws for the clusters it finds, Sec. 4), on
+ * the correlation distance d_ij = sqrt(2 (1 - C_ij)) (the upper-triangle
+ * entry C_ij, i < j, is the one read), by Prim's algorithm from each
+ * cluster's first gene; ties go to the lower gene index.
+ * C: device, N x N FP64 row-major; labels: device, N int32 in [0, N) (e.g. the
+ * canonical labels from ga_best). edge_u, edge_v, edge_w: device, room for
+ * N - 1 entries each: the edges (u < v, d) of the clusters in first-occurrence
+ * order, each cluster's n_s - 1 edges in the order Prim adds them;
+ * *n_edges (host, optional) = N - number of clusters. Singletons have no edge.
+ * Errors: GPGA_ERR_ARG (NULL pointer, N outside [1, GPGA_MAX_N], a label
+ * outside [0, N)). Blocks the host until the stream reaches the end of the call.
+ */
+GPGA_API int cluster_mst(const double *C, int N, const int32_t *labels, int32_t *edge_u,
+                         int32_t *edge_v, double *edge_w, int *n_edges, void *stream);
+
+/*
  * gpga_log_selftest -- diagnostic with no counterpart in the paper: evaluates
  * the library's table-driven fixed-point logarithm (Q62 mantissa log plus
  * e ln 2, the kernel of the Eq. 8 assembly) and CUDA's log on the same n

@@ -751,6 +751,32 @@ GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L)
     return GPGA_OK;
 }
 
+GPGA_API int cluster_mst(const double *C, int N, const int32_t *labels, int32_t *edge_u,
+                         int32_t *edge_v, double *edge_w, int *n_edges, void *stream)
+{
+    g_err[0] = 0;
+    if (!C || !labels || !edge_u || !edge_v || !edge_w)
+        return set_error(GPGA_ERR_ARG, "cluster_mst: NULL pointer");
+    if (N < 1 || N > GPGA_MAX_N) return set_error(GPGA_ERR_ARG, "cluster_mst: N=%d out of range", N);
+    int rc = prepare_device();
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *info = nullptr;
+    GPGA_CUDA(cudaMallocAsync((void **)&info, 2 * sizeof(int), s));
+    int hinfo[2] = {0, 0};
+    rc = launch_cluster_mst(C, N, labels, edge_u, edge_v, edge_w, info, s);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "cluster_mst sync", __FILE__, __LINE__);
+    }
+    cudaFreeAsync(info, s);
+    if (rc) return rc;
+    if (hinfo[0]) return set_error(GPGA_ERR_ARG, "cluster_mst: a label lies outside [0, N)");
+    if (n_edges) *n_edges = hinfo[1];
+    return GPGA_OK;
+}
+
 GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *y_cuda,
                                void *stream)
 {

@@ -167,8 +167,211 @@ template int launch_init_threshold<int32_t>(int32_t *, int, int, int, const int3
                                             const int32_t *, const double *, double, double,
                                             uint32_t, uint32_t, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Minimum spanning tree of every cluster of one configuration (the cluster
+// trees drawn in Sec. 4) on the correlation distance d_ij = sqrt(2 (1 - C_ij)),
+// by Prim's algorithm from each cluster's first gene. One CTA: canonical ids
+// by first occurrence (atomicMin + block scan), members grouped by cluster,
+// then the clusters one after another, every Prim step a block-wide argmin
+// (distance, then gene index). Edges: clusters in first-occurrence order, each
+// cluster's n_s - 1 edges (u < v, d) in Prim order.
+// ---------------------------------------------------------------------------
+// the distance of genes a != b from the upper-triangle entry of C
+__device__ __forceinline__ double corr_dist(const double *C, int N, int a, int b)
+{
+    const int u = min(a, b), v = max(a, b);
+    return sqrt(2.0 * (1.0 - C[(size_t)u * N + v]));
+}
+
+__global__ void __launch_bounds__(1024)
+    cluster_mst_kernel(const double *__restrict__ C, int N, const int32_t *__restrict__ labels,
+                       int32_t *__restrict__ eu, int32_t *__restrict__ ev,
+                       double *__restrict__ ew, int *__restrict__ info)
+{
+    extern __shared__ double sm_mst[];
+    double *key = sm_mst;                                     // N: Prim keys by member position
+    int *li = reinterpret_cast<int *>(key + N);               // N labels
+    int *first = li + N;                                      // N: label -> first gene
+    int *cid = first + N;                                     // N: gene -> canonical cluster
+    int *cnt = cid + N;                                       // N + 1: sizes, then starts
+    int *mem = cnt + N + 1;                                   // N: genes grouped by cluster
+    int *src = mem + N;                                       // N: Prim parent by position
+    int *intree = src + N;                                    // N
+    __shared__ double s_bk[32];
+    __shared__ int s_bi[32];
+    __shared__ int s_part[32];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int nwarps = nt >> 5;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) {
+        int v = labels[i];
+        if (v < 0 || v >= N) {
+            s_bad = 1;
+            v = 0;
+        }
+        li[i] = v;
+        first[i] = N;
+        cnt[i] = 0;
+        src[i] = 0; // fill counters of the grouping below
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) info[0] = 1;
+        return;
+    }
+    for (int i = tid; i < N; i += nt) atomicMin(&first[li[i]], i);
+    __syncthreads();
+    // canonical ids: exclusive scan of the first-occurrence flags (chunked)
+    const int chunk = (N + nt - 1) / nt;
+    const int lo = min(N, tid * chunk), hi = min(N, lo + chunk);
+    int c0 = 0;
+    for (int i = lo; i < hi; ++i) c0 += first[li[i]] == i;
+    int v = c0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_part[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < nwarps ? s_part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_part[lane] = w;
+    }
+    __syncthreads();
+    int run = v - c0 + (wid ? s_part[wid - 1] : 0);
+    for (int i = lo; i < hi; ++i)
+        if (first[li[i]] == i) cid[i] = run++; // cid of a cluster's first gene
+    const int K = s_part[nwarps - 1];
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) {
+        const int c = cid[first[li[i]]];
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    // cluster starts (sequential over K by thread 0: K <= N, integer work)
+    if (tid == 0) {
+        int acc = 0;
+        for (int c = 0; c < K; ++c) {
+            const int n = cnt[c];
+            cnt[c] = acc;
+            acc += n;
+        }
+        cnt[K] = acc;
+    }
+    __syncthreads();
+    // group the genes by cluster (positions inside a cluster in any order:
+    // Prim's ties go to the lower gene index, not the position)
+    for (int i = tid; i < N; i += nt) {
+        const int c = cid[first[li[i]]];
+        mem[atomicAdd(&src[c], 1) + cnt[c]] = i;
+    }
+    __syncthreads();
+    for (int c = 0; c < K; ++c) {
+        const int st = cnt[c], n = cnt[c + 1] - st;
+        if (n < 2) continue; // (CTA-uniform)
+        const int root = first[li[mem[st]]]; // the cluster's first gene
+        for (int t = tid; t < n; t += nt) {
+            const int g = mem[st + t];
+            key[t] = g == root ? 0.0 : corr_dist(C, N, root, g);
+            src[t] = root;
+            intree[t] = g == root;
+        }
+        __syncthreads();
+        const int ebase = st - c;
+        for (int step = 0; step < n - 1; ++step) {
+            double bk = INFINITY;
+            int bg = 0x7fffffff, bt = -1;
+            for (int t = tid; t < n; t += nt) {
+                if (intree[t]) continue;
+                const double k = key[t];
+                const int g = mem[st + t];
+                if (k < bk || (k == bk && g < bg)) {
+                    bk = k;
+                    bg = g;
+                    bt = t;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+                const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                if (ok < bk || (ok == bk && og < bg)) {
+                    bk = ok;
+                    bg = og;
+                    bt = ot;
+                }
+            }
+            if (lane == 0) {
+                s_bk[wid] = bk;
+                s_bi[wid] = bt;
+                s_part[wid] = bg;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                bk = lane < nwarps ? s_bk[lane] : INFINITY;
+                bt = lane < nwarps ? s_bi[lane] : -1;
+                bg = lane < nwarps ? s_part[lane] : 0x7fffffff;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                    const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+                    const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                    if (ok < bk || (ok == bk && og < bg)) {
+                        bk = ok;
+                        bg = og;
+                        bt = ot;
+                    }
+                }
+                if (lane == 0) {
+                    s_bi[0] = bt;
+                    const int a = src[bt], b = mem[st + bt];
+                    eu[ebase + step] = min(a, b);
+                    ev[ebase + step] = max(a, b);
+                    ew[ebase + step] = bk;
+                    intree[bt] = 1;
+                }
+            }
+            __syncthreads();
+            const int vt = s_bi[0];
+            const int vg = mem[st + vt];
+            for (int t = tid; t < n; t += nt) {
+                if (intree[t]) continue;
+                const double d = corr_dist(C, N, vg, mem[st + t]);
+                if (d < key[t]) {
+                    key[t] = d;
+                    src[t] = vg;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        info[0] = 0;
+        info[1] = N - K;
+    }
+}
+
+int launch_cluster_mst(const double *C, int N, const int32_t *labels, int32_t *eu, int32_t *ev,
+                       double *ew, int *info, cudaStream_t s)
+{
+    const size_t smem = (size_t)N * sizeof(double) + (size_t)(7 * N + 1) * sizeof(int);
+    cluster_mst_kernel<<<1, 1024, smem, s>>>(C, N, labels, eu, ev, ew, info);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
 int prepare_init_kernels(int maxsmem)
 {
+    if (int rc = raise_smem(cluster_mst_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(mst_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(init_threshold_kernel<uint16_t>, maxsmem)) return rc;
     if (int rc = raise_smem(init_threshold_kernel<int32_t>, maxsmem)) return rc;

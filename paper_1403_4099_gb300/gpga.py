@@ -27,7 +27,7 @@ EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score",
            "ga_population", "gpga_log_selftest", "ga_score_noalloc", "ga_free",
            "ga_batch_init", "ga_batch_step", "ga_batch_status", "ga_batch_best",
            "ga_batch_tuning", "ga_batch_free", "serve_create", "serve_submit", "serve_tick",
-           "serve_result", "serve_stats", "serve_free"]
+           "serve_result", "serve_stats", "serve_free", "cluster_mst"]
 
 
 class GpgaError(RuntimeError):
@@ -108,6 +108,7 @@ def lib() -> ct.CDLL:
                                   ct.POINTER(ct.c_longlong), ct.POINTER(i32), ct.POINTER(i32),
                                   vp]),
             "serve_free": (i32, [vp]),
+            "cluster_mst": (i32, [vp, i32, vp, vp, vp, vp, ct.POINTER(i32), vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -196,6 +197,23 @@ def ga_evolve(pop, L, params: Params, seed: int, generation: int, stream=None):
                            _dev(perm, "int32"), _dev(par, "int32") if par.numel() else None,
                            _stream_ptr(stream)))
     return nxt, perm, par
+
+
+def cluster_mst(C, labels, stream=None):
+    """Per-cluster minimum spanning trees on d = sqrt(2 (1 - C)) of one
+    configuration (labels: device int32 N): host arrays (u, v, d)."""
+    import torch
+    N = C.shape[0]
+    cap = max(N - 1, 1)
+    eu = torch.empty(cap, dtype=torch.int32, device=C.device)
+    ev = torch.empty(cap, dtype=torch.int32, device=C.device)
+    ew = torch.empty(cap, dtype=torch.float64, device=C.device)
+    n = ct.c_int()
+    _check(lib().cluster_mst(_dev(C, "float64"), N, _dev(labels, "int32"), _dev(eu, "int32"),
+                             _dev(ev, "int32"), _dev(ew, "float64"), ct.byref(n),
+                             _stream_ptr(stream)))
+    k = n.value
+    return eu[:k].cpu().numpy(), ev[:k].cpu().numpy(), ew[:k].cpu().numpy()
 
 
 def log_selftest(x, stream=None):
