@@ -330,6 +330,26 @@ GPGA_API int ga_batch_best(gpga_batch *h, int run, int32_t *labels, double *L, i
  * generation launch in ms (each output optional). */
 GPGA_API int ga_batch_tuning(gpga_batch *h, int *warps_per_cta, int *ctas, float *ms);
 
+/* ga_batch_population -- the current population of run `run` (host, P x N
+ * int32) and its fitness (host, P FP64), each optional; synchronises. */
+GPGA_API int ga_batch_population(gpga_batch *h, int run, int32_t *pop, double *L);
+
+/*
+ * ga_island_init -- the island variant the paper proposes (Sec. 5): `islands`
+ * populations of the same C (device, N x N FP64, copied), island k seeded
+ * with seed + k, advanced together like a batch (ga_batch_step, _status,
+ * _best, _population, _free apply). Migration on a ring: when the generation
+ * being built is a multiple of migrate_every, the `migrants` best individuals
+ * of island k (its elites, slots 0..migrants-1 of the new population) replace
+ * the last `migrants` children of island (k + 1) mod islands, with their
+ * fitness, before selection; islands that terminated or stand at another
+ * generation take no part. Requires islands >= 2, migrate_every >= 1,
+ * 1 <= migrants <= elite and 2 migrants <= P (else GPGA_ERR_ARG).
+ */
+GPGA_API int ga_island_init(int islands, const double *C, int N, const gpga_params *p,
+                            uint64_t seed, int migrate_every, int migrants, void *stream,
+                            gpga_batch **out);
+
 /* ga_batch_free -- release the batch and all its device memory (NULL: no-op). */
 GPGA_API int ga_batch_free(gpga_batch *h);
 

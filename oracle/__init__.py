@@ -112,6 +112,8 @@ def _load():
             "orc_ari": (ct.c_double, [i32p, i32p, ct.c_int]),
             "orc_cluster_mst": (ct.c_int, [i32p, ct.c_int, f64p, i32p, i32p, f64p,
                                            ct.POINTER(ct.c_int32)]),
+            "orc_island_migrate": (ct.c_int, [i32p, f64p, ct.c_int, ct.c_int, ct.c_int,
+                                              ct.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -306,3 +308,15 @@ def cluster_mst(s, C):
     _check(_load().orc_cluster_mst(s, N, _f64(C), eu, ev, ew, ct.byref(n)), "cluster_mst")
     k = n.value
     return eu[:k], ev[:k], ew[:k]
+
+
+def island_migrate(pops, Ls, m):
+    """Ring migration of the island model: island k's first m members (and
+    fitness) replace the last m of island k + 1. pops: K x P x N int32, Ls:
+    K x P FP64; returns new arrays."""
+    pops = np.array(pops, dtype=np.int32, order="C", copy=True)
+    Ls = np.array(Ls, dtype=np.float64, order="C", copy=True)
+    K, P, N = pops.shape
+    _check(_load().orc_island_migrate(pops.reshape(-1), Ls.reshape(-1), K, P, N, int(m)),
+           "island_migrate")
+    return pops, Ls

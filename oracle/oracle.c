@@ -682,6 +682,37 @@ done:
     return rc;
 }
 
+/* Island model (the variant proposed in Sec. 5), ring migration after the
+ * operators of one generation: K populations of P x N (pops, island-major)
+ * with the fitness of their members (Ls); island k's first m members (its
+ * elites, m <= E) replace, with their fitness, the last m members of island
+ * (k + 1) mod K. Every island reads its own first m members before any is
+ * overwritten (2 m <= P keeps the two ranges apart). */
+int orc_island_migrate(int32_t *pops, double *Ls, int K, int P, int N, int m)
+{
+    if (!pops || !Ls || K < 2 || m < 1 || 2 * m > P) return ORC_ERR_ARG;
+    int32_t *head = (int32_t *)malloc((size_t)K * m * N * sizeof(int32_t));
+    double *hl = (double *)malloc((size_t)K * m * sizeof(double));
+    if (!head || !hl) {
+        free(head);
+        free(hl);
+        return ORC_ERR_OOM;
+    }
+    for (int k = 0; k < K; ++k) {
+        memcpy(head + (size_t)k * m * N, pops + (size_t)k * P * N, (size_t)m * N * sizeof(int32_t));
+        memcpy(hl + (size_t)k * m, Ls + (size_t)k * P, (size_t)m * sizeof(double));
+    }
+    for (int k = 0; k < K; ++k) {
+        const int to = (k + 1) % K;
+        memcpy(pops + ((size_t)to * P + (P - m)) * N, head + (size_t)k * m * N,
+               (size_t)m * N * sizeof(int32_t));
+        memcpy(Ls + (size_t)to * P + (P - m), hl + (size_t)k * m, (size_t)m * sizeof(double));
+    }
+    free(head);
+    free(hl);
+    return ORC_OK;
+}
+
 /* "Determine if termination criteria are met" (Algorithm 1; Table 3: number of
  * generations, error tolerance, stall generations). Reading: stop after scoring
  * generation g when g >= max_gens, or when g >= G_stall and

@@ -94,6 +94,7 @@ struct Fleet {
     bool retune = false;      // tune again when the items double
     cudaGraphExec_t gU = nullptr, g1 = nullptr;
     int U = 8;
+    int migrate_every = 0, migrants = 0; // island model (0: independent runs)
 };
 
 static size_t run_bytes(const Fleet *f, int N, char *base, RunMem *m)
@@ -415,6 +416,17 @@ static int fleet_tune(Fleet *f)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     f->tune_items = f->nitems;
+    // the trials rewrote each run's fitness with that of the next population:
+    // score the current populations again (the selection already used the
+    // right values, so the runs' results do not change)
+    for (int i = 0; i < f->cap && !rc; ++i) {
+        const Slot &s = f->slots[i];
+        if (!s.used) continue;
+        const uint16_t *lab2[2] = {s.m.d.pop0, s.m.d.pop1};
+        rc = launch_gather_score<uint16_t>(lab2, s.m.d.Np, 0, f->P, s.N, s.m.d.Np, s.m.d.Dfix,
+                                           s.m.diag, f->logtab, s.m.d.L, s.m.err, s.m.d.st,
+                                           nullptr, f->stream);
+    }
     return rc;
 }
 
@@ -425,6 +437,9 @@ static int fleet_graph(Fleet *f, int gens, cudaGraphExec_t *out)
     int rc = GPGA_OK;
     for (int k = 0; k < gens && !rc; ++k) {
         rc = fleet_gen_launch(f, f->warps, f->ctas);
+        if (!rc && f->migrate_every > 0)
+            rc = launch_fleet_migrate(f->d_runs, f->d_hdr, f->P, f->migrate_every, f->migrants,
+                                      f->cap, f->stream);
         if (!rc) rc = launch_fleet_select(f->d_runs, f->d_hdr, fleet_select_cfg(f, f->Nmax, 1),
                                           f->cap, f->stream);
     }
@@ -538,6 +553,55 @@ GPGA_API int ga_batch_init(int runs, const double *const *C, const int *ldc,
     h->f = f;
     h->runs = runs;
     *out = h;
+    return GPGA_OK;
+}
+
+GPGA_API int ga_island_init(int islands, const double *C, int N, const gpga_params *p,
+                            uint64_t seed, int migrate_every, int migrants, void *stream,
+                            gpga_batch **out)
+{
+    if (!out) return set_error(GPGA_ERR_ARG, "ga_island_init: out is NULL");
+    *out = nullptr;
+    if (islands < 2 || !C || !p)
+        return set_error(GPGA_ERR_ARG, "ga_island_init: islands=%d (>= 2) or a NULL argument",
+                         islands);
+    if (migrate_every < 1 || migrants < 1 || migrants > p->elite || 2 * migrants > p->P)
+        return set_error(GPGA_ERR_ARG,
+                         "ga_island_init: migrate_every=%d, migrants=%d (1 <= migrants <= elite, "
+                         "2 migrants <= P)",
+                         migrate_every, migrants);
+    std::vector<const double *> Cs(islands, C);
+    std::vector<int> Ns(islands, N);
+    std::vector<uint64_t> seeds(islands);
+    for (int k = 0; k < islands; ++k) seeds[k] = seed + (uint64_t)k;
+    gpga_batch *h = nullptr;
+    int rc = ga_batch_init(islands, Cs.data(), nullptr, nullptr, Ns.data(), p, seeds.data(),
+                           stream, &h);
+    if (rc) return rc;
+    // migration enters the captured generation graphs (none is built yet)
+    h->f->migrate_every = migrate_every;
+    h->f->migrants = migrants;
+    *out = h;
+    return GPGA_OK;
+}
+
+GPGA_API int ga_batch_population(gpga_batch *h, int run, int32_t *pop, double *L)
+{
+    if (!h) return set_error(GPGA_ERR_ARG, "ga_batch_population: NULL handle");
+    if (run < 0 || run >= h->runs) return set_error(GPGA_ERR_ARG, "ga_batch_population: run %d", run);
+    Fleet *f = h->f;
+    int rc = fleet_status(f);
+    if (rc) return rc;
+    const RunMem &m = f->slots[run].m;
+    const int P = f->P, N = m.d.N, Np = m.d.Np;
+    if (pop) {
+        std::vector<uint16_t> tmp((size_t)P * Np);
+        const uint16_t *buf = (f->h_st[0][run].gen & 1) ? m.d.pop1 : m.d.pop0;
+        GPGA_CUDA(cudaMemcpy(tmp.data(), buf, tmp.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < P; ++q)
+            for (int j = 0; j < N; ++j) pop[(size_t)q * N + j] = tmp[(size_t)q * Np + j];
+    }
+    if (L) GPGA_CUDA(cudaMemcpy(L, m.d.L, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost));
     return GPGA_OK;
 }
 

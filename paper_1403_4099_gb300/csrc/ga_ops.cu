@@ -391,6 +391,49 @@ int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectC
     return GPGA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Island model (the variant the paper proposes, Sec. 5): the runs of a fleet
+// are islands on one C, in a ring by table position. When the generation
+// being built, g + 1, is a multiple of `every`, island z copies the first m
+// slots of its new population -- its m best of generation g, placed there by
+// elitism (m <= E) -- with their fitness over the last m slots (children) of
+// island (z + 1) mod K, before the selection ranks the new populations. Both
+// islands must be active and at the same generation. Runs after the fused
+// generation kernel, every generation (a no-op between migrations).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    fleet_migrate_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
+                         int P, int every, int m)
+{
+    const int K = hdr->nruns;
+    if (K < 2) return;
+    for (int z = blockIdx.x; z < K; z += gridDim.x) {
+        const FleetRun &a = runs[z];
+        const FleetRun &b = runs[(z + 1) % K];
+        if (a.st->done || b.st->done) continue;
+        const int g = a.st->gen;
+        if (b.st->gen != g || (g + 1) % every != 0) continue;
+        // the new population (generation g + 1) is buffer (g + 1) & 1
+        const uint16_t *src = ((g + 1) & 1) ? a.pop1 : a.pop0;
+        uint16_t *dst = ((g + 1) & 1) ? b.pop1 : b.pop0;
+        const int Np = a.Np;
+        for (int idx = threadIdx.x; idx < m * Np; idx += blockDim.x) {
+            const int r = idx / Np, j = idx - r * Np;
+            dst[(size_t)(P - m + r) * Np + j] = src[(size_t)r * Np + j];
+        }
+        for (int r = threadIdx.x; r < m; r += blockDim.x) b.L[P - m + r] = a.L[r];
+    }
+}
+
+int launch_fleet_migrate(const FleetRun *runs, const FleetHdr *hdr, int P, int every, int m,
+                         int cap, cudaStream_t s)
+{
+    const int grid = cap < 152 ? cap : 152;
+    fleet_migrate_kernel<<<grid, 256, 0, s>>>(runs, hdr, P, every, m);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
 template <typename LabT>
 int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *perm,
                   uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,

@@ -643,6 +643,11 @@ int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectC
 int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
                             int warps, int ctas, int prop, cudaStream_t s);
+// island migration over the fleet's runs (ring by table position): every
+// `every` generations, the m elites of each run replace the last m children
+// of the next run
+int launch_fleet_migrate(const FleetRun *runs, const FleetHdr *hdr, int P, int every, int m,
+                         int cap, cudaStream_t s);
 // largest warps per CTA whose shared-memory slices fit, and the resident CTAs
 // per SM of the fleet generation kernel at that shape
 int fleet_max_warps(int Np_max);

@@ -27,7 +27,8 @@ EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score",
            "ga_population", "gpga_log_selftest", "ga_score_noalloc", "ga_free",
            "ga_batch_init", "ga_batch_step", "ga_batch_status", "ga_batch_best",
            "ga_batch_tuning", "ga_batch_free", "serve_create", "serve_submit", "serve_tick",
-           "serve_result", "serve_stats", "serve_free", "cluster_mst"]
+           "serve_result", "serve_stats", "serve_free", "cluster_mst", "ga_island_init",
+           "ga_batch_population"]
 
 
 class GpgaError(RuntimeError):
@@ -109,6 +110,9 @@ def lib() -> ct.CDLL:
                                   vp]),
             "serve_free": (i32, [vp]),
             "cluster_mst": (i32, [vp, i32, vp, vp, vp, vp, ct.POINTER(i32), vp]),
+            "ga_island_init": (i32, [i32, vp, i32, ct.POINTER(Params), ct.c_uint64, i32, i32, vp,
+                                     ct.POINTER(vp)]),
+            "ga_batch_population": (i32, [vp, i32, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -364,6 +368,27 @@ class Batch:
         _check(lib().ga_batch_best(self._h, int(run), lab.ctypes.data, Lb.ctypes.data,
                                    ct.byref(g)))
         return lab, float(Lb[0]), g.value
+
+    def population(self, run: int):
+        pop = np.zeros((self.params.P, self.N[run]), np.int32)
+        L = np.zeros(self.params.P, np.float64)
+        _check(lib().ga_batch_population(self._h, int(run), pop.ctypes.data, L.ctypes.data))
+        return pop, L
+
+    @classmethod
+    def islands(cls, C, params: Params, islands: int, seed: int, migrate_every: int,
+                migrants: int, stream=None):
+        """The island model: `islands` populations on C with ring migration."""
+        self = cls.__new__(cls)
+        self.R = int(islands)
+        self.params = params
+        self.N = [int(C.shape[0])] * self.R
+        h = ct.c_void_p()
+        _check(lib().ga_island_init(self.R, _dev(C, "float64"), int(C.shape[0]), ct.byref(params),
+                                    ct.c_uint64(seed), int(migrate_every), int(migrants),
+                                    _stream_ptr(stream), ct.byref(h)))
+        self._h = h
+        return self
 
     def tuning(self):
         w, c, ms = ct.c_int(), ct.c_int(), ct.c_float()

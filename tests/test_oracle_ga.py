@@ -284,3 +284,21 @@ def test_paper_shaped_inputs():
     st = synth.paper_stream()
     assert st.R.shape == (1800 + 1760 - 1, 18) and st.W == 1800 and st.windows == 1760
     assert sorted(np.bincount(st.truth).tolist()) == [6, 6, 6]
+
+
+def test_island_migration_ring(orc):
+    """Ring migration: island k's first m members land, in order, on the last m
+    slots of island k + 1 (the last island feeds the first); the rest of every
+    island is untouched, and the fitness travels with the members."""
+    rng = np.random.default_rng(41)
+    K, P, N, m = 4, 10, 6, 3
+    pops = rng.integers(0, N, (K, P, N)).astype(np.int32)
+    Ls = rng.standard_normal((K, P))
+    new, nl = orc.island_migrate(pops, Ls, m)
+    for k in range(K):
+        to = (k + 1) % K
+        assert np.array_equal(new[to, P - m:], pops[k, :m])
+        assert np.array_equal(nl[to, P - m:], Ls[k, :m])
+        assert np.array_equal(new[to, :P - m], pops[to, :P - m])
+    with pytest.raises(Exception):
+        orc.island_migrate(pops, Ls, 6)  # 2 m > P
