@@ -114,6 +114,8 @@ def _load():
                                            ct.POINTER(ct.c_int32)]),
             "orc_island_migrate": (ct.c_int, [i32p, f64p, ct.c_int, ct.c_int, ct.c_int,
                                               ct.c_int]),
+            "orc_pearson_ewma": (ct.c_int, [f64p, ct.c_int, ct.c_int, ct.c_int, ct.c_double,
+                                            f64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -320,3 +322,29 @@ def island_migrate(pops, Ls, m):
     _check(_load().orc_island_migrate(pops.reshape(-1), Ls.reshape(-1), K, P, N, int(m)),
            "island_migrate")
     return pops, Ls
+
+
+def pearson_ewma(R, lam: float) -> np.ndarray:
+    """EWMA-weighted Pearson (rows weighted lam^(T-1-t)); lam = 1 is Eq. 7."""
+    R = _f64(R)
+    T, N = R.shape
+    C = np.zeros((N, N), np.float64)
+    _check(_load().orc_pearson_ewma(R, T, N, N, float(lam), C), "pearson_ewma")
+    return C
+
+
+def remove_market(C):
+    """Market-mode removal: the largest eigenpair (lambda_1, v) of C (LAPACK's
+    symmetric eigensolver as the step), C' = C - lambda_1 v v^T, renormalised
+    to unit diagonal, C''_ij = C'_ij / sqrt(C'_ii C'_jj), clamped to [-1, 1].
+    Returns (C'', lambda_1)."""
+    C = _f64(C)
+    w, V = np.linalg.eigh(C)
+    lam, v = float(w[-1]), V[:, -1]
+    Cp = C - lam * np.outer(v, v)
+    d = np.diag(Cp).copy()
+    if not np.all(d > 0):
+        raise RuntimeError("oracle remove_market: a diagonal entry is not positive after the removal")
+    out = Cp / np.sqrt(np.outer(d, d))
+    np.fill_diagonal(out, 1.0)
+    return np.clip(out, -1.0, 1.0), lam

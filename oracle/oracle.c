@@ -823,6 +823,64 @@ int orc_brute_force(const double *C, int N, int32_t *best, double *bestL, int64_
 /*   E   = sum_i C(a_i,2) sum_j C(b_j,2) / C(N,2).                              */
 /* The denominator vanishes only when both are all-singleton or both a single  */
 /* cluster, i.e. identical: 1 is returned. NaN on bad labels.                  */
+/* EWMA-weighted Pearson correlation (pre-processing upstream of C: the
+ * exponentially weighted estimate used for near-real-time updates, Sec. 5):
+ * rows weighted w_t = lambda^(T-1-t) (the newest row weighs 1), weighted
+ * means mu_j = sum_t w_t R_tj / sum_t w_t, and
+ * C_ij = sum_t w_t (R_ti - mu_i)(R_tj - mu_j) / sqrt(q_i q_j),
+ * q_j = sum_t w_t (R_tj - mu_j)^2; diagonal 1, clamped to [-1, 1].
+ * lambda = 1 is the plain Pearson of Eq. 7. Sequential FP64 sums. */
+int orc_pearson_ewma(const double *R, int T, int N, int ld, double lambda, double *C)
+{
+    if (!R || !C || T < 2 || N < 1 || ld < N || !(lambda > 0.0 && lambda <= 1.0))
+        return ORC_ERR_ARG;
+    double *w = (double *)malloc((size_t)T * sizeof(double));
+    double *mu = (double *)malloc((size_t)N * sizeof(double));
+    double *q = (double *)malloc((size_t)N * sizeof(double));
+    if (!w || !mu || !q) {
+        free(w);
+        free(mu);
+        free(q);
+        return ORC_ERR_OOM;
+    }
+    double W = 0.0;
+    for (int t = 0; t < T; ++t) {
+        w[t] = pow(lambda, (double)(T - 1 - t));
+        W += w[t];
+    }
+    int rc = ORC_OK;
+    for (int j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += w[t] * R[(size_t)t * ld + j];
+        mu[j] = s / W;
+        double v = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const double z = R[(size_t)t * ld + j] - mu[j];
+            v += w[t] * z * z;
+        }
+        q[j] = v;
+        if (!(v > 0.0) || !isfinite(v)) rc = ORC_ERR_DEGENERATE;
+    }
+    if (rc == ORC_OK)
+        for (int i = 0; i < N; ++i) {
+            C[(size_t)i * N + i] = 1.0;
+            for (int j = i + 1; j < N; ++j) {
+                double s = 0.0;
+                for (int t = 0; t < T; ++t)
+                    s += w[t] * (R[(size_t)t * ld + i] - mu[i]) * (R[(size_t)t * ld + j] - mu[j]);
+                double c = s / sqrt(q[i] * q[j]);
+                if (c > 1.0) c = 1.0;
+                if (c < -1.0) c = -1.0;
+                C[(size_t)i * N + j] = c;
+                C[(size_t)j * N + i] = c;
+            }
+        }
+    free(w);
+    free(mu);
+    free(q);
+    return rc;
+}
+
 /* Minimum spanning tree of every cluster of configuration s (the trees the
  * paper draws for the clusters it finds, Sec. 4), on the correlation distance
  * d_ij = sqrt(2 (1 - C_ij)), by Kruskal's algorithm: the cluster's pairs
