@@ -228,6 +228,32 @@ GPGA_API int ga_kernel_times(gpga_ga *h, float *ms, int cap, int *count);
 GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
 
 /*
+ * cluster_corr_ewma -- pre-processing upstream of C (no counterpart in the
+ * hot path; Sec. 5 names exponentially weighted estimates for near-real-time
+ * use): the EWMA-weighted Pearson correlation of R (device, T x N FP64,
+ * leading dimension ld): rows weighted w_t = lambda^(T-1-t) (the newest row
+ * weighs 1) in the means, the variances and the cross products; lambda = 1 is
+ * cluster_corr. C (device, N x N FP64) written, diagonal 1. Errors as
+ * cluster_corr, plus GPGA_ERR_ARG for lambda outside (0, 1]. Blocks the host
+ * until the stream reaches the end of the call.
+ */
+GPGA_API int cluster_corr_ewma(const double *R, int T, int N, int ld, double lambda, double *C,
+                               void *stream);
+
+/*
+ * corr_remove_market -- pre-processing upstream of C: removes the market mode
+ * from a correlation matrix in place. The largest eigenpair (lambda_1, v) of C
+ * (device, N x N FP64, symmetric) by power iteration from the uniform vector
+ * in FP64 (until no component of v moves by more than 1e-14, at most
+ * max_iters), then C <- C - lambda_1 v v^T renormalised to unit diagonal and
+ * clamped to [-1, 1]. lambda1, iters (host, optional): the eigenvalue and the
+ * iterations used. GPGA_ERR_DEGENERATE if a diagonal entry is not positive
+ * after the removal. Blocks the host until the stream reaches the end.
+ */
+GPGA_API int corr_remove_market(double *C, int N, int max_iters, double *lambda1, int *iters,
+                                void *stream);
+
+/*
  * cluster_mst -- minimum spanning tree of every cluster of one configuration
  * (the cluster trees the paper draws for the clusters it finds, Sec. 4), on
  * the correlation distance d_ij = sqrt(2 (1 - C_ij)) (the upper-triangle

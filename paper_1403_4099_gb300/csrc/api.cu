@@ -80,6 +80,7 @@ int prepare_device()
     if (!rc) rc = prepare_init_kernels(maxsmem);
     if (!rc) rc = prepare_tc_kernels(maxsmem);
     if (!rc) rc = prepare_gather_kernels(maxsmem);
+    if (!rc) rc = prepare_corr_kernels(maxsmem);
     if (rc) return rc;
     ready[dev] = true;
     return GPGA_OK;
@@ -406,6 +407,32 @@ GPGA_API int cluster_corr(const double *R, int T, int N, int ld, double *C, void
     int rc = prepare_device();
     if (rc) return rc;
     return corr_run(R, T, N, ld, C, (cudaStream_t)stream);
+}
+
+GPGA_API int cluster_corr_ewma(const double *R, int T, int N, int ld, double lambda, double *C,
+                               void *stream)
+{
+    g_err[0] = 0;
+    if (!R || !C) return set_error(GPGA_ERR_ARG, "cluster_corr_ewma: NULL pointer");
+    if (T < 2 || N < 2 || N > GPGA_MAX_N || ld < N)
+        return set_error(GPGA_ERR_ARG, "cluster_corr_ewma: T=%d N=%d ld=%d out of range", T, N, ld);
+    if (!(lambda > 0.0 && lambda <= 1.0))
+        return set_error(GPGA_ERR_ARG, "cluster_corr_ewma: lambda must lie in (0, 1]");
+    int rc = prepare_device();
+    if (rc) return rc;
+    return corr_run_weighted(R, T, N, ld, lambda, C, (cudaStream_t)stream);
+}
+
+GPGA_API int corr_remove_market(double *C, int N, int max_iters, double *lambda1, int *iters,
+                                void *stream)
+{
+    g_err[0] = 0;
+    if (!C) return set_error(GPGA_ERR_ARG, "corr_remove_market: NULL pointer");
+    if (N < 2 || N > GPGA_MAX_N || max_iters < 1)
+        return set_error(GPGA_ERR_ARG, "corr_remove_market: N=%d max_iters=%d", N, max_iters);
+    int rc = prepare_device();
+    if (rc) return rc;
+    return market_remove(C, N, max_iters, lambda1, iters, (cudaStream_t)stream);
 }
 
 GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double *C, double *L,

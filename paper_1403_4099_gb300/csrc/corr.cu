@@ -19,8 +19,11 @@ namespace gpga {
 static constexpr int CS_COLS = 32, CS_ROWS = 8; // column-stat CTA: 32 columns x 8 row lanes
 static constexpr int T_SLAB = 512;              // rows per column-stat CTA
 
+// column sums over a slab of rows: sum_t w_t (R_tj - mean_j)^2 with mean, else
+// sum_t w_t R_tj (w == nullptr: all weights 1)
 __global__ void colsum_kernel(const double *__restrict__ R, int T, int N, int ld,
-                              const double *__restrict__ mean, double *__restrict__ part)
+                              const double *__restrict__ mean, const double *__restrict__ w,
+                              double *__restrict__ part)
 {
     __shared__ double red[CS_ROWS][CS_COLS + 1];
     const int cx = threadIdx.x, ry = threadIdx.y;
@@ -32,7 +35,8 @@ __global__ void colsum_kernel(const double *__restrict__ R, int T, int N, int ld
         const double mu = mean ? mean[j] : 0.0;
         for (int t = t0 + ry; t < t1; t += CS_ROWS) {
             const double v = R[(size_t)t * ld + j] - mu;
-            s += mean ? v * v : v;
+            const double x = mean ? v * v : v;
+            s += w ? w[t] * x : x;
         }
     }
     red[ry][cx] = s;
@@ -44,8 +48,10 @@ __global__ void colsum_kernel(const double *__restrict__ R, int T, int N, int ld
     }
 }
 
-__global__ void colfinal_kernel(const double *__restrict__ part, int nslab, int T, int N,
-                                double *__restrict__ out, int mode, int *__restrict__ err)
+// wsum: total weight (nullptr: uniform weights, T)
+__global__ void colfinal_kernel(const double *__restrict__ part, int nslab, int T,
+                                const double *wsum, int N, double *__restrict__ out, int mode,
+                                int *__restrict__ err)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -53,7 +59,7 @@ __global__ void colfinal_kernel(const double *__restrict__ part, int nslab, int 
     for (int k = 0; k < nslab; ++k) a += part[(size_t)k * N + j];
     if (mode == 0) { // means
         if (!isfinite(a)) atomicOr(err, 2);
-        out[j] = a / (double)T;
+        out[j] = a / (wsum ? *wsum : (double)T);
     } else { // 1 / sqrt(q)
         if (!(a > 0.0) || !isfinite(a)) {
             atomicOr(err, 2);
@@ -64,17 +70,44 @@ __global__ void colfinal_kernel(const double *__restrict__ part, int nslab, int 
     }
 }
 
+// Z_tj = sqrt(w_t) (R_tj - mean_j) / sqrt(q_j) (sw = sqrt(w), nullptr: 1)
 __global__ void normalise_kernel(const double *__restrict__ R, int T, int N, int ld, int Np,
                                  const double *__restrict__ mean, const double *__restrict__ inv,
-                                 float *__restrict__ Z)
+                                 const double *__restrict__ sw, float *__restrict__ Z)
 {
     const size_t total = (size_t)T * Np;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int t = (int)(idx / Np), j = (int)(idx - (size_t)t * Np);
         float z = 0.f;
-        if (j < N) z = (float)((R[(size_t)t * ld + j] - mean[j]) * inv[j]);
+        if (j < N) {
+            const double x = (R[(size_t)t * ld + j] - mean[j]) * inv[j];
+            z = (float)(sw ? sw[t] * x : x);
+        }
         Z[idx] = z;
+    }
+}
+
+// exponentially weighted rows: w_t = lambda^(T-1-t) (the newest row weighs 1),
+// their square roots, and (one CTA, fixed order) their sum
+__global__ void ewma_weights_kernel(int T, double lambda, double *__restrict__ w,
+                                    double *__restrict__ sw, double *__restrict__ wsum)
+{
+    __shared__ double part[1024];
+    const double ll = log(lambda);
+    double s = 0.0;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const double v = lambda == 1.0 ? 1.0 : exp((double)(T - 1 - t) * ll);
+        w[t] = v;
+        sw[t] = sqrt(v);
+        s += v;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) a += part[k];
+        *wsum = a;
     }
 }
 
@@ -174,6 +207,13 @@ __global__ void gram_final_kernel(const double *__restrict__ part, int nslab, in
 
 int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s)
 {
+    return corr_run_weighted(R, T, N, ld, 1.0, C, s);
+}
+
+int corr_run_weighted(const double *R, int T, int N, int ld, double lambda, double *C,
+                      cudaStream_t s)
+{
+    const bool weighted = lambda != 1.0;
     const int Np = pad_n(N);
     const int nslab_c = (T + T_SLAB - 1) / T_SLAB;
     const int nb = Np / GT;
@@ -189,7 +229,8 @@ int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s)
     const size_t b_vec = (size_t)N * sizeof(double);
     const size_t b_z = (size_t)T * Np * sizeof(float);
     const size_t b_g = (size_t)nsplit * ntiles * GT * GT * sizeof(double);
-    const size_t total = b_part + 2 * b_vec + b_z + b_g + 256;
+    const size_t b_w = weighted ? (size_t)2 * T * sizeof(double) : 0;
+    const size_t total = b_part + 2 * b_vec + b_z + b_g + b_w + 512;
     char *ws = nullptr;
     GPGA_CUDA(cudaMallocAsync((void **)&ws, total, s));
     double *part = (double *)ws;
@@ -197,6 +238,9 @@ int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s)
     double *inv = mean + N;
     float *Z = (float *)(ws + b_part + 2 * b_vec);
     double *gpart = (double *)(ws + b_part + 2 * b_vec + b_z);
+    double *wv = weighted ? (double *)(ws + b_part + 2 * b_vec + b_z + b_g) : nullptr;
+    double *swv = weighted ? wv + T : nullptr;
+    double *wsum = (double *)(ws + total - 512);
     int *err = (int *)(ws + total - 256);
     int rc = GPGA_OK;
     int herr = 0;
@@ -205,15 +249,17 @@ int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s)
             rc = set_error(GPGA_ERR_CUDA, "cluster_corr: memset failed");
             break;
         }
+        if (weighted) ewma_weights_kernel<<<1, 1024, 0, s>>>(T, lambda, wv, swv, wsum);
+        const double *ws_ = weighted ? wsum : nullptr;
         dim3 cgrid((N + CS_COLS - 1) / CS_COLS, nslab_c), cblock(CS_COLS, CS_ROWS);
-        colsum_kernel<<<cgrid, cblock, 0, s>>>(R, T, N, ld, nullptr, part);
-        colfinal_kernel<<<(N + 255) / 256, 256, 0, s>>>(part, nslab_c, T, N, mean, 0, err);
-        colsum_kernel<<<cgrid, cblock, 0, s>>>(R, T, N, ld, mean, part);
-        colfinal_kernel<<<(N + 255) / 256, 256, 0, s>>>(part, nslab_c, T, N, inv, 1, err);
+        colsum_kernel<<<cgrid, cblock, 0, s>>>(R, T, N, ld, nullptr, wv, part);
+        colfinal_kernel<<<(N + 255) / 256, 256, 0, s>>>(part, nslab_c, T, ws_, N, mean, 0, err);
+        colsum_kernel<<<cgrid, cblock, 0, s>>>(R, T, N, ld, mean, wv, part);
+        colfinal_kernel<<<(N + 255) / 256, 256, 0, s>>>(part, nslab_c, T, ws_, N, inv, 1, err);
         const size_t zt = (size_t)T * Np;
         int zb = (int)((zt + 255) / 256);
         if (zb > 8192) zb = 8192;
-        normalise_kernel<<<zb, 256, 0, s>>>(R, T, N, ld, Np, mean, inv, Z);
+        normalise_kernel<<<zb, 256, 0, s>>>(R, T, N, ld, Np, mean, inv, swv, Z);
         gram_kernel<<<dim3(ntiles, nsplit), 256, 0, s>>>(Z, T, Np, nb, trange, gpart, ntiles);
         gram_final_kernel<<<ntiles, 256, 0, s>>>(gpart, nsplit, ntiles, nb, N, C);
         cudaError_t e = cudaGetLastError();
@@ -235,4 +281,162 @@ int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s)
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Market-mode removal (pre-processing upstream of C): the largest eigenpair
+// (lambda_1, v) of C by power iteration from the uniform vector (one CTA, one
+// warp per row, FP64; stops when no component of v moves by more than 1e-14,
+// or after max_iters), then C' = C - lambda_1 v v^T renormalised to unit diagonal:
+// C''_ij = C'_ij / sqrt(C'_ii C'_jj), diagonal 1, clamped to [-1, 1].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    market_power_kernel(const double *__restrict__ C, int N, int max_iters,
+                        double *__restrict__ vout, double *__restrict__ info)
+{
+    extern __shared__ double smk[];
+    double *v = smk, *u = smk + N;
+    __shared__ double s_red[32];
+    __shared__ double s_lam;
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const double v0 = 1.0 / sqrt((double)N);
+    for (int i = tid; i < N; i += blockDim.x) v[i] = v0;
+    if (tid == 0) {
+        s_lam = 0.0;
+        s_stop = 0;
+    }
+    __syncthreads();
+    int it = 0;
+    for (; it < max_iters; ++it) {
+        // u = C v, one warp per row
+        for (int r = wid; r < N; r += nw) {
+            double a = 0.0;
+            for (int j = lane; j < N; j += 32) a += C[(size_t)r * N + j] * v[j];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) u[r] = a;
+        }
+        __syncthreads();
+        // lambda = v . u and |u|^2 (fixed-order block reductions)
+        double pl = 0.0, pn = 0.0;
+        for (int i = tid; i < N; i += blockDim.x) {
+            pl += v[i] * u[i];
+            pn += u[i] * u[i];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            pl += __shfl_xor_sync(0xffffffffu, pl, o);
+            pn += __shfl_xor_sync(0xffffffffu, pn, o);
+        }
+        if (lane == 0) s_red[wid] = pl;
+        __syncthreads();
+        double lam = 0.0;
+        for (int k = 0; k < nw; ++k) lam += s_red[k];
+        __syncthreads();
+        if (lane == 0) s_red[wid] = pn;
+        __syncthreads();
+        double nrm = 0.0;
+        for (int k = 0; k < nw; ++k) nrm += s_red[k];
+        nrm = sqrt(nrm);
+        double dv = 0.0; // largest change of a component of v
+        for (int i = tid; i < N; i += blockDim.x) {
+            const double x = u[i] / nrm;
+            dv = fmax(dv, fabs(x - v[i]));
+            v[i] = x;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+        __syncthreads();
+        if (lane == 0) s_red[wid] = dv;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int k = 0; k < nw; ++k) m = fmax(m, s_red[k]);
+            s_lam = lam;
+            s_stop = m <= 1e-14;
+        }
+        __syncthreads();
+        if (s_stop) {
+            ++it;
+            break;
+        }
+    }
+    for (int i = tid; i < N; i += blockDim.x) vout[i] = v[i];
+    if (tid == 0) {
+        info[0] = s_lam;
+        info[1] = (double)it;
+    }
+}
+
+__global__ void market_diag_kernel(const double *__restrict__ C, int N,
+                                   const double *__restrict__ v, const double *__restrict__ info,
+                                   double *__restrict__ dg, int *__restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double d = C[(size_t)i * N + i] - info[0] * v[i] * v[i];
+    if (!(d > 0.0)) atomicOr(err, 1);
+    dg[i] = d > 0.0 ? d : 1.0;
+}
+
+__global__ void market_clean_kernel(double *__restrict__ C, int N, const double *__restrict__ v,
+                                    const double *__restrict__ info,
+                                    const double *__restrict__ dg)
+{
+    const size_t total = (size_t)N * N;
+    const double lam = info[0];
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / N), j = (int)(idx - (size_t)i * N);
+        double c = 1.0;
+        if (i != j) {
+            c = (C[idx] - lam * v[i] * v[j]) / sqrt(dg[i] * dg[j]);
+            if (c > 1.0) c = 1.0;
+            if (c < -1.0) c = -1.0;
+        }
+        C[idx] = c;
+    }
+}
+
+int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, cudaStream_t s)
+{
+    const size_t bytes = (size_t)N * 2 * sizeof(double) + 2 * sizeof(double) + 256;
+    char *ws = nullptr;
+    GPGA_CUDA(cudaMallocAsync((void **)&ws, bytes, s));
+    double *v = (double *)ws, *dg = v + N, *info = dg + N;
+    int *err = (int *)(ws + bytes - 64);
+    double hinfo[2] = {0.0, 0.0};
+    int herr = 0, rc = GPGA_OK;
+    do {
+        if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
+            rc = set_error(GPGA_ERR_CUDA, "corr_remove_market: memset failed");
+            break;
+        }
+        market_power_kernel<<<1, 1024, (size_t)2 * N * sizeof(double), s>>>(C, N, max_iters, v, info);
+        market_diag_kernel<<<(N + 255) / 256, 256, 0, s>>>(C, N, v, info, dg, err);
+        const size_t total = (size_t)N * N;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        market_clean_kernel<<<blocks, 256, 0, s>>>(C, N, v, info, dg);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "corr_remove_market", __FILE__, __LINE__);
+    } while (0);
+    cudaFreeAsync(ws, s);
+    if (rc) return rc;
+    if (lambda1) *lambda1 = hinfo[0];
+    if (iters) *iters = (int)hinfo[1];
+    if (herr)
+        return set_error(GPGA_ERR_DEGENERATE,
+                         "corr_remove_market: a diagonal entry is not positive after the removal");
+    return GPGA_OK;
+}
+
+int prepare_corr_kernels(int maxsmem)
+{
+    return raise_smem(market_power_kernel, maxsmem);
+}
+
 } // namespace gpga
+

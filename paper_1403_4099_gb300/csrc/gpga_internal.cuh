@@ -330,6 +330,9 @@ int prepare_ga_kernels(int maxsmem);
 int prepare_init_kernels(int maxsmem);
 int prepare_tc_kernels(int maxsmem);
 int prepare_gather_kernels(int maxsmem);
+int prepare_corr_kernels(int maxsmem);
+// market-mode removal in place (corr.cu): lambda1 / iters optional (host)
+int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, cudaStream_t s);
 
 
 // ---------------------------------------------------------------------------
@@ -669,6 +672,10 @@ int launch_init_threshold(LabT *pop, int ldp, int P, int N, const int32_t *edge_
 // host launchers (corr.cu)
 // ---------------------------------------------------------------------------
 int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s);
+// EWMA-weighted Pearson: rows weighted lambda^(T-1-t) in the means, the
+// variances and the cross products (lambda = 1: plain Pearson)
+int corr_run_weighted(const double *R, int T, int N, int ld, double lambda, double *C,
+                      cudaStream_t s);
 
 // uint64 threshold of a probability: floor(p 2^32), 2^32 for p >= 1
 uint64_t prob_threshold(double p);

@@ -28,7 +28,7 @@ EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score",
            "ga_batch_init", "ga_batch_step", "ga_batch_status", "ga_batch_best",
            "ga_batch_tuning", "ga_batch_free", "serve_create", "serve_submit", "serve_tick",
            "serve_result", "serve_stats", "serve_free", "cluster_mst", "ga_island_init",
-           "ga_batch_population"]
+           "ga_batch_population", "cluster_corr_ewma", "corr_remove_market"]
 
 
 class GpgaError(RuntimeError):
@@ -113,6 +113,8 @@ def lib() -> ct.CDLL:
             "ga_island_init": (i32, [i32, vp, i32, ct.POINTER(Params), ct.c_uint64, i32, i32, vp,
                                      ct.POINTER(vp)]),
             "ga_batch_population": (i32, [vp, i32, vp, vp]),
+            "cluster_corr_ewma": (i32, [vp, i32, i32, i32, f64, vp, vp]),
+            "corr_remove_market": (i32, [vp, i32, i32, ct.POINTER(f64), ct.POINTER(i32), vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -164,6 +166,26 @@ def cluster_corr(R, C=None, stream=None):
     _check(lib().cluster_corr(_dev(R, "float64"), T, N, N, _dev(C, "float64"),
                               _stream_ptr(stream)))
     return C
+
+
+def cluster_corr_ewma(R, lam: float, C=None, stream=None):
+    """EWMA-weighted Pearson C (rows weighted lam^(T-1-t)) of R (T x N FP64, device)."""
+    import torch
+    T, N = R.shape
+    if C is None:
+        C = torch.empty((N, N), dtype=torch.float64, device=R.device)
+    _check(lib().cluster_corr_ewma(_dev(R, "float64"), T, N, N, float(lam), _dev(C, "float64"),
+                                   _stream_ptr(stream)))
+    return C
+
+
+def corr_remove_market(C, max_iters: int = 1000, stream=None):
+    """Market mode removed from C (device, in place); returns (lambda_1, iterations)."""
+    lam = ct.c_double()
+    it = ct.c_int()
+    _check(lib().corr_remove_market(_dev(C, "float64"), int(C.shape[0]), int(max_iters),
+                                    ct.byref(lam), ct.byref(it), _stream_ptr(stream)))
+    return lam.value, it.value
 
 
 def ga_score(labels, C, form: int = FORM_PLAIN, L=None, stream=None):
