@@ -348,3 +348,51 @@ def remove_market(C):
     out = Cp / np.sqrt(np.outer(d, d))
     np.fill_diagonal(out, 1.0)
     return np.clip(out, -1.0, 1.0), lam
+
+
+def wishart_range(N, T):
+    """Marchenko-Pastur support of the eigenvalues of a sample correlation
+    matrix of N independent series over T observations, q = N / T:
+    [(1 - sqrt q)^2, (1 + sqrt q)^2]."""
+    q = N / float(T)
+    r = np.sqrt(q)
+    return (1.0 - r) ** 2, (1.0 + r) ** 2
+
+
+def rmt_clip(C, T):
+    """The trace-preserving eigenvalue clipping of Sec. 4.2 before the
+    renormalisation: C = sum_k lambda_k v_k v_k^T (LAPACK's symmetric
+    eigensolver as the step); the eigenvalues inside the Wishart range are the
+    noise set and are replaced by their mean m, so
+    C' = m I + sum_{k kept} (lambda_k - m) v_k v_k^T (same trace). With an
+    empty noise set C' = C. Returns (C', eigenvalues ascending, noise mask, m)."""
+    C = _f64(C)
+    N = C.shape[0]
+    lo, hi = wishart_range(N, T)
+    w, V = np.linalg.eigh(C)
+    noise = (w >= lo) & (w <= hi)
+    if not noise.any():
+        return C.copy(), w, noise, float("nan")
+    m = float(w[noise].mean())
+    keep = ~noise
+    Vk = V[:, keep]
+    Cp = (Vk * (w[keep] - m)) @ Vk.T
+    Cp = 0.5 * (Cp + Cp.T) + m * np.eye(N)  # symmetric as defined (the product rounds unevenly)
+    return Cp, w, noise, m
+
+
+def clean_rmt(C, T):
+    """Random-matrix cleaning of a correlation matrix estimated from T
+    observations (Sec. 4.2): rmt_clip, then renormalised to unit diagonal,
+    C''_ij = C'_ij / sqrt(C'_ii C'_jj), clamped to [-1, 1]; C unchanged when
+    no eigenvalue lies in the Wishart range. Returns (C'', eigenvalues
+    ascending, size of the noise set)."""
+    Cp, w, noise, _ = rmt_clip(C, T)
+    if not noise.any():
+        return Cp, w, 0
+    d = np.diag(Cp).copy()
+    if not np.all(d > 0):
+        raise RuntimeError("oracle clean_rmt: a diagonal entry is not positive after the cleaning")
+    out = Cp / np.sqrt(np.outer(d, d))
+    np.fill_diagonal(out, 1.0)
+    return np.clip(out, -1.0, 1.0), w, int(noise.sum())
