@@ -49,11 +49,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recover", action="store_true")
     ap.add_argument("--workload", default="planted",
-                    choices=["planted", "batched", "serving", "paper"],
+                    choices=["planted", "batched", "serving", "paper", "preprocess"],
                     help="planted: the N=500 headline; batched: 256 sliding intraday windows "
                          "in one fleet; serving: Poisson request stream; paper: the paper's "
                          "shapes (40-stock training set, 18-stock 1760-window stream, Table 3 "
-                         "parameters, a P_m x P_c sweep)")
+                         "parameters, a P_m x P_c sweep); preprocess: the steps upstream of C "
+                         "(EWMA correlation, market-mode removal, random-matrix cleaning)")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
@@ -705,6 +706,101 @@ def run_paper(args, ranks):
     runtime.barrier(ranks)
 
 
+# FP64 rate of a GB300 (nominal; no measured FP64 peak is available): the
+# Jacobi rotations are plain FP64 multiply-adds
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def run_preprocess(args, ranks):
+    """The pre-processing upstream of C through the library's public calls (each
+    blocks until its stream is done, so host wall time is the call's time):
+    EWMA correlation and market-mode removal at N = 500, random-matrix cleaning
+    of one N = 500 matrix and of the 18-stock stream's 1760 windows as one
+    batch; the FP64 oracle's cleaning timed on the host beside it."""
+    import torch
+
+    import oracle
+    from paper_1403_4099_gb300 import gpga, runtime, synth
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    runtime.init_dist(ranks, "nccl")
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn, reps):
+        fn()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        stream.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    pl = synth.n500(replicate=ranks.rank)
+    T = pl.R.shape[0]
+    st = synth.paper_stream(replicate=ranks.rank)
+    with torch.cuda.stream(stream):
+        R = torch.from_numpy(pl.R).to(dev)
+        C = gpga.cluster_corr(R, stream=stream)
+        ewma_s = timed(lambda: gpga.cluster_corr_ewma(R, 0.98, stream=stream), max(3, args.steps // 4))
+        mkt_s = timed(lambda: gpga.corr_remove_market(C.clone(), stream=stream), 3)
+        rmt_one = lambda: gpga.corr_clean_rmt(C.clone(), T, stream=stream)  # noqa: E731
+        rmt500_s = timed(rmt_one, 2)
+        _, nn500, sw500 = rmt_one()
+        Rs = torch.from_numpy(st.R).to(dev)
+        Cs = torch.empty((st.windows, 18, 18), dtype=torch.float64, device=dev)
+        for k in range(st.windows):
+            gpga.cluster_corr(Rs[k:k + st.W], Cs[k], stream)
+        rmt_batch = lambda: gpga.corr_clean_rmt(Cs.clone(), st.W, stream=stream)  # noqa: E731
+        runtime.barrier(ranks)
+        rmtB_s = timed(rmt_batch, 3)
+        _, nnB, swB = rmt_batch()
+    max_secs, total = runtime.aggregate(ranks, rmtB_s, float(st.windows), device=dev)
+    if ranks.rank != 0:
+        runtime.barrier(ranks)
+        return
+    # Jacobi FP64 work: per round 3 n2^2 flops on A (upper pair-blocks, 24 flops
+    # per 2 x 2 block) and 3 n2^2 on V, n2 - 1 rounds per sweep
+    def jacobi_flops(N, sweeps, B=1):
+        n2 = N + (N & 1)
+        return float(B) * sweeps * (n2 - 1) * 6.0 * n2 * n2
+    f500 = jacobi_flops(500, sw500) / rmt500_s / 1e12
+    fB = jacobi_flops(18, swB, st.windows) / rmtB_s / 1e12
+    # the oracle (NumPy / LAPACK, its default threads) on the same inputs
+    Ch = C.cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.clean_rmt(Ch, T)
+    orc500 = time.perf_counter() - t0
+    Csh = Cs.cpu().numpy()
+    nb = 200
+    t0 = time.perf_counter()
+    for k in range(nb):
+        oracle.clean_rmt(Csh[k], st.W)
+    orcB = (time.perf_counter() - t0) / nb
+    line = {"metric": "windows/s (random-matrix cleaning of the 18-stock stream: 1760 "
+                      "correlation windows of 1800 bars, one batch)",
+            "value": total / max_secs, "unit": "windows/s", "n_gpus": ranks.world, "steps": 3,
+            "warmup": 1, "ms_per_step": 1e3 * max_secs, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "rmt_clean_n18_w1800_x1760"},
+            "rmt_stream": {"sweeps": swB, "noise_set_sizes": sorted(set(nnB)),
+                           "jacobi_tflops": fB},
+            "rmt_n500": {"ms": 1e3 * rmt500_s, "sweeps": sw500, "noise_set": nn500[0],
+                         "jacobi_tflops": f500},
+            "roofline": {"bound": "alu", "kernel": "jacobi_round (N=500)", "achieved": f500,
+                         "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                         "frac": f500 / FP64_TFLOPS_NOMINAL, "traffic": None,
+                         "peak_source": "nominal FP64 rate (fallback: no measured FP64 peak)"},
+            "ewma_corr_n500_t5000_ms": 1e3 * ewma_s,
+            "market_removal_n500_ms": 1e3 * mkt_s,
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(),
+                             "rmt_n500_ms": 1e3 * orc500,
+                             "value": 1.0 / orcB, "unit": "windows/s",
+                             "sample": f"{nb} of the 1760 windows, one by one (NumPy eigh, its "
+                                       "default threads), and the N=500 matrix once"}}
+    print(json.dumps(line), flush=True)
+    runtime.barrier(ranks)
+
+
 def main():
     args = parse()
     from paper_1403_4099_gb300 import runtime
@@ -720,6 +816,9 @@ def main():
         return
     if args.workload == "paper":
         run_paper(args, ranks)
+        return
+    if args.workload == "preprocess":
+        run_preprocess(args, ranks)
         return
     run_gpu(args, ranks)
 

@@ -254,6 +254,30 @@ GPGA_API int corr_remove_market(double *C, int N, int max_iters, double *lambda1
                                 void *stream);
 
 /*
+ * corr_clean_rmt -- pre-processing upstream of C: random-matrix cleaning
+ * (Sec. 4.2: the eigenvalues in the Wishart range are removed in a
+ * trace-preserving way) of `batch` correlation matrices in place. C: device,
+ * batch x N x N FP64, each symmetric, estimated from T observations.
+ * Per matrix: the eigen-decomposition C = sum_k lambda_k v_k v_k^T (parallel
+ * cyclic Jacobi in FP64 until every off-diagonal entry is below 1e-14
+ * ||A||_F); the noise set is the eigenvalues inside the Marchenko-Pastur range
+ * [(1 - sqrt q)^2, (1 + sqrt q)^2], q = N / T, and they are replaced by their
+ * mean m: C' = m I + sum_{k not noise} (lambda_k - m) v_k v_k^T (same trace);
+ * then C <- C'_ij / sqrt(C'_ii C'_jj), clamped to [-1, 1], unit diagonal. A
+ * matrix with an empty noise set is left unchanged.
+ * eigvals (device, optional, batch x N): the input's eigenvalues, ascending.
+ * n_noise (host, optional, batch): the noise-set sizes. sweeps (host,
+ * optional): Jacobi sweeps run (the batch sweeps together).
+ * Errors: GPGA_ERR_ARG (NULL or host C, batch outside [1, 65535], N outside
+ * [2, GPGA_MAX_N], T not positive, a non-finite entry), GPGA_ERR_DEGENERATE
+ * (no convergence in 40 sweeps, or a non-positive diagonal after the
+ * cleaning). Device scratch of 3 batch n2^2 doubles (n2 = N rounded up to
+ * even). Blocks the host until the stream reaches the end of the call.
+ */
+GPGA_API int corr_clean_rmt(double *C, int batch, int N, double T, double *eigvals, int *n_noise,
+                           int *sweeps, void *stream);
+
+/*
  * cluster_mst -- minimum spanning tree of every cluster of one configuration
  * (the cluster trees the paper draws for the clusters it finds, Sec. 4), on
  * the correlation distance d_ij = sqrt(2 (1 - C_ij)) (the upper-triangle

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" boundary of libgpga.so (declared in include/gpga.h):
 // argument checks, status codes, the GA handle and its device memory, and the
 // per-generation launch sequence, captured once into CUDA graphs.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -263,7 +264,10 @@ static int mark(gpga_ga *h, cudaEvent_t *evs, int k)
     return GPGA_OK;
 }
 
-int enqueue_generation(gpga_ga *h, cudaEvent_t *evs)
+// after_kernel: the node captured last before this generation is a kernel
+// (the selection; not the start of the graph, not an event). The fused
+// generation kernel is then launched as a programmatic dependent of it.
+int enqueue_generation(gpga_ga *h, cudaEvent_t *evs, bool after_kernel)
 {
     EvolveCfg e;
     e.P = h->P;
@@ -284,10 +288,11 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs)
     int rc = mark(h, evs, 0);
     if (h->prm.form == GPGA_FORM_GATHER) {
         // selection, crossover, mutation, replacement and scoring in one kernel
+        const bool pdl_gen = after_kernel && !(evs && marked(h, 0));
         if (!rc)
             rc = launch_gather_generation<uint16_t>(pop2, next2, e, h->perm, prefix, h->Np, h->Dfix,
                                                     h->diag, h->logtab, h->L, h->st, h->pairs,
-                                                    h->stream);
+                                                    pdl_gen, h->stream);
         if (!rc) rc = mark(h, evs, 1);
         if (!rc) rc = mark(h, evs, 2);
         if (!rc) rc = mark(h, evs, 3);
@@ -354,10 +359,13 @@ int build_graph(gpga_ga *h, int gens, cudaGraphExec_t *out)
     // profile 1 times the dominant kernel of the graph's first generation only
     // (each event node costs about 2 us of the step); profile 2 every stage of
     // every generation
-    for (int k = 0; k < gens && rc == GPGA_OK; ++k)
-        rc = enqueue_generation(h, (h->prm.profile >= 2 || (h->prm.profile == 1 && k == 0))
-                                       ? evs[k]
-                                       : nullptr);
+    bool after_kernel = false;
+    for (int k = 0; k < gens && rc == GPGA_OK; ++k) {
+        cudaEvent_t *ek =
+            (h->prm.profile >= 2 || (h->prm.profile == 1 && k == 0)) ? evs[k] : nullptr;
+        rc = enqueue_generation(h, ek, after_kernel);
+        after_kernel = !(ek && marked(h, 4));
+    }
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -433,6 +441,21 @@ GPGA_API int corr_remove_market(double *C, int N, int max_iters, double *lambda1
     int rc = prepare_device();
     if (rc) return rc;
     return market_remove(C, N, max_iters, lambda1, iters, (cudaStream_t)stream);
+}
+
+GPGA_API int corr_clean_rmt(double *C, int batch, int N, double T, double *eigvals, int *n_noise,
+                           int *sweeps, void *stream)
+{
+    g_err[0] = 0;
+    if (!C) return set_error(GPGA_ERR_ARG, "corr_clean_rmt: NULL pointer");
+    if (batch < 1 || batch > 65535 || N < 2 || N > GPGA_MAX_N || !(T > 0.0) || !isfinite(T))
+        return set_error(GPGA_ERR_ARG, "corr_clean_rmt: batch=%d N=%d T=%g out of range", batch, N,
+                         T);
+    if (!is_device_ptr(C) || (eigvals && !is_device_ptr(eigvals)))
+        return set_error(GPGA_ERR_ARG, "corr_clean_rmt: C and eigvals must be device memory");
+    int rc = prepare_device();
+    if (rc) return rc;
+    return rmt_clean(C, batch, N, T, eigvals, n_noise, sweeps, (cudaStream_t)stream);
 }
 
 GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double *C, double *L,

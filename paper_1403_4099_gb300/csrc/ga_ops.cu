@@ -173,6 +173,8 @@ struct SelectSmem {
     int si[RANK_CHUNK];
     uint64_t s_part[RANK_CHUNK];
     int s_last;
+    int s_best;      // the individual of rank 0
+    double s_bestL;  // its fitness
 };
 
 // the body of one CTA (blockIdx.x, blockIdx.y) of the selection grid of one run
@@ -263,7 +265,18 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // a generation kernel launched as a programmatic dependent may be scheduled
+    // now; it waits for this grid to complete before it reads anything written here
+    griddep_launch();
     const int g = st ? __ldcg(&st->gen) + cfg.gen_off : 0; // (loaded while perm is built)
+    // the bookkeeping inputs that do not depend on the ranks, loaded alongside them
+    const bool stall = st && cfg.tol >= 0.0 && cfg.stall_gens > 0 && g >= cfg.stall_gens;
+    long long lsum = 0;
+    double prev = 0.0;
+    if (st && tid == 0) {
+        lsum = __ldcg(&st->lsum);
+        if (stall) prev = hist[g - cfg.stall_gens];
+    }
     for (int i0 = tid; i0 < P; i0 += 16 * nt) { // 16 rank loads in flight per thread
         int r[16];
 #pragma unroll
@@ -277,23 +290,23 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
             if (i < P) {
                 perm[r[u]] = i;
                 rank[i] = 0;
+                if (r[u] == 0) { // the fittest: its index and fitness, without a perm read
+                    sm.s_best = i;
+                    sm.s_bestL = L[i];
+                }
             }
         }
     }
     __syncthreads(); // perm is visible to the whole CTA
     if (tid == 0) ticket[0] = 0u;
-    const int bidx = perm[0];
+    const int bidx = sm.s_best;
     if (st) {
         if (cfg.record && ring) {
             const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
             for (int j = tid; j < cfg.N; j += nt) ring[(size_t)g * cfg.N + j] = src[j];
         }
         if (tid == 0) {
-            // the loads first (independent), then the decisions, the mean last
-            double best = L[bidx];
-            const long long lsum = __ldcg(&st->lsum);
-            const bool stall = cfg.tol >= 0.0 && cfg.stall_gens > 0 && g >= cfg.stall_gens;
-            const double prev = stall ? hist[g - cfg.stall_gens] : 0.0;
+            double best = sm.s_bestL;
             if (isnan(best)) best = -INFINITY;
             st->gen = g;
             st->best = best;
@@ -317,7 +330,7 @@ __device__ __forceinline__ void select_cta(const double *__restrict__ L, const S
     if (cfg.scaling != GPGA_SCALING_PROP) return;
     // proportional weights by rank, w = floor(max(L, 0) / L_max 2^32) (all 1 if
     // L_max <= 0), and their inclusive prefix: chunked sequential scan
-    double lmax = L[bidx];
+    double lmax = sm.s_bestL;
     if (isnan(lmax)) lmax = -INFINITY;
     const int chunk = (P + nt - 1) / nt;
     const int lo = tid * chunk, hi = min(P, lo + chunk);

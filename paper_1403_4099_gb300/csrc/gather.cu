@@ -329,6 +329,12 @@ __global__ void __launch_bounds__(256, 4)
                              double *__restrict__ L, const DevState *__restrict__ st,
                              unsigned long long *__restrict__ pairs)
 {
+    // launched as a programmatic dependent of the selection (which lets it be
+    // scheduled while its last CTA finishes): wait for that grid before reading
+    // perm, the prefix and the state. (Letting the selection in turn be
+    // scheduled early, from here, measured slower: its waiting CTAs cost the
+    // generation more than the launch gap they hide.)
+    griddep_wait();
     if (st->done) return;
     const int g = st->gen;
     const LabT *cur = (g & 1) ? pop1 : pop0;
@@ -407,16 +413,15 @@ template <typename LabT>
 int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
                              const int32_t *perm, const uint64_t *prefix, int Np,
                              const int32_t *Dfix, const int *diag_flag, const double *logtab,
-                             double *L, const DevState *st, unsigned long long *pairs,
+                             double *L, const DevState *st, unsigned long long *pairs, bool pdl,
                              cudaStream_t s)
 {
     const int nw = warps_for(Np);
     const size_t smem = nw * gather_slice_bytes(Np);
     const int grid = (cfg.P + nw - 1) / nw;
-    gather_generation_kernel<LabT><<<grid, 32 * nw, smem, s>>>(
-        pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, Dfix, diag_flag, logtab, L,
-        st, pairs);
-    GPGA_LAUNCH_CHECK();
+    GPGA_CUDA(launch_pdl(gather_generation_kernel<LabT>, dim3(grid), dim3(32 * nw), smem, s, pdl,
+                         pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, Dfix,
+                         diag_flag, logtab, L, st, pairs));
     return GPGA_OK;
 }
 
@@ -459,7 +464,7 @@ template int launch_gather_generation<uint16_t>(const uint16_t *const *, uint16_
                                                 const EvolveCfg &, const int32_t *,
                                                 const uint64_t *, int, const int32_t *,
                                                 const int *, const double *, double *,
-                                                const DevState *, unsigned long long *,
+                                                const DevState *, unsigned long long *, bool,
                                                 cudaStream_t);
 
 int prepare_gather_kernels(int maxsmem)

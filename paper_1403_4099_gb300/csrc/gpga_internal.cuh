@@ -29,6 +29,38 @@ int cuda_error(cudaError_t e, const char *what, const char *file, int line);
     } while (0)
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch. A kernel launched with pdl = true may be
+// scheduled while the previous kernel of the stream is still running; it calls
+// griddep_wait() before its first access to anything that kernel writes (the
+// wait returns once that grid has completed and its memory is visible; for a
+// kernel launched without the attribute it returns at once). griddep_launch()
+// lets the next kernel be scheduled once every CTA of this grid has called it
+// or exited; it changes nothing about memory visibility.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, bool pdl, Args... args)
+{
+    cudaLaunchConfig_t c = {};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = smem;
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = at;
+    c.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&c, k, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): two 32x32 -> 64-bit
 // multiplies per round, ten rounds, key bumped by the Weyl constants.
 // Counter layout of the GA: (generation, index, block, stream).
@@ -333,6 +365,11 @@ int prepare_gather_kernels(int maxsmem);
 int prepare_corr_kernels(int maxsmem);
 // market-mode removal in place (corr.cu): lambda1 / iters optional (host)
 int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, cudaStream_t s);
+// random-matrix cleaning of B matrices N x N in place (rmt.cu): eig_sorted
+// (device, B x N, optional) the input's eigenvalues ascending; n_noise (host,
+// B, optional) the noise-set sizes; sweeps (host, optional) Jacobi sweeps run
+int rmt_clean(double *C, int B, int N, double T, double *eig_sorted, int *n_noise, int *sweeps,
+              cudaStream_t s);
 
 
 // ---------------------------------------------------------------------------
@@ -631,7 +668,7 @@ template <typename LabT>
 int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
                              const int32_t *perm, const uint64_t *prefix, int Np,
                              const int32_t *Dfix, const int *diag_flag, const double *logtab,
-                             double *L, const DevState *st, unsigned long long *pairs,
+                             double *L, const DevState *st, unsigned long long *pairs, bool pdl,
                              cudaStream_t s);
 
 int launch_state_init(DevState *st, unsigned long long *ts0, uint32_t k0, uint32_t k1,

@@ -28,7 +28,7 @@ EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score",
            "ga_batch_init", "ga_batch_step", "ga_batch_status", "ga_batch_best",
            "ga_batch_tuning", "ga_batch_free", "serve_create", "serve_submit", "serve_tick",
            "serve_result", "serve_stats", "serve_free", "cluster_mst", "ga_island_init",
-           "ga_batch_population", "cluster_corr_ewma", "corr_remove_market"]
+           "ga_batch_population", "cluster_corr_ewma", "corr_remove_market", "corr_clean_rmt"]
 
 
 class GpgaError(RuntimeError):
@@ -115,6 +115,7 @@ def lib() -> ct.CDLL:
             "ga_batch_population": (i32, [vp, i32, vp, vp]),
             "cluster_corr_ewma": (i32, [vp, i32, i32, i32, f64, vp, vp]),
             "corr_remove_market": (i32, [vp, i32, i32, ct.POINTER(f64), ct.POINTER(i32), vp]),
+            "corr_clean_rmt": (i32, [vp, i32, i32, f64, vp, ct.POINTER(i32), ct.POINTER(i32), vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -186,6 +187,21 @@ def corr_remove_market(C, max_iters: int = 1000, stream=None):
     _check(lib().corr_remove_market(_dev(C, "float64"), int(C.shape[0]), int(max_iters),
                                     ct.byref(lam), ct.byref(it), _stream_ptr(stream)))
     return lam.value, it.value
+
+
+def corr_clean_rmt(C, T: float, stream=None):
+    """Random-matrix cleaning of C in place (device FP64, N x N or batch x N x N,
+    each estimated from T observations). Returns (eigenvalues of the input,
+    ascending, device batch x N; noise-set sizes, list; Jacobi sweeps)."""
+    import torch
+    N = int(C.shape[-1])
+    B = 1 if C.dim() == 2 else int(C.shape[0])
+    ev = torch.empty((B, N), dtype=torch.float64, device=C.device)
+    nn = (ct.c_int * B)()
+    sw = ct.c_int()
+    _check(lib().corr_clean_rmt(_dev(C, "float64"), B, N, float(T), _dev(ev, "float64"), nn,
+                                ct.byref(sw), _stream_ptr(stream)))
+    return ev, list(nn), sw.value
 
 
 def ga_score(labels, C, form: int = FORM_PLAIN, L=None, stream=None):
