@@ -112,6 +112,7 @@ struct gpga_ga {
     int *rank = nullptr;
     unsigned *ticket = nullptr;
     uint64_t *rank_prefix = nullptr, *work_prefix = nullptr;
+    int32_t *sus_tab = nullptr; // SUS brackets of rank_prefix (P + 1)
     DevState *st = nullptr;
     double *hist = nullptr;
     uint16_t *ring = nullptr;
@@ -168,6 +169,7 @@ size_t carve(gpga_ga *h, char *base)
     h->ticket = c.take<unsigned>(TICKETS);
     h->rank_prefix = c.take<uint64_t>(P);
     h->work_prefix = c.take<uint64_t>(P);
+    h->sus_tab = c.take<int32_t>(P + 1);
     h->st = c.take<DevState>(1);
     h->hist = c.take<double>(G);
     h->ring = h->prm.record ? c.take<uint16_t>(G * N) : nullptr;
@@ -282,6 +284,7 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs, bool after_kernel)
     e.k0 = h->k0;
     e.k1 = h->k1;
     e.gen = 0;
+    e.sus_tab = h->prm.scaling == GPGA_SCALING_PROP ? nullptr : h->sus_tab;
     const uint16_t *pop2[2] = {h->pop[0], h->pop[1]};
     uint16_t *next2[2] = {h->pop[1], h->pop[0]};
     const uint64_t *prefix = h->prm.scaling == GPGA_SCALING_PROP ? h->work_prefix : h->rank_prefix;
@@ -325,7 +328,7 @@ int enqueue_start(gpga_ga *h, const double *C)
     rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->Dfix, h->logtab,
                        h->diag, h->stream);
     if (rc) return rc;
-    rc = rank_prefix_table(h->rank_prefix, h->P, h->stream);
+    rc = rank_prefix_table(h->rank_prefix, h->P, h->M, h->sus_tab, h->stream);
     if (rc) return rc;
     if (h->prm.init == GPGA_INIT_THRESHOLD) {
         rc = launch_mst(h->C64, h->N, h->mst_order, h->mst_from, h->mst_w, h->stream);
@@ -554,7 +557,7 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
             rc = set_error(GPGA_ERR_CUDA, "ga_evolve: memset failed");
             break;
         }
-        rc = rank_prefix_table(rpre, P, s);
+        rc = rank_prefix_table(rpre, P, M, nullptr, s);
         if (rc) break;
         SelectCfg sc;
         sc.P = P;
@@ -586,6 +589,7 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
         e.k0 = sc.k0;
         e.k1 = sc.k1;
         e.gen = generation;
+        e.sus_tab = nullptr; // the general search (no bracket table here)
         const int32_t *pop2[2] = {pop, pop};
         int32_t *next2[2] = {next, next};
         rc = launch_evolve<int32_t>(pop2, next2, e, pm_,

@@ -76,6 +76,7 @@ struct Fleet {
     int cap = 0, Nmax = 0, Np_max = 0;
     char *shared = nullptr;        // rank table, log tables, run table, states
     uint64_t *rank_prefix = nullptr;
+    int32_t *sus_tab = nullptr; // SUS brackets of rank_prefix (M + 1)
     double *logtab = nullptr;
     FleetRun *d_runs = nullptr;
     FleetHdr *d_hdr = nullptr;
@@ -162,6 +163,7 @@ static EvolveCfg fleet_evolve_cfg(const Fleet *f)
     e.k0 = 0;
     e.k1 = 0;
     e.gen = 0;
+    e.sus_tab = f->prm.scaling == GPGA_SCALING_PROP ? nullptr : f->sus_tab;
     return e;
 }
 
@@ -217,6 +219,7 @@ static int fleet_create(const gpga_params *p, int cap, int Nmax, void *stream, F
     for (int pass = 0; pass < 2; ++pass) {
         Carve c(f->shared);
         uint64_t *rp = c.take<uint64_t>(f->P);
+        int32_t *stab = c.take<int32_t>((size_t)f->M + 1);
         double *lt = c.take<double>(logtab_len(Nmax));
         FleetRun *dr = c.take<FleetRun>(cap);
         FleetHdr *dh = c.take<FleetHdr>(1);
@@ -230,6 +233,7 @@ static int fleet_create(const gpga_params *p, int cap, int Nmax, void *stream, F
             }
         } else {
             f->rank_prefix = rp;
+            f->sus_tab = stab;
             f->logtab = lt;
             f->d_runs = dr;
             f->d_hdr = dh;
@@ -247,7 +251,7 @@ static int fleet_create(const gpga_params *p, int cap, int Nmax, void *stream, F
         f->h_hdr[b]->nruns = 0;
         f->h_hdr[b]->nitems = 0;
     }
-    rc = rank_prefix_table(f->rank_prefix, f->P, f->stream);
+    rc = rank_prefix_table(f->rank_prefix, f->P, f->M, f->sus_tab, f->stream);
     if (!rc) rc = launch_logtab(f->logtab, Nmax, f->stream);
     if (!rc && cudaMemsetAsync(f->d_hdr, 0, sizeof(FleetHdr), f->stream) != cudaSuccess)
         rc = set_error(GPGA_ERR_CUDA, "fleet: memset failed");

@@ -101,10 +101,33 @@ __global__ void rank_prefix_kernel(uint64_t *__restrict__ prefix, int P)
     for (int r = lo; r < hi; ++r) prefix[r] += part[t];
 }
 
-int rank_prefix_table(uint64_t *prefix, int P, cudaStream_t s)
+// SUS brackets of the fixed prefix: tab[k] = first rank r with
+// prefix[r] > floor(k W / M), k = 0..M, W = prefix[P - 1] (k W < 2^56)
+__global__ void sus_table_kernel(const uint64_t *__restrict__ prefix, int P, int M,
+                                 int32_t *__restrict__ tab)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > M) return;
+    const uint64_t x = (uint64_t)k * prefix[P - 1] / (uint64_t)M;
+    int lo = 0, hi = P;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] > x)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    tab[k] = lo;
+}
+
+int rank_prefix_table(uint64_t *prefix, int P, int M, int32_t *sus_tab, cudaStream_t s)
 {
     rank_prefix_kernel<<<1, 1024, 0, s>>>(prefix, P);
     GPGA_LAUNCH_CHECK();
+    if (sus_tab) {
+        sus_table_kernel<<<(M + 1 + 255) / 256, 256, 0, s>>>(prefix, P, M, sus_tab);
+        GPGA_LAUNCH_CHECK();
+    }
     return GPGA_OK;
 }
 

@@ -143,11 +143,19 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
     }
     __syncwarp();
     // scatter gene indices by label (order inside a cluster is irrelevant: the
-    // pair sums below are exact integer sums)
-    for (int i = lane; i < N; i += 32) {
-        const int s = sl.lab[i], sh = (s & 1) << 4;
-        const uint32_t old = atomicAdd(&sl.cnt[s >> 1], 1u << sh);
-        sl.mem[(old >> sh) & 0xffffu] = (uint16_t)i;
+    // pair sums below are exact integer sums), four atomics in flight per lane
+    for (int i0 = lane; i0 < N; i0 += 128) {
+        int sv[4];
+        uint32_t old[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sv[u] = i0 + 32 * u < N ? (int)sl.lab[i0 + 32 * u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            old[u] = sv[u] >= 0 ? atomicAdd(&sl.cnt[sv[u] >> 1], 1u << ((sv[u] & 1) << 4)) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (sv[u] >= 0)
+                sl.mem[(old[u] >> ((sv[u] & 1) << 4)) & 0xffffu] = (uint16_t)(i0 + 32 * u);
     }
     __syncwarp();
     const int *list = sl.list;

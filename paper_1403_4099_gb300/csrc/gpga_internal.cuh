@@ -385,7 +385,9 @@ struct SelectCfg {
     int record;
 };
 
-int rank_prefix_table(uint64_t *prefix, int P, cudaStream_t s);
+// the fixed rank-scaling prefix (P entries) and, if sus_tab is given, its SUS
+// brackets (M + 1 entries, see sus_parent_tab)
+int rank_prefix_table(uint64_t *prefix, int P, int M, int32_t *sus_tab, cudaStream_t s);
 
 template <typename LabT>
 int launch_init_uniform(LabT *pop, int ldp, int P, int N, int K0, uint32_t k0, uint32_t k1,
@@ -437,6 +439,7 @@ struct EvolveCfg {
     uint32_t k0, k1;
     int gen; // stateless generation (when st == nullptr)
     uint32_t gap[MUT_BLOCK];
+    const int32_t *sus_tab; // SUS brackets of a fixed prefix (rank scaling), or nullptr
 };
 
 // fill cfg->thr_pm and cfg->gap for mutation probability pm (host)
@@ -514,6 +517,29 @@ __device__ __forceinline__ int sus_parent_half(uint32_t k, uint32_t u, uint64_t 
     return perm[lo];
 }
 
+// The same parent with the brackets of a prefix that does not change between
+// generations (rank scaling): tab[k] = first rank r with prefix[r] > floor(k W / M),
+// k = 0..M. Pointer k lies in [floor(k W / M), floor((k + 1) W / M)], so its rank
+// is tab[k] + #{r in [tab[k], tab[k+1]) : prefix[r] <= x_k}: the bracket loads
+// do not wait for x_k, and one round of at most 16 prefix loads per half-warp
+// replaces the 16-ary search. A wider bracket (very few pointers for the
+// ranks) takes the general search.
+__device__ __forceinline__ int sus_parent_tab(uint32_t k, uint32_t u, uint64_t W, int M, int P,
+                                              double inv_md, const uint64_t *__restrict__ prefix,
+                                              const int32_t *__restrict__ tab,
+                                              const int32_t *__restrict__ perm, int lane)
+{
+    const int lo = __ldg(tab + k), hi = __ldg(tab + k + 1);
+    if (__all_sync(0xffffffffu, hi - lo <= 16)) {
+        const uint64_t x = sus_pointer(k, u, W, (uint32_t)M, inv_md);
+        const int l = lane & 15;
+        const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
+        const bool le = l < hi - lo && __ldg(prefix + lo + l) <= x;
+        return perm[lo + __popc(__ballot_sync(0xffffffffu, le) & half)];
+    }
+    return sus_parent_half(k, u, W, M, P, inv_md, prefix, perm, lane);
+}
+
 // number of genes the next mutation skips for word u: #{t : u < gap[t]}
 __device__ __forceinline__ int mutation_skip(uint32_t u, const EvolveCfg &cfg)
 {
@@ -576,8 +602,11 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
     const int M = cfg.M;
     const uint64_t W = __ldg(prefix + cfg.P - 1);
     const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
-    const int par = sus_parent_half(lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M), su.x, W,
-                                    M, cfg.P, cfg.inv_md, prefix, perm, lane);
+    const uint32_t kp = lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M);
+    const int par = cfg.sus_tab ? sus_parent_tab(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix,
+                                                 cfg.sus_tab, perm, lane)
+                                : sus_parent_half(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix, perm,
+                                                  lane);
     const int ia = __shfl_sync(0xffffffffu, par, 0);
     const int ib = __shfl_sync(0xffffffffu, par, 16);
     if (parents_out && lane == 0) parents_out[k] = ia;
