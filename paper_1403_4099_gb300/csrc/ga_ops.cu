@@ -1,6 +1,6 @@
 // ga_ops.cu -- the device-resident GA generation of Algorithm 1 after scoring:
 // evaluate state and statistics, termination test, isolate fittest, elitism,
-// scaling, SUS selection (one single-CTA kernel), then crossover, mutation and
+// scaling, SUS selection (one grid launch per generation), then crossover, mutation and
 // replacement (one warp per child). All decisions are integer or exact
 // comparisons of FP64 values, so the result is bit-identical to any other
 // implementation of the same rules fed the same fitness vector and Philox key.
