@@ -304,7 +304,8 @@ __device__ __forceinline__ void generation_slot(const LabT *cur, LabT *nxt, cons
                                                 const int32_t *__restrict__ Dfix, int diag,
                                                 const double *__restrict__ logtab,
                                                 double *__restrict__ L, const GatherSlice &sl,
-                                                int lane, unsigned long long *pairs_out)
+                                                int lane, unsigned long long *pairs_out,
+                                                const SusPre *pre = nullptr)
 {
     const int N = cfg.N, ldp = cfg.ldp;
     LabT *dst = nxt + (size_t)slot * ldp;
@@ -318,7 +319,7 @@ __device__ __forceinline__ void generation_slot(const LabT *cur, LabT *nxt, cons
     } else {
         const int k = slot - cfg.E;
         child_genes<LabT>(cur, ldp, N, cfg, g, k, k0, k1, perm, prefix, nullptr, dst, sl.lab,
-                          lane);
+                          lane, pre);
     }
     __syncwarp();
     const double v = gather_score_warp(sl, N, Np, Dfix, diag,
@@ -337,23 +338,29 @@ __global__ void __launch_bounds__(256, 4)
                              double *__restrict__ L, const DevState *__restrict__ st,
                              unsigned long long *__restrict__ pairs)
 {
+    extern __shared__ unsigned char smem_g[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int slot = blockIdx.x * nw + warp;
+    if (slot >= cfg.P) return;
+    // the SUS loads that depend on no generation (fixed tables written at the
+    // start of the run), issued before the wait below
+    SusPre pre;
+    const bool use_pre = cfg.sus_tab != nullptr && slot >= cfg.E;
+    if (use_pre) pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
     // launched as a programmatic dependent of the selection (which lets it be
     // scheduled while its last CTA finishes): wait for that grid before reading
-    // perm, the prefix and the state. (Letting the selection in turn be
-    // scheduled early, from here, measured slower: its waiting CTAs cost the
-    // generation more than the launch gap they hide.)
+    // perm and the state. (Letting the selection in turn be scheduled early,
+    // from here, measured slower: its waiting CTAs cost the generation more
+    // than the launch gap they hide.)
     griddep_wait();
     if (st->done) return;
     const int g = st->gen;
     const LabT *cur = (g & 1) ? pop1 : pop0;
     LabT *nxt = (g & 1) ? next1 : next0;
-    extern __shared__ unsigned char smem_g[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int slot = blockIdx.x * nw + warp;
-    if (slot >= cfg.P) return;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
     generation_slot<LabT>(cur, nxt, cfg, g, st->k0, st->k1, slot, perm, prefix, Np, Dfix,
-                          *diag_flag, logtab, L, sl, lane, pairs ? pairs + g + 1 : nullptr);
+                          *diag_flag, logtab, L, sl, lane, pairs ? pairs + g + 1 : nullptr,
+                          use_pre ? &pre : nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -540,6 +540,30 @@ __device__ __forceinline__ int sus_parent_tab(uint32_t k, uint32_t u, uint64_t W
     return sus_parent_half(k, u, W, M, P, inv_md, prefix, perm, lane);
 }
 
+// The loads of sus_parent_tab that do not depend on the generation: the bracket
+// of the lane's pointer (k for lanes 0-15, (k + M/2) mod M for 16-31), the
+// lane's candidate prefix value in it and W. Both tables are fixed for the run,
+// so a kernel issues these before it waits for the selection.
+struct SusPre {
+    int lo, hi;    // bracket [lo, hi) of the lane's pointer
+    uint64_t cand; // prefix[lo + (lane & 15)] if that rank is inside the bracket
+    uint64_t W;    // prefix[P - 1]
+};
+
+__device__ __forceinline__ SusPre sus_prefetch(uint32_t k, int M, int P,
+                                               const uint64_t *__restrict__ prefix,
+                                               const int32_t *__restrict__ tab, int lane)
+{
+    SusPre s;
+    const uint32_t kp = lane < 16 ? k : (k + (uint32_t)M / 2) % (uint32_t)M;
+    s.lo = __ldg(tab + kp);
+    s.hi = __ldg(tab + kp + 1);
+    s.W = __ldg(prefix + P - 1);
+    const int l = lane & 15;
+    s.cand = l < s.hi - s.lo ? __ldg(prefix + s.lo + l) : 0ull;
+    return s;
+}
+
 // number of genes the next mutation skips for word u: #{t : u < gap[t]}
 __device__ __forceinline__ int mutation_skip(uint32_t u, const EvolveCfg &cfg)
 {
@@ -591,22 +615,32 @@ __device__ __forceinline__ void mutate_child(const EvolveCfg &cfg, int N, int g,
     __syncwarp();
 }
 
+// pre (optional): this child's sus_prefetch, issued earlier by the caller
 template <typename LabT>
 __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, const EvolveCfg &cfg,
                                             int g, int k, uint32_t k0, uint32_t k1,
                                             const int32_t *__restrict__ perm,
                                             const uint64_t *__restrict__ prefix,
                                             int32_t *__restrict__ parents_out,
-                                            LabT *__restrict__ dst, uint16_t *lab_s, int lane)
+                                            LabT *__restrict__ dst, uint16_t *lab_s, int lane,
+                                            const SusPre *pre = nullptr)
 {
     const int M = cfg.M;
-    const uint64_t W = __ldg(prefix + cfg.P - 1);
+    const uint64_t W = pre ? pre->W : __ldg(prefix + cfg.P - 1);
     const U4 su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1);
     const uint32_t kp = lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M);
-    const int par = cfg.sus_tab ? sus_parent_tab(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix,
-                                                 cfg.sus_tab, perm, lane)
-                                : sus_parent_half(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix, perm,
-                                                  lane);
+    int par;
+    if (pre && __all_sync(0xffffffffu, pre->hi - pre->lo <= 16)) {
+        // sus_parent_tab with its loads already in registers
+        const uint64_t x = sus_pointer(kp, su.x, W, (uint32_t)M, cfg.inv_md);
+        const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
+        const bool le = (lane & 15) < pre->hi - pre->lo && pre->cand <= x;
+        par = perm[pre->lo + __popc(__ballot_sync(0xffffffffu, le) & half)];
+    } else {
+        par = cfg.sus_tab ? sus_parent_tab(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix, cfg.sus_tab,
+                                           perm, lane)
+                          : sus_parent_half(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix, perm, lane);
+    }
     const int ia = __shfl_sync(0xffffffffu, par, 0);
     const int ib = __shfl_sync(0xffffffffu, par, 16);
     if (parents_out && lane == 0) parents_out[k] = ia;
