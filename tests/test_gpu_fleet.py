@@ -67,6 +67,35 @@ def test_batch_matches_single_runs(gpga):
     b.close()
 
 
+def test_batch_long_runs_match_single_runs(gpga):
+    """Seventy generations without the stall rule, runs with clusters large
+    enough for the warp-wide pair sums: every run still equals the same run
+    alone, bit for bit, down to its whole final population and fitness."""
+    Ns = [100, 160, 48]
+    Cs = _windows(gpga, Ns, rep=7)
+    seeds = [5 + 3 * k for k in range(len(Ns))]
+    prm = _params(gpga, P=256, max_gens=70, tol=-1.0)
+    b = gpga.Batch(Cs, prm, seeds)
+    while b.step(8) > 0:
+        pass
+    gens, done, _ = b.status()
+    assert done.all() and (gens == 70).all()
+    for k, C in enumerate(Cs):
+        ga = gpga.GA(C, prm, seed=seeds[k])
+        ga.step(prm.max_gens)
+        lab, L, g = ga.best()
+        pop, Lpop = ga.population()
+        ga.close()
+        lb, Lb, gb = b.best(k)
+        assert gb == g == 70
+        np.testing.assert_array_equal(lb, lab)
+        assert Lb == L, (k, Lb, L)
+        pop_b, Lpop_b = b.population(k)
+        np.testing.assert_array_equal(pop_b, pop)
+        np.testing.assert_array_equal(Lpop_b, Lpop)
+    b.close()
+
+
 def test_batch_column_subsets(gpga):
     import torch
     win = synth.intraday(N=120, windows=4, W=390, stride=30)
