@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recover", action="store_true")
     ap.add_argument("--workload", default="planted",
-                    choices=["planted", "batched", "serving", "paper", "preprocess"],
+                    choices=["planted", "batched", "serving", "paper", "preprocess", "islands"],
                     help="planted: the N=500 headline; batched: 256 sliding intraday windows "
                          "in one fleet; serving: Poisson request stream; paper: the paper's "
                          "shapes (40-stock training set, 18-stock 1760-window stream, Table 3 "
-                         "parameters, a P_m x P_c sweep); preprocess: the steps upstream of C "
-                         "(EWMA correlation, market-mode removal, random-matrix cleaning)")
+                         "parameters, a P_m x P_c sweep); preprocess: the steps around the path "
+                         "(EWMA correlation, market-mode removal, random-matrix cleaning, "
+                         "per-cluster trees); islands: the island model against one population")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
@@ -754,6 +755,8 @@ def run_preprocess(args, ranks):
         runtime.barrier(ranks)
         rmtB_s = timed(rmt_batch, 3)
         _, nnB, swB = rmt_batch()
+        lab = torch.from_numpy(pl.truth.astype(np.int32)).to(dev)
+        mst_s = timed(lambda: gpga.cluster_mst(C, lab, stream=stream), 3)
     max_secs, total = runtime.aggregate(ranks, rmtB_s, float(st.windows), device=dev)
     if ranks.rank != 0:
         runtime.barrier(ranks)
@@ -776,6 +779,9 @@ def run_preprocess(args, ranks):
     for k in range(nb):
         oracle.clean_rmt(Csh[k], st.W)
     orcB = (time.perf_counter() - t0) / nb
+    t0 = time.perf_counter()
+    oracle.cluster_mst(pl.truth, Ch)
+    orc_mst = time.perf_counter() - t0
     line = {"metric": "windows/s (random-matrix cleaning of the 18-stock stream: 1760 "
                       "correlation windows of 1800 bars, one batch)",
             "value": total / max_secs, "unit": "windows/s", "n_gpus": ranks.world, "steps": 3,
@@ -792,12 +798,87 @@ def run_preprocess(args, ranks):
                          "peak_source": "nominal FP64 rate (fallback: no measured FP64 peak)"},
             "ewma_corr_n500_t5000_ms": 1e3 * ewma_s,
             "market_removal_n500_ms": 1e3 * mkt_s,
+            "cluster_mst_n500_planted_ms": 1e3 * mst_s,
             "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(),
                              "rmt_n500_ms": 1e3 * orc500,
+                             "cluster_mst_n500_planted_ms": 1e3 * orc_mst,
                              "value": 1.0 / orcB, "unit": "windows/s",
                              "sample": f"{nb} of the 1760 windows, one by one (NumPy eigh, its "
                                        "default threads), and the N=500 matrix once"}}
     print(json.dumps(line), flush=True)
+    runtime.barrier(ranks)
+
+
+def run_islands(args, ranks):
+    """The island model (the variant the paper proposes, Sec. 5) against one
+    population of the same total size, on the N = 100 workload: 8 islands of 512
+    with ring migration of 2 elites every 10 generations, and one population of
+    4096; 200 generations each without the stall rule, so both make the same
+    number of evaluations. Each timed from its start call to its last step."""
+    import torch
+
+    from paper_1403_4099_gb300 import gpga, metrics, runtime, synth
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    runtime.init_dist(ranks, "nccl")
+    stream = torch.cuda.Stream(device=dev)
+    G, K, PI = 200, 8, 512
+    pl = synth.n100(replicate=ranks.rank)
+    with torch.cuda.stream(stream):
+        C = gpga.cluster_corr(torch.from_numpy(pl.R).to(dev), stream=stream)
+        stream.synchronize()
+
+        def island_job(seed):
+            prm = gpga.default_params(P=PI, elite=10, max_gens=G, tol=-1.0, pm=0.01,
+                                      form=gpga.FORM_GATHER)
+            t0 = time.perf_counter()
+            b = gpga.Batch.islands(C, prm, K, seed=seed, migrate_every=10, migrants=2,
+                                   stream=stream)
+            while b.step(16) > 0:
+                pass
+            stream.synchronize()
+            secs = time.perf_counter() - t0
+            best = max((b.best(k) for k in range(K)), key=lambda t: t[1])
+            b.close()
+            return secs, best
+
+        def single_job(seed):
+            prm = gpga.default_params(P=K * PI, elite=10, max_gens=G, tol=-1.0, pm=0.01,
+                                      form=gpga.FORM_GATHER)
+            t0 = time.perf_counter()
+            ga = gpga.GA(C, prm, seed=seed, stream=stream)
+            ga.step(G)
+            stream.synchronize()
+            secs = time.perf_counter() - t0
+            best = ga.best()
+            ga.close()
+            return secs, best
+
+        island_job(1)  # warm-up (library, tuner, graphs)
+        single_job(1)
+        runtime.barrier(ranks)
+        res_i = [island_job(100 + k) for k in range(args.steps // 4 or 1)]
+        res_s = [single_job(100 + k) for k in range(args.steps // 4 or 1)]
+    ti = float(np.median([r[0] for r in res_i]))
+    ts = float(np.median([r[0] for r in res_s]))
+    evals = float(K * PI * (G + 1))
+    max_t, total = runtime.aggregate(ranks, ti, evals, device=dev)
+    if ranks.rank == 0:
+        def summary(res):
+            return {"best_L": [float(r[1][1]) for r in res],
+                    "ari": [float(metrics.ari(r[1][0], pl.truth)) for r in res]}
+        line = {"metric": "fitness evals/s (island model: 8 islands x P=512, N=100, 200 "
+                          "generations, ring migration of 2 elites every 10)",
+                "value": total / max_t, "unit": "evals/s", "n_gpus": ranks.world,
+                "steps": len(res_i), "warmup": 1, "ms_per_step": 1e3 * max_t,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "islands_n100_t2000_k8_p512_g200", "migrate_every": 10,
+                           "migrants": 2, "pm": 0.01},
+                "islands": summary(res_i),
+                "single_population_p4096": {"evals_per_s": evals / ts, "ms": 1e3 * ts,
+                                            **summary(res_s)}}
+        print(json.dumps(line), flush=True)
     runtime.barrier(ranks)
 
 
@@ -819,6 +900,9 @@ def main():
         return
     if args.workload == "preprocess":
         run_preprocess(args, ranks)
+        return
+    if args.workload == "islands":
+        run_islands(args, ranks)
         return
     run_gpu(args, ranks)
 
