@@ -761,7 +761,7 @@ def run_preprocess(args, ranks):
     if ranks.rank != 0:
         runtime.barrier(ranks)
         return
-    # Jacobi FP64 work: per round 3 n2^2 flops on A (upper pair-blocks, 24 flops
+    # Jacobi FP64 work: per Jacobi round 3 n2^2 flops on A (upper pair-blocks, 24 flops
     # per 2 x 2 block) and 3 n2^2 on V, n2 - 1 rounds per sweep
     def jacobi_flops(N, sweeps, B=1):
         n2 = N + (N & 1)

@@ -1,4 +1,4 @@
-"""Oracle pre-processing upstream of C (SURVEY NEXT-1): the EWMA-weighted
+"""Oracle pre-processing upstream of C: the EWMA-weighted
 Pearson correlation and the market-mode removal, pinned against library
 routines (NumPy's weighted covariance, LAPACK eigenvectors) and closed forms."""
 import numpy as np
