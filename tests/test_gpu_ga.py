@@ -36,6 +36,7 @@ CASES = [
     (333, 65, 5, 0.7, 0.3, 0.05, 1, 2),
     (2, 2, 1, 1.0, 1.0, 1.0, 0, 1),
     (129, 31, 128, 0.9, 0.9, 0.5, 1, 9),
+    (16384, 40, 10, 0.9, 0.9, 0.05, 0, 5),  # the largest population accepted
 ]
 
 

@@ -71,6 +71,30 @@ def test_ragged_sizes(g, orc, form, N):
         assert_L_close(got, orc.loglik_batch(pop, C), f"N={N} P={P}")
 
 
+_MAXN = {}
+
+
+def _max_n_corr(orc):
+    # one C for the three forms (the oracle's Pearson at N = 4096 takes seconds)
+    if "C" not in _MAXN:
+        rng = np.random.default_rng(4096)
+        R = rng.standard_normal((300, 4096)) + rng.standard_normal((300, 1))
+        _MAXN["C"] = orc.pearson(R)
+    return _MAXN["C"]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_maximum_n(g, orc, form):
+    """N = 4096, the largest configuration the library accepts: singletons
+    mostly (K = N) and about 40 members per cluster (K = N / 100)."""
+    C = _max_n_corr(orc)
+    N = C.shape[0]
+    rng = np.random.default_rng(7)
+    for K in (N, N // 100):
+        pop = synth.random_labels(rng, 6, N, K=K)
+        assert_L_close(_score(g, pop, C, form), orc.loglik_batch(pop, C), f"K={K}")
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_full_size_n500_p4096(g, orc, form):
     """The benchmark's workload size, in the benchmark's launch shape: every
