@@ -17,7 +17,7 @@
 namespace gpga {
 
 static constexpr int CS_COLS = 32, CS_ROWS = 8; // column-stat CTA: 32 columns x 8 row lanes
-static constexpr int T_SLAB = 512;              // rows per column-stat CTA
+static constexpr int T_SLAB = 128;              // rows per column-stat CTA
 
 // column sums over a slab of rows: sum_t w_t (R_tj - mean_j)^2 with mean, else
 // sum_t w_t R_tj (w == nullptr: all weights 1)
@@ -33,11 +33,25 @@ __global__ void colsum_kernel(const double *__restrict__ R, int T, int N, int ld
     double s = 0.0;
     if (j < N) {
         const double mu = mean ? mean[j] : 0.0;
-        for (int t = t0 + ry; t < t1; t += CS_ROWS) {
+        // four rows in flight per thread, four partial sums (fixed order)
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        int t = t0 + ry;
+        for (; t + 3 * CS_ROWS < t1; t += 4 * CS_ROWS) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = R[(size_t)(t + u * CS_ROWS) * ld + j] - mu;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double x = mean ? v[u] * v[u] : v[u];
+                a[u] += w ? w[t + u * CS_ROWS] * x : x;
+            }
+        }
+        for (; t < t1; t += CS_ROWS) {
             const double v = R[(size_t)t * ld + j] - mu;
             const double x = mean ? v * v : v;
-            s += w ? w[t] * x : x;
+            a[0] += w ? w[t] * x : x;
         }
+        s = (a[0] + a[1]) + (a[2] + a[3]);
     }
     red[ry][cx] = s;
     __syncthreads();
@@ -70,21 +84,24 @@ __global__ void colfinal_kernel(const double *__restrict__ part, int nslab, int 
     }
 }
 
-// Z_tj = sqrt(w_t) (R_tj - mean_j) / sqrt(q_j) (sw = sqrt(w), nullptr: 1)
+// Z_tj = sqrt(w_t) (R_tj - mean_j) / sqrt(q_j) (sw = sqrt(w), nullptr: 1);
+// CTA y takes rows y, y + gridDim.y, ...; its threads the columns of a row
 __global__ void normalise_kernel(const double *__restrict__ R, int T, int N, int ld, int Np,
                                  const double *__restrict__ mean, const double *__restrict__ inv,
                                  const double *__restrict__ sw, float *__restrict__ Z)
 {
-    const size_t total = (size_t)T * Np;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int t = (int)(idx / Np), j = (int)(idx - (size_t)t * Np);
-        float z = 0.f;
-        if (j < N) {
-            const double x = (R[(size_t)t * ld + j] - mean[j]) * inv[j];
-            z = (float)(sw ? sw[t] * x : x);
+    for (int t = blockIdx.y; t < T; t += gridDim.y) {
+        const double st = sw ? sw[t] : 1.0;
+        const double *row = R + (size_t)t * ld;
+        float *zr = Z + (size_t)t * Np;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Np; j += gridDim.x * blockDim.x) {
+            float z = 0.f;
+            if (j < N) {
+                const double x = (row[j] - mean[j]) * inv[j];
+                z = (float)(sw ? st * x : x);
+            }
+            zr[j] = z;
         }
-        Z[idx] = z;
     }
 }
 
@@ -120,8 +137,8 @@ __global__ void __launch_bounds__(256)
     gram_kernel(const float *__restrict__ Z, int T, int Np, int nb, int trange,
                 double *__restrict__ part, int ntiles)
 {
-    __shared__ float As[GK][GT];
-    __shared__ float Bs[GK][GT];
+    __shared__ float As[2][GK][GT];
+    __shared__ float Bs[2][GK][GT];
     // tile index -> (bi, bj) with bi <= bj
     int tile = blockIdx.x, bi = 0;
     while (tile >= nb - bi) {
@@ -137,6 +154,25 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc64[a][b] = 0.0;
+    // 16 rows x 64 columns of each operand per slice: 1024 floats, 4 per thread
+    float ra[4], rb[4];
+    auto fetch = [&](int t, int te) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = threadIdx.x + 256 * r;
+            const int tt = t + (e >> 6), c = e & 63;
+            ra[r] = tt < te ? Z[(size_t)tt * Np + bi * GT + c] : 0.f;
+            rb[r] = tt < te ? Z[(size_t)tt * Np + bj * GT + c] : 0.f;
+        }
+    };
+    auto stage = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = threadIdx.x + 256 * r;
+            As[buf][e >> 6][e & 63] = ra[r];
+            Bs[buf][e >> 6][e & 63] = rb[r];
+        }
+    };
     for (int ts = t0; ts < t1; ts += SUB) {
         const int te = min(t1, ts + SUB);
         float acc[4][4];
@@ -144,31 +180,31 @@ __global__ void __launch_bounds__(256)
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        // double-buffered slices: the next slice's loads are in flight while the
+        // current one is multiplied (one barrier per slice)
+        fetch(ts, te);
+        stage(0);
+        __syncthreads();
+        int buf = 0;
         for (int t = ts; t < te; t += GK) {
-            // 16 rows x 64 columns of each operand: 1024 floats, 4 per thread
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int e = threadIdx.x + 256 * r;
-                const int kk = e >> 6, c = e & 63;
-                const int tt = t + kk;
-                As[kk][c] = tt < te ? Z[(size_t)tt * Np + bi * GT + c] : 0.f;
-                Bs[kk][c] = tt < te ? Z[(size_t)tt * Np + bj * GT + c] : 0.f;
-            }
-            __syncthreads();
+            const bool more = t + GK < te;
+            if (more) fetch(t + GK, te);
 #pragma unroll
             for (int kk = 0; kk < GK; ++kk) {
                 float a[4], b[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    a[q] = As[kk][ty * 4 + q];
-                    b[q] = Bs[kk][tx * 4 + q];
+                    a[q] = As[buf][kk][ty * 4 + q];
+                    b[q] = Bs[buf][kk][tx * 4 + q];
                 }
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
 #pragma unroll
                     for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
             }
+            if (more) stage(buf ^ 1);
             __syncthreads();
+            buf ^= 1;
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
@@ -182,26 +218,39 @@ __global__ void __launch_bounds__(256)
         for (int y = 0; y < 4; ++y) dst[(ty * 4 + x) * GT + tx * 4 + y] = acc64[x][y];
 }
 
-__global__ void gram_final_kernel(const double *__restrict__ part, int nslab, int ntiles, int nb,
-                                  int N, double *__restrict__ C)
+// CTA (tile, y): rows 16 y .. 16 y + 15 of tile `tile` (upper triangle, bi <= bj);
+// the partials summed in slab order, then written as rows (coalesced) and, from
+// shared memory, as the columns of the mirrored tile
+__global__ void __launch_bounds__(256)
+    gram_final_kernel(const double *__restrict__ part, int nslab, int ntiles, int nb, int N,
+                      double *__restrict__ C)
 {
+    __shared__ double a_s[16][GT + 1];
     int tile = blockIdx.x, bi = 0;
     while (tile >= nb - bi) {
         tile -= nb - bi;
         ++bi;
     }
     const int bj = bi + tile;
-    for (int e = threadIdx.x; e < GT * GT; e += blockDim.x) {
-        const int r = e / GT, c = e - r * GT;
-        const int i = bi * GT + r, j = bj * GT + c;
-        if (i >= N || j >= N || (bi == bj && j < i)) continue;
+    const int r0 = blockIdx.y * 16;
+    const size_t tstride = (size_t)ntiles * (GT * GT);
+    for (int e = threadIdx.x; e < 16 * GT; e += blockDim.x) {
+        const int rr = e / GT, c = e - rr * GT, r = r0 + rr;
+        const double *src = part + (size_t)blockIdx.x * (GT * GT) + r * GT + c;
         double a = 0.0;
-        for (int k = 0; k < nslab; ++k) a += part[((size_t)k * ntiles + blockIdx.x) * (GT * GT) + e];
+        for (int k = 0; k < nslab; ++k) a += src[(size_t)k * tstride];
+        const int i = bi * GT + r, j = bj * GT + c;
         if (i == j) a = 1.0;
         if (a > 1.0) a = 1.0;
         if (a < -1.0) a = -1.0;
-        C[(size_t)i * N + j] = a;
-        C[(size_t)j * N + i] = a;
+        a_s[rr][c] = a;
+        if (i < N && j < N && !(bi == bj && j < i)) C[(size_t)i * N + j] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * GT; e += blockDim.x) {
+        const int c = e >> 4, rr = e & 15, r = r0 + rr;
+        const int i = bi * GT + r, j = bj * GT + c;
+        if (i < N && j < N && !(bi == bj && j < i)) C[(size_t)j * N + i] = a_s[rr][c];
     }
 }
 
@@ -256,12 +305,11 @@ int corr_run_weighted(const double *R, int T, int N, int ld, double lambda, doub
         colfinal_kernel<<<(N + 255) / 256, 256, 0, s>>>(part, nslab_c, T, ws_, N, mean, 0, err);
         colsum_kernel<<<cgrid, cblock, 0, s>>>(R, T, N, ld, mean, wv, part);
         colfinal_kernel<<<(N + 255) / 256, 256, 0, s>>>(part, nslab_c, T, ws_, N, inv, 1, err);
-        const size_t zt = (size_t)T * Np;
-        int zb = (int)((zt + 255) / 256);
-        if (zb > 8192) zb = 8192;
-        normalise_kernel<<<zb, 256, 0, s>>>(R, T, N, ld, Np, mean, inv, swv, Z);
+        const int zx = (Np + 255) / 256;
+        const int zy = T < 65535 / zx ? T : 65535 / zx;
+        normalise_kernel<<<dim3(zx, zy), 256, 0, s>>>(R, T, N, ld, Np, mean, inv, swv, Z);
         gram_kernel<<<dim3(ntiles, nsplit), 256, 0, s>>>(Z, T, Np, nb, trange, gpart, ntiles);
-        gram_final_kernel<<<ntiles, 256, 0, s>>>(gpart, nsplit, ntiles, nb, N, C);
+        gram_final_kernel<<<dim3(ntiles, GT / 16), 256, 0, s>>>(gpart, nsplit, ntiles, nb, N, C);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             rc = cuda_error(e, "cluster_corr kernels", __FILE__, __LINE__);
