@@ -168,7 +168,8 @@ def gather_roofline(launch_ms, pk, pk_kind, pairs_per_gen):
 def launches_per_step(form: str, gens: int) -> int:
     corr = 7                      # colsum x2, colfinal x2, normalise, gram, gram_final
     score = {"plain": 2, "tensor": 4, "gather": 1}[form]
-    start = 5 + score + 1         # state, prep_d, rank table, SUS brackets, init, score, select
+    start = 3 + score + 1         # state, prep_d, init, score, select (the rank and SUS
+                                  # tables are built once per handle, before the timed steps)
     per_gen = (1 if form == "gather" else 1 + score) + 1  # (fused | evolve + score), select
     return corr + start + gens * per_gen
 

@@ -113,6 +113,7 @@ struct gpga_ga {
     unsigned *ticket = nullptr;
     uint64_t *rank_prefix = nullptr, *work_prefix = nullptr;
     int32_t *sus_tab = nullptr; // SUS brackets of rank_prefix (P + 1)
+    bool tables_ready = false;  // rank_prefix and sus_tab depend on P and E only
     DevState *st = nullptr;
     double *hist = nullptr;
     uint16_t *ring = nullptr;
@@ -328,8 +329,11 @@ int enqueue_start(gpga_ga *h, const double *C)
     rc = launch_prep_d(h->C64, h->N, h->N, h->Np, h->D32, h->Dhi, h->Dlo, h->Dfix, h->logtab,
                        h->diag, h->stream);
     if (rc) return rc;
-    rc = rank_prefix_table(h->rank_prefix, h->P, h->M, h->sus_tab, h->stream);
-    if (rc) return rc;
+    if (!h->tables_ready) { // once per handle: a reset keeps P and E
+        rc = rank_prefix_table(h->rank_prefix, h->P, h->M, h->sus_tab, h->stream);
+        if (rc) return rc;
+        h->tables_ready = true;
+    }
     if (h->prm.init == GPGA_INIT_THRESHOLD) {
         rc = launch_mst(h->C64, h->N, h->mst_order, h->mst_from, h->mst_w, h->stream);
         if (rc) return rc;
