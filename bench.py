@@ -811,7 +811,7 @@ def run_preprocess(args, ranks):
 
 
 def run_islands(args, ranks):
-    """The island model (the variant the paper proposes, Sec. 5) against one
+    """The island model (the variant the paper proposes, Sec. 5.2 and 6) against one
     population of the same total size, on the N = 100 workload: 8 islands of 512
     with ring migration of 2 elites every 10 generations, and one population of
     4096; 200 generations each without the stall rule, so both make the same

@@ -229,8 +229,8 @@ GPGA_API int ga_population(gpga_ga *h, int32_t *pop, double *L);
 
 /*
  * cluster_corr_ewma -- pre-processing upstream of C (no counterpart in the
- * hot path; Sec. 5 names exponentially weighted estimates for near-real-time
- * use): the EWMA-weighted Pearson correlation of R (device, T x N FP64,
+ * hot path; Sec. 4.2 computes the covariance with an online exponentially
+ * weighted filter): the EWMA-weighted Pearson correlation of R (device, T x N FP64,
  * leading dimension ld): rows weighted w_t = lambda^(T-1-t) (the newest row
  * weighs 1) in the means, the variances and the cross products; lambda = 1 is
  * cluster_corr. C (device, N x N FP64) written, diagonal 1. Errors as
@@ -279,7 +279,7 @@ GPGA_API int corr_clean_rmt(double *C, int batch, int N, double T, double *eigva
 
 /*
  * cluster_mst -- minimum spanning tree of every cluster of one configuration
- * (the cluster trees the paper draws for the clusters it finds, Sec. 4), on
+ * (the cluster trees the paper draws for the clusters it finds, Sec. 4.2), on
  * the correlation distance d_ij = sqrt(2 (1 - C_ij)) (the upper-triangle
  * entry C_ij, i < j, is the one read), by Prim's algorithm from each
  * cluster's first gene; ties go to the lower gene index.
@@ -332,7 +332,7 @@ GPGA_API int ga_free(gpga_ga *h);
 
 /* ------------------------------------------------------------------------
  * Batch: many independent GA runs (e.g. one per sliding window of a returns
- * series, each window's C being the input of one run as in Sec. 4) advanced
+ * series, each window's C being the input of one run as in Sec. 4.2) advanced
  * together. Each run is exactly the single-run gather form with its own C, N
  * and seed: same parameters as ga_init (p->form must be GPGA_FORM_GATHER;
  * record and profile must be 0), and bit-for-bit the same result as ga_init +
@@ -385,7 +385,7 @@ GPGA_API int ga_batch_tuning(gpga_batch *h, int *warps_per_cta, int *ctas, float
 GPGA_API int ga_batch_population(gpga_batch *h, int run, int32_t *pop, double *L);
 
 /*
- * ga_island_init -- the island variant the paper proposes (Sec. 5): `islands`
+ * ga_island_init -- the island variant the paper proposes (Sec. 5.2 and 6): `islands`
  * populations of the same C (device, N x N FP64, copied), island k seeded
  * with seed + k, advanced together like a batch (ga_batch_step, _status,
  * _best, _population, _free apply). Migration on a ring: when the generation

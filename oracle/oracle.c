@@ -682,7 +682,7 @@ done:
     return rc;
 }
 
-/* Island model (the variant proposed in Sec. 5), ring migration after the
+/* Island model (the variant proposed in Sec. 5.2 and 6), ring migration after the
  * operators of one generation: K populations of P x N (pops, island-major)
  * with the fitness of their members (Ls); island k's first m members (its
  * elites, m <= E) replace, with their fitness, the last m members of island
@@ -824,7 +824,7 @@ int orc_brute_force(const double *C, int N, int32_t *best, double *bestL, int64_
 /* The denominator vanishes only when both are all-singleton or both a single  */
 /* cluster, i.e. identical: 1 is returned. NaN on bad labels.                  */
 /* EWMA-weighted Pearson correlation (pre-processing upstream of C: the
- * exponentially weighted estimate used for near-real-time updates, Sec. 5):
+ * covariance the paper computes with an online exponentially weighted filter, Sec. 4.2):
  * rows weighted w_t = lambda^(T-1-t) (the newest row weighs 1), weighted
  * means mu_j = sum_t w_t R_tj / sum_t w_t, and
  * C_ij = sum_t w_t (R_ti - mu_i)(R_tj - mu_j) / sqrt(q_i q_j),
@@ -882,7 +882,7 @@ int orc_pearson_ewma(const double *R, int T, int N, int ld, double lambda, doubl
 }
 
 /* Minimum spanning tree of every cluster of configuration s (the trees the
- * paper draws for the clusters it finds, Sec. 4), on the correlation distance
+ * paper draws for the clusters it finds, Sec. 4.2), on the correlation distance
  * d_ij = sqrt(2 (1 - C_ij)), by Kruskal's algorithm: the cluster's pairs
  * i < j sorted by (d, i, j), each joining two components kept (union-find).
  * Output, clusters in first-occurrence order, for each its n_s - 1 edges

@@ -428,7 +428,7 @@ int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectC
 }
 
 // ---------------------------------------------------------------------------
-// Island model (the variant the paper proposes, Sec. 5): the runs of a fleet
+// Island model (the variant the paper proposes, Sec. 5.2 and 6): the runs of a fleet
 // are islands on one C, in a ring by table position. When the generation
 // being built, g + 1, is a multiple of `every`, island z copies the first m
 // slots of its new population -- its m best of generation g, placed there by

@@ -169,7 +169,7 @@ template int launch_init_threshold<int32_t>(int32_t *, int, int, int, const int3
 
 // ---------------------------------------------------------------------------
 // Minimum spanning tree of every cluster of one configuration (the cluster
-// trees drawn in Sec. 4) on the correlation distance d_ij = sqrt(2 (1 - C_ij)),
+// trees drawn in Sec. 4.2) on the correlation distance d_ij = sqrt(2 (1 - C_ij)),
 // by Prim's algorithm from each cluster's first gene. One CTA: canonical ids
 // by first occurrence (atomicMin + block scan), members grouped by cluster,
 // then the clusters one after another, every Prim step a block-wide argmin
