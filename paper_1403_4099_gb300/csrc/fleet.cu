@@ -350,11 +350,12 @@ static int fleet_upload(Fleet *f, int b, long long tick)
     return GPGA_OK;
 }
 
-static int fleet_gen_launch(Fleet *f, int warps, int ctas)
+// pdl: the launch directly follows the fleet's selection in a captured graph
+static int fleet_gen_launch(Fleet *f, int warps, int ctas, bool pdl = false)
 {
     return launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
                                    f->logtab, f->Np_max, warps, ctas,
-                                   f->prm.scaling == GPGA_SCALING_PROP, f->stream);
+                                   f->prm.scaling == GPGA_SCALING_PROP, f->stream, pdl);
 }
 
 // Autotuner: warps per CTA (individuals per CTA) and grid shape of the fused
@@ -440,7 +441,7 @@ static int fleet_graph(Fleet *f, int gens, cudaGraphExec_t *out)
     GPGA_CUDA(cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
     int rc = GPGA_OK;
     for (int k = 0; k < gens && !rc; ++k) {
-        rc = fleet_gen_launch(f, f->warps, f->ctas);
+        rc = fleet_gen_launch(f, f->warps, f->ctas, k > 0);
         if (!rc && f->migrate_every > 0)
             rc = launch_fleet_migrate(f->d_runs, f->d_hdr, f->P, f->migrate_every, f->migrants,
                                       f->cap, f->stream);

@@ -374,6 +374,9 @@ __global__ void __launch_bounds__(512, 2)
                             EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
                             const double *__restrict__ logtab, int Np_max, int prop)
 {
+    // may be launched as a programmatic dependent of the fleet's selection:
+    // wait for that grid before reading any run's state, permutation or prefix
+    griddep_wait();
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max);
@@ -456,14 +459,13 @@ int fleet_ctas_per_sm(int Np_max, int warps, int *out)
 
 int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
-                            int warps, int ctas, int prop, cudaStream_t s)
+                            int warps, int ctas, int prop, cudaStream_t s, bool pdl)
 {
     if (warps < 1 || warps > 16 || ctas < 1)
         return set_error(GPGA_ERR_ARG, "fleet generation: %d warps x %d CTAs", warps, ctas);
     const size_t smem = warps * gather_slice_bytes(Np_max);
-    fleet_generation_kernel<<<ctas, 32 * warps, smem, s>>>(runs, hdr, cfg, rank_prefix, logtab,
-                                                           Np_max, prop);
-    GPGA_LAUNCH_CHECK();
+    GPGA_CUDA(launch_pdl(fleet_generation_kernel, dim3(ctas), dim3(32 * warps), smem, s, pdl, runs,
+                         hdr, cfg, rank_prefix, logtab, Np_max, prop));
     return GPGA_OK;
 }
 

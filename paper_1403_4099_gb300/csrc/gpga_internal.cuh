@@ -745,7 +745,7 @@ int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectC
                         int cap, cudaStream_t s);
 int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
-                            int warps, int ctas, int prop, cudaStream_t s);
+                            int warps, int ctas, int prop, cudaStream_t s, bool pdl = false);
 // island migration over the fleet's runs (ring by table position): every
 // `every` generations, the m elites of each run replace the last m children
 // of the next run
