@@ -79,9 +79,10 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def profiled_value(kernel: str, src_hash: str, key: str):
+    """A per-launch counter (`key`) from the committed ncu summary
+    profiles/<kernel>_traffic.txt, if it was taken on the current kernel
+    source (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -93,9 +94,23 @@ def profiled_traffic(kernel: str, src_hash: str):
     if vals.get("source_hash") != src_hash:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(kernel: str, src_hash: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return profiled_value(kernel, src_hash, "dram_bytes_per_launch")
+
+
+def issue_fraction(warp_insts, launch_ms, sm_mhz):
+    """Warp instructions of one launch over the issue slots of its duration:
+    SMs x 4 schedulers x one instruction per cycle at the sampled SM clock."""
+    if not warp_insts or not launch_ms or not sm_mhz:
+        return None
+    slots = SMS * 4 * sm_mhz * 1e6 * launch_ms / 1e3
+    return warp_insts / slots
 
 
 # ---------------------------------------------------------------------------
@@ -149,21 +164,51 @@ def run_reference(args, ranks):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def gather_roofline(launch_ms, pk, pk_kind, pairs_per_gen):
+GATHER_PROFILE = ("gather_generation_n500_p4096", ("gather.cu", "gpga_internal.cuh"))
+
+
+def gather_roofline(launch_ms, pk, pk_kind, pairs_per_gen, sm_mhz=None):
     """Fused generation kernel (gather form): algorithmic bytes per launch =
     per child 2 parents read + child written (2 B labels, N genes) + one 4-byte
     D entry per same-cluster pair + 8 B of fitness; pairs measured on the
-    device for the timed generations."""
+    device for the timed generations. The working set is L2-resident, so the
+    bound that binds is instruction issue: `issue` gives the warp instructions
+    of one launch (committed ncu capture of the same source) over the issue
+    slots of the live launch time at the sampled SM clock."""
     bytes_per_launch = P * (3 * 2 * N + 8) + 4.0 * pairs_per_gen
     t = launch_ms / 1e3
     gbs = bytes_per_launch / t / 1e9
     peak = pk["hbm_gbs"]
+    kern, srcs = GATHER_PROFILE
+    h = source_hash(*srcs)
+    insts = profiled_value(kern, h, "warp_instructions_per_launch")
+    frac_issue = issue_fraction(insts, launch_ms, sm_mhz)
     return {"bound": "hbm", "kernel": "gather_generation", "achieved": gbs, "peak": peak,
             "unit": "GB/s", "frac": gbs / peak,
-            "traffic": profiled_traffic("gather_generation_n500_p4096",
-                                        source_hash("gather.cu", "gpga_internal.cuh")),
+            "traffic": profiled_traffic(kern, h),
             "peak_source": f"hbm_gbs ({pk_kind})", "algorithmic_bytes_per_launch": bytes_per_launch,
-            "same_cluster_pairs_per_launch": pairs_per_gen, "launch_ms": launch_ms}
+            "same_cluster_pairs_per_launch": pairs_per_gen, "launch_ms": launch_ms,
+            "issue": None if frac_issue is None else {
+                "bound": "issue", "frac": frac_issue,
+                "warp_instructions_per_launch": insts,
+                "warp_instructions_per_individual": insts / P,
+                "sm_mhz": sm_mhz,
+                "peak_source": f"{SMS} SMs x 4 schedulers x 1 warp instruction per cycle at "
+                               "the median SM clock sampled in the timed region"}}
+
+# arithmetic type of the path per form (what it computes in) and its detail
+DTYPE = {
+    "gather": ("int64", "pair sums of D = 1 - C as int32 fixed point 2^-30 added in int64 "
+                        "(exact); Eq. 8 assembled in integer fixed point (Q62 table log, "
+                        "result in Q40); FP64 column statistics in the Pearson prelude (FP32 "
+                        "Gram); integer GA operators"),
+    "plain": ("f32", "FP32 pair accumulation of D = 1 - C, fixed-point per-cluster sums, "
+                     "integer Eq. 8 assembly; integer GA operators"),
+    "tensor": ("bf16", "one-hot x D split BF16 hi + lo on tcgen05, FP32 accumulation in TMEM, "
+                       "fixed-point per-cluster sums, integer Eq. 8 assembly; integer GA "
+                       "operators"),
+}
+
 
 def launches_per_step(form: str, gens: int) -> int:
     corr = 7                      # colsum x2, colfinal x2, normalise, gram, gram_final
@@ -235,6 +280,7 @@ def run_gpu(args, ranks):
         ga_all.step(G)
         stages_all = ga_all.kernel_times()
         ga_all.close()
+        converged = run_converged(args, C, stream, form) if ranks.rank == 0 else None
     runtime.barrier(ranks)
 
     secs = sum(step_ms) / 1e3
@@ -291,17 +337,17 @@ def run_gpu(args, ranks):
         # launch (graphs of GRAPH_GENS generations, then single generations)
         tg = G if G % GRAPH_GENS else G - GRAPH_GENS + 1
         pairs = hist["pairs"]
-        roof = gather_roofline(main_ms, pk, pk_kind, float(pairs[tg]) if tg < len(pairs) else 0.0)
+        roof = gather_roofline(main_ms, pk, pk_kind, float(pairs[tg]) if tg < len(pairs) else 0.0,
+                               (clocks or {}).get("sm_mhz"))
         roof["timed_generation"] = int(tg)
     else:
         roof = None  # filled by the tensor form
 
-    # recovery: first generation whose best individual has ARI >= 0.99 vs the planted labels
-    ari = [metrics.ari(l, planted.truth) for l in hist["labels"]]
-    rec = next((g for g, a in enumerate(ari) if a >= 0.99), None)
-    ms_rec = {"uniform_init": None if rec is None else
-              float(hist["t_ns"][1 + rec] - hist["t_ns"][0]) / 1e6,
-              "uniform_init_best_ari": float(max(ari))}
+    # recovery within the timed step itself (first generation whose best
+    # individual has ARI >= 0.99 vs the planted labels)
+    g_rec, ms_step_rec, ari_best, _ = first_recovery(hist, planted.truth)
+    ms_rec = {"within_timed_step": {"generations": G, "generation": g_rec, "ms": ms_step_rec,
+                                    "best_ari": ari_best}}
 
     # end-to-end leg on every rank, aggregated like the device-timed value
     runtime.barrier(ranks)
@@ -334,17 +380,18 @@ def run_gpu(args, ranks):
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ranks.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_secs / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "dtype_detail": "FP32 pair accumulation, FP64 column statistics and log terms, "
-                            "integer GA operators",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.form][0], "dtype_detail": DTYPE[args.form][1],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "T": T, "P": P, "elite": ELITE,
                        "generations_per_step": G, "form": args.form, "init": "uniform",
                        "l2": "flushed between steps (256 MB memset outside the step events)"},
             "generations_per_s": gens_per_s,
-            "non_singleton_clusters_per_individual": {
+            **({"non_singleton_clusters_per_individual": {
                 "first_generation": float(hist["clusters"][0]) / P,
-                "last_generation": float(hist["clusters"][-1]) / P},
+                "last_generation": float(hist["clusters"][-1]) / P}}
+               if form == gpga.FORM_TENSOR else {}),
+            "converged_regime": converged,
             "same_cluster_pairs_per_individual": {
                 "first_generation": float(hist["pairs"][0]) / P,
                 "last_generation": float(hist["pairs"][-1]) / P,
@@ -360,6 +407,45 @@ def run_gpu(args, ranks):
         }
         print(json.dumps(line), flush=True)
     runtime.barrier(ranks)
+
+
+def run_converged(args, C, stream, form):
+    """The same G generations from a converged start: the correlation-threshold
+    initial population (components of C > tau, tau ~ U[0.05, 0.6)), whose
+    configurations hold the planted clusters, so that every child has large
+    clusters and the same-cluster pair gathers dominate. Only ga_step is
+    timed (CUDA events on the run's stream, L2 flushed before each step)."""
+    import torch
+
+    from paper_1403_4099_gb300 import gpga
+    G = args.gens
+    prm = gpga.default_params(P=P, elite=ELITE, max_gens=G, stall_gens=50, tol=-1.0, pm=0.01,
+                              form=form, init=gpga.INIT_THRESHOLD, record=1, profile=1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=C.device)
+    ga = gpga.GA(C, prm, seed=11, stream=stream)
+    ms, kern = [], []
+    steps = max(3, args.steps // 4)
+    for k in range(2 + steps):
+        ga.reset(C, 500 + k)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ga.step(G)
+        e1.record(stream)
+        kt = ga.kernel_times()
+        stream.synchronize()
+        if k >= 2:
+            ms.append(e0.elapsed_time(e1))
+            kern.append(float(kt[:, 0 if form == gpga.FORM_GATHER else 1].mean()))
+    h = ga.history()
+    ga.close()
+    t = float(np.mean(ms))
+    return {"init": "threshold (tau ~ U[0.05, 0.6))", "generations": G, "steps": steps,
+            "value": P * G / (t / 1e3), "unit": "evals/s", "ms_per_step": t,
+            "dominant_kernel_ms": float(np.mean(kern)),
+            "same_cluster_pairs_per_individual": {
+                "first_generation": float(h["pairs"][1]) / P,
+                "last_generation": float(h["pairs"][-1]) / P}}
 
 
 def run_e2e(args, ranks, R_host, dev, form, G):
@@ -396,15 +482,74 @@ def run_e2e(args, ranks, R_host, dev, form, G):
             "h2d_bytes_per_step": int(R_host.numel() * 8), "d2h_bytes_per_step": int(N * 4 + 8)}
 
 
+RECOVER_CONFIGS = (
+    # name, planted workload, P, E, generation cap
+    ("small16_p64", "small16", 64, 2, 2000),
+    ("n100_p1024", "n100", 1024, 10, 3000),
+    ("n500_p4096", "n500", 4096, 10, 5000),
+)
+RECOVER_SEEDS = (101, 202, 303)
+
+
+def first_recovery(h, truth):
+    """(generation, device ms from the start of ga_reset to the end of that
+    generation) of the first best configuration with ARI >= 0.99 (None if
+    none), and the best ARI with its generation."""
+    from paper_1403_4099_gb300 import metrics
+    labs = h["labels"]
+    ari = np.empty(len(labs))
+    prev, prev_a = None, 0.0
+    for g, l in enumerate(labs):
+        if prev is None or not np.array_equal(l, prev):  # the best changes rarely
+            prev, prev_a = l, metrics.ari(l, truth)
+        ari[g] = prev_a
+    hit = np.flatnonzero(ari >= 0.99)
+    g0 = int(hit[0]) if hit.size else None
+    ms = None if g0 is None else float(h["t_ns"][1 + g0] - h["t_ns"][0]) / 1e6
+    return g0, ms, float(ari.max()), int(ari.argmax())
+
+
 def run_recover(args, ranks, planted, dev, form):
-    """Device time from the start of ga_reset to the first generation whose best
-    individual has ARI >= 0.99, with the correlation-threshold initial
-    population; plus the prelude's own time."""
+    """Recovery of the planted clusters by the GA itself (Algorithm 1 from the
+    uniform initial population): for each workload and seed, device time from
+    the start of ga_reset to the first generation whose best individual has
+    ARI >= 0.99 against the planted partition (stall rule off, up to a cap of
+    generations). Also the correlation-threshold initialiser, reported apart:
+    it is a single-linkage cut of C and recovers the partition before any GA
+    operator runs (generation 0)."""
     import torch
 
-    from paper_1403_4099_gb300 import gpga, metrics
+    from paper_1403_4099_gb300 import gpga, metrics, synth
     stream = torch.cuda.Stream(device=dev)
+    out = {"uniform_init": {}}
     with torch.cuda.stream(stream):
+        for name, wl, Pw, Ew, cap in RECOVER_CONFIGS:
+            pl = planted if wl == "n500" else getattr(synth, wl)()
+            Rw = torch.from_numpy(pl.R).to(dev)
+            Nw = pl.R.shape[1]
+            Cw = torch.empty((Nw, Nw), dtype=torch.float64, device=dev)
+            gpga.cluster_corr(Rw, Cw, stream)
+            prm = gpga.default_params(P=Pw, elite=Ew, max_gens=cap, stall_gens=50, tol=-1.0,
+                                      pm=0.01, form=form, record=1)
+            ga = gpga.GA(Cw, prm, seed=1, stream=stream)
+            runs = []
+            for sd in RECOVER_SEEDS:
+                ga.reset(Cw, sd)
+                ga.step(cap)
+                h = ga.history()
+                g0, ms, best, gbest = first_recovery(h, pl.truth)
+                runs.append({"seed": sd, "generation": g0, "ms": ms, "best_ari": best,
+                             "best_ari_generation": gbest,
+                             "ms_per_generation": float(h["t_ns"][-1] - h["t_ns"][0]) / 1e6 /
+                                                  (len(h["t_ns"]) - 1)})
+            ga.close()
+            ok = [r["ms"] for r in runs if r["ms"] is not None]
+            out["uniform_init"][name] = {
+                "N": Nw, "P": Pw, "elite": Ew, "generation_cap": cap,
+                "recovered": f"{len(ok)}/{len(runs)}",
+                "median_ms": float(np.median(ok)) if ok else None,
+                "runs": runs}
+        # the single-linkage initialiser at the headline workload (not the GA)
         R = torch.from_numpy(planted.R).to(dev)
         C = torch.empty((N, N), dtype=torch.float64, device=dev)
         gpga.cluster_corr(R, C, stream)
@@ -422,12 +567,13 @@ def run_recover(args, ranks, planted, dev, form):
         ga.step(50)
         h = ga.history()
         ga.close()
-    ari = [metrics.ari(l, planted.truth) for l in h["labels"]]
-    rec = next((g for g, a in enumerate(ari) if a >= 0.99), None)
-    ms = None if rec is None else float(h["t_ns"][1 + rec] - h["t_ns"][0]) / 1e6
-    return {"threshold_init": ms, "threshold_init_generation": rec,
-            "threshold_init_best_ari": float(max(ari)), "prelude_ms": corr_ms,
-            "threshold_init_with_prelude": None if ms is None else ms + corr_ms}
+    g0, ms, best, _ = first_recovery(h, planted.truth)
+    out["single_linkage_initialiser"] = {
+        "what": "correlation-threshold initial population (components of C > tau_p, a "
+                "single-linkage cut); recovers before any GA operator runs",
+        "ms": ms, "generation": g0, "best_ari": best, "prelude_ms": corr_ms,
+        "ms_with_prelude": None if ms is None else ms + corr_ms}
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -108,6 +108,22 @@ GPGA_API int gpga_default_params(gpga_params *p);
 GPGA_API const char *gpga_last_error(void);
 
 /*
+ * gpga_set_wait_budget -- failure detection; the paper has no counterpart.
+ * Every wait of a kernel of this library on an on-chip barrier (the mbarrier
+ * hand-offs of the tcgen05 pipeline of GPGA_FORM_TENSOR) gives up once it has
+ * spent `cycles` SM clock cycles: the kernel then stops issuing work, waits
+ * (with the full default bound) for the tensor-core operations it has already
+ * issued, releases its tensor memory and returns; the call reports
+ * GPGA_ERR_TIMEOUT (ga_score at once; a GA run at ga_step with `done` or at
+ * ga_best) and the device context stays usable. cycles = 0 makes every such
+ * wait give up at its first check; cycles < 0 restores the default, 2^32
+ * cycles (about 2 s at the maximum SM clock). Process-wide; applies to kernels
+ * launched after the call, and a GA handle's generation graphs keep the budget
+ * in force when ga_step first captured them. Returns GPGA_OK.
+ */
+GPGA_API int gpga_set_wait_budget(long long cycles);
+
+/*
  * cluster_corr -- Pearson correlation matrix, Eq. 7 (Sec. 2.1; data normalised
  * to zero mean and unit variance below Eq. 2):
  *   C_ij = sum_t z_ti z_tj / sqrt(sum_t z_ti^2 sum_t z_tj^2),  z = R - column mean.
@@ -133,8 +149,10 @@ GPGA_API int cluster_corr(const double *R, int T, int N, int ld, double *C, void
  * which leaves Eq. 6 unchanged). L: device, P FP64 (written).
  * form: GPGA_FORM_PLAIN, GPGA_FORM_TENSOR or GPGA_FORM_GATHER.
  * Errors: GPGA_ERR_ARG for sizes out of range or any label outside [0, N)
- * (found on the device; the matching L entries are NaN). Blocks the host until
- * the stream reaches the end of the call.
+ * (found on the device; the matching L entries are NaN); GPGA_ERR_TIMEOUT if a
+ * bounded wait of the tensor form's tcgen05 pipeline gave up (every L is then
+ * NaN; see gpga_set_wait_budget). Blocks the host until the stream reaches the
+ * end of the call.
  */
 GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double *C, double *L,
                       int form, void *stream);
@@ -160,38 +178,61 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
                        int32_t *parents, void *stream);
 
 /*
- * ga_init -- create a GA run on correlation matrix C (device, N x N FP64; copied
- * and derived from, so the caller may free it on return): allocates the
- * population buffers, the FP32 and BF16 hi/lo forms of D = 1 - C and the
- * per-generation records, creates the initial population and scores it
- * (generation 0). Asynchronous on `stream`, which the handle keeps for all
- * later calls. Errors: GPGA_ERR_ARG (N < 2, N > GPGA_MAX_N, bad params),
- * GPGA_ERR_OOM. *out is NULL on error.
+ * ga_init -- create a GA run on correlation matrix C: Algorithm 1 "create
+ * initial population" and "evaluate fitness" of generation 0. The population
+ * is P label vectors in the representation of Eq. 9 (gene j = the cluster of
+ * stock j; 0-based labels, K = N), drawn uniformly (params.init =
+ * GPGA_INIT_UNIFORM) or as correlation-threshold components
+ * (GPGA_INIT_THRESHOLD), then scored with Eq. 8; the fittest is isolated and
+ * the termination test of Table 3 is applied.
+ * C: device, N x N FP64 (copied and derived from, so the caller may free it
+ * on return). Allocates the population buffers, the forms of D = 1 - C that
+ * params.form needs and the per-generation records; the handle owns them.
+ * Asynchronous on `stream`, which the handle keeps for all later calls
+ * (NULL: the handle creates its own non-blocking stream).
+ * Errors: GPGA_ERR_ARG (NULL C or out, N < 2, N > GPGA_MAX_N, bad params),
+ * GPGA_ERR_OOM, GPGA_ERR_CUDA. *out is NULL on error.
  */
 GPGA_API int ga_init(const double *C, int N, const gpga_params *p, uint64_t seed, void *stream,
                      gpga_ga **out);
 
 /*
- * ga_reset -- restart handle h on a new correlation matrix C (device, same N)
- * and seed without reallocating; generation 0 is created and scored.
- * Asynchronous.
+ * ga_reset -- restart handle h on a new correlation matrix C (device, same N,
+ * copied) and seed without reallocating: Algorithm 1 "create initial
+ * population" (Eq. 9) and the scoring of generation 0 (Eq. 8), exactly as
+ * ga_init. Clears the device error word. Asynchronous on the handle's stream.
+ * Errors: GPGA_ERR_ARG (NULL h or C), GPGA_ERR_CUDA.
  */
 GPGA_API int ga_reset(gpga_ga *h, const double *C, uint64_t seed);
 
 /*
- * ga_step -- run up to `generations` generations (evolve, score, rank, test
- * termination), all on the device with no host round trip; generations after
- * termination are no-ops. Asynchronous when done == NULL; otherwise waits for
- * the stream and writes 1 to *done if the run has terminated, else 0.
+ * ga_step -- run up to `generations` iterations of the loop of Algorithm 1
+ * (Sec. 3.1 operators: isolate fittest and elitism, scaling, stochastic
+ * universal sampling, crossover, mutation, replacement; then "evaluate
+ * fitness" with Eq. 8 and "determine if termination criteria are met" with
+ * Table 3's generation limit and stall rule), all on the device with no host
+ * round trip; generations after termination are no-ops. The generations run
+ * as CUDA graphs captured on the first call.
+ * Asynchronous when done == NULL. Otherwise waits for the stream, writes 1 to
+ * *done if the run has terminated (else 0) and reports the device error word:
+ * GPGA_ERR_TIMEOUT if a bounded device wait gave up (GPGA_FORM_TENSOR; the
+ * affected fitness values are NaN). Errors: GPGA_ERR_ARG (NULL h,
+ * generations < 0), GPGA_ERR_CUDA.
  */
 GPGA_API int ga_step(gpga_ga *h, int generations, int *done);
 
 /*
- * ga_best -- the fittest configuration of the current generation, canonically
- * relabelled by first occurrence (0, 1, 2, ...), with L re-scored in FP64
- * directly from the FP64 C (the final re-score). labels: host or device, N
- * int32 (optional); L: host or device, 1 FP64 (optional); generation: host
- * (optional). Waits for the handle's stream.
+ * ga_best -- the output of the method (Sec. 4.2: the cluster configuration of
+ * the fittest individual and its likelihood): the fittest configuration of the
+ * current generation, canonically relabelled by first occurrence (0, 1, 2,
+ * ...), with L_c (Eq. 8) re-scored in FP64 directly from the FP64 C (the
+ * final re-score, independent of the form that ranked it).
+ * labels: host or device, N int32 (optional); L: host or device, 1 FP64
+ * (optional); generation: host (optional). Waits for the handle's stream.
+ * The outputs are written in every case; the status then reports the device
+ * error word of the run: GPGA_ERR_TIMEOUT if a bounded device wait gave up
+ * since the last ga_init / ga_reset (GPGA_FORM_TENSOR). Errors: GPGA_ERR_ARG
+ * (NULL h), GPGA_ERR_CUDA.
  */
 GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation);
 
@@ -310,13 +351,17 @@ GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *
  * have the library allocate device memory while scoring (a host whose own
  * pool allocator already owns nearly all GPU memory, or a latency-critical
  * loop that forbids allocator calls). Its working memory is a fixed file-scope
- * __device__ array of about 8 MiB that every GPU loading the library holds
+ * __device__ array of about 4.3 MiB that every GPU loading the library holds
  * until the process exits; the call makes no cudaMalloc, cudaFree or other
- * allocating call. The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture. The caller passes inputs and outputs exactly as
- * for ga_score: labels (device, P x N int32 in [0, N), leading dimension
- * ld >= N), C (device, N x N FP64), L (device, P FP64, written).
+ * allocating call. Set-up: the first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) once, with that device current, and
+ * keeps it for the process; a cudaDeviceReset invalidates it, so do not call
+ * this entry point on a device after resetting that device in the same
+ * process. The call waits for its stream at the end, so no call of it can be
+ * captured into a CUDA graph. The caller passes inputs and
+ * outputs exactly as for ga_score: labels (device, P x N int32 in [0, N),
+ * leading dimension ld >= N), C (device, N x N FP64), L (device, P FP64,
+ * written).
  * Limits: 2 <= N <= 1024 (GPGA_ERR_ARG beyond), 1 <= P <= 2^24.
  * All calls share the one array and it keeps the previous call's contents
  * (the call clears what must start at zero): calls that overlap on the GPU,
@@ -327,7 +372,12 @@ GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *
 GPGA_API int ga_score_noalloc(const int32_t *labels, int P, int N, int ld, const double *C,
                               double *L, void *stream);
 
-/* ga_free -- release the handle and all its device memory (NULL is a no-op). */
+/*
+ * ga_free -- release handle h (from ga_init) with all its device memory, its
+ * graphs and events, and its stream if it created one; the end of the run of
+ * Algorithm 1 (no counterpart in the paper beyond that). Waits for the
+ * handle's stream first. NULL is a no-op. Always returns GPGA_OK.
+ */
 GPGA_API int ga_free(gpga_ga *h);
 
 /* ------------------------------------------------------------------------

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -23,6 +24,23 @@ int set_error(int code, const char *fmt, ...)
     vsnprintf(g_err, sizeof g_err, fmt, ap);
     va_end(ap);
     return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+static std::atomic<long long> g_wait_budget{1ll << 32};
+
+long long wait_budget() { return g_wait_budget.load(std::memory_order_relaxed); }
+
+int device_error_status(int err_word, const char *what)
+{
+    if (err_word & 4)
+        return set_error(GPGA_ERR_TIMEOUT,
+                         "%s: a bounded device wait gave up (the affected fitness values are NaN)",
+                         what);
+    if (err_word & 1)
+        return set_error(GPGA_ERR_ARG, "%s: a label lies outside [0, N) (its L is NaN)", what);
+    return GPGA_OK;
 }
 
 int cuda_error(cudaError_t e, const char *what, const char *file, int line)
@@ -391,6 +409,13 @@ extern "C" {
 
 GPGA_API const char *gpga_last_error(void) { return g_err; }
 
+GPGA_API int gpga_set_wait_budget(long long cycles)
+{
+    g_err[0] = 0;
+    g_wait_budget.store(cycles < 0 ? (1ll << 32) : cycles, std::memory_order_relaxed);
+    return GPGA_OK;
+}
+
 GPGA_API int gpga_default_params(gpga_params *p)
 {
     if (!p) return set_error(GPGA_ERR_ARG, "params is NULL");
@@ -527,8 +552,7 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
         if (e != cudaSuccess) rc = cuda_error(e, "ga_score sync", __FILE__, __LINE__);
     } while (0);
     cudaFreeAsync(ws, s);
-    if (rc == GPGA_OK && (herr & 1))
-        rc = set_error(GPGA_ERR_ARG, "ga_score: a label lies outside [0, N) (its L is NaN)");
+    if (rc == GPGA_OK) rc = device_error_status(herr, "ga_score");
     return rc;
 }
 
@@ -690,9 +714,12 @@ GPGA_API int ga_step(gpga_ga *h, int generations, int *done)
     }
     if (done) {
         DevState st;
+        int herr = 0;
         GPGA_CUDA(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+        GPGA_CUDA(cudaMemcpyAsync(&herr, h->err, sizeof herr, cudaMemcpyDeviceToHost, h->stream));
         GPGA_CUDA(cudaStreamSynchronize(h->stream));
         *done = st.done;
+        return device_error_status(herr, "ga_step");
     }
     return GPGA_OK;
 }
@@ -715,10 +742,12 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation)
                                                    : cudaMemcpyDeviceToHost,
                                   h->stream));
     DevState st;
+    int herr = 0;
     GPGA_CUDA(cudaMemcpyAsync(&st, h->st, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    GPGA_CUDA(cudaMemcpyAsync(&herr, h->err, sizeof herr, cudaMemcpyDeviceToHost, h->stream));
     GPGA_CUDA(cudaStreamSynchronize(h->stream));
     if (generation) *generation = st.gen;
-    return GPGA_OK;
+    return device_error_status(herr, "ga_best");
 }
 
 GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns,

@@ -15,6 +15,13 @@ namespace gpga {
 // ---------------------------------------------------------------------------
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// empty this thread's error message (every exported call starts with it)
+void clear_error();
+// cycles a bounded device wait may spend before it gives up (gpga_set_wait_budget)
+long long wait_budget();
+// the status of a run's device error word: bit 0 (value 1) a label outside
+// [0, N), bit 2 (value 4) a bounded wait that gave up
+int device_error_status(int err_word, const char *what);
 
 #define GPGA_CUDA(expr)                                                              \
     do {                                                                             \

@@ -18,21 +18,21 @@ namespace gpga {
 constexpr int NOALLOC_MAX_N = 1024;
 constexpr int NOALLOC_MAX_NP = (NOALLOC_MAX_N + 63) & ~63;
 
-// layout of the scratch: FP32 D, int32 fixed-point D, log tables, two flags
-constexpr size_t NA_D32 = 0;
-constexpr size_t NA_DFIX = NA_D32 + (size_t)NOALLOC_MAX_NP * NOALLOC_MAX_NP * sizeof(float);
+// layout of the scratch: int32 fixed-point D, log tables, two flags
+constexpr size_t NA_DFIX = 0;
 constexpr size_t NA_LOG = NA_DFIX + (size_t)NOALLOC_MAX_NP * NOALLOC_MAX_NP * sizeof(int32_t);
 constexpr size_t NA_FLAGS =
     NA_LOG + ((2 * LOG_TAB + (size_t)NOALLOC_MAX_N + 1) * sizeof(double) + 255) / 256 * 256;
 constexpr size_t NA_BYTES = NA_FLAGS + 256;
 
-// Every device that loads the library holds this array (about 8 MiB) until the
-// process exits. In host code the name is only a host-side stand-in; the device
-// address comes from cudaGetSymbolAddress below.
+// Every device that loads the library holds this array (about 4.3 MiB) until
+// the process exits. In host code the name is only a host-side stand-in; the
+// device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// device address of g_noalloc_scratch per device ordinal, looked up once with
-// that device current
+// Set-up: the device address of g_noalloc_scratch per device ordinal, looked
+// up once with that device current and kept for the process (a
+// cudaDeviceReset of that device invalidates it).
 static unsigned char *noalloc_base(int dev, int *rc)
 {
     static std::mutex mu;
@@ -51,8 +51,6 @@ static unsigned char *noalloc_base(int dev, int *rc)
     return base[dev];
 }
 
-int prepare_device();
-
 } // namespace gpga
 
 using namespace gpga;
@@ -60,6 +58,7 @@ using namespace gpga;
 extern "C" GPGA_API int ga_score_noalloc(const int32_t *labels, int P, int N, int ld,
                                          const double *C, double *L, void *stream)
 {
+    clear_error();
     if (!labels || !C || !L) return set_error(GPGA_ERR_ARG, "ga_score_noalloc: NULL pointer");
     if (N < 2 || N > NOALLOC_MAX_N || P < 1 || P > (1 << 24) || ld < N)
         return set_error(GPGA_ERR_ARG,
@@ -74,13 +73,15 @@ extern "C" GPGA_API int ga_score_noalloc(const int32_t *labels, int P, int N, in
     if (!base) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int Np = pad_n(N);
-    float *D32 = reinterpret_cast<float *>(base + NA_D32);
     int32_t *Dfix = reinterpret_cast<int32_t *>(base + NA_DFIX);
     double *logtab = reinterpret_cast<double *>(base + NA_LOG);
     int *err = reinterpret_cast<int *>(base + NA_FLAGS); // [0] label error, [1] diagonal flag
     // the scratch keeps the previous call's contents: clear the flags
     GPGA_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
-    rc = launch_prep_d(C, N, N, Np, D32, nullptr, nullptr, Dfix, logtab, err + 1, s);
+    // only the fixed-point D (with its diagonal flag) and the log tables: the
+    // gather form reads nothing else
+    rc = launch_fleet_prep(C, N, nullptr, N, Np, nullptr, Dfix, err + 1, s);
+    if (!rc) rc = launch_logtab(logtab, N, s);
     if (rc) return rc;
     const int32_t *lab2[2] = {labels, labels};
     rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, Dfix, err + 1, logtab, L, err,

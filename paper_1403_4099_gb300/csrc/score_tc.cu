@@ -23,8 +23,10 @@
 //                       accumulate) and commits to the stage's mbarrier
 //   tc_assemble_kernel  one warp per individual: Eq. 8 over its columns in
 //                       the fixed-point one-log form
-// Every wait is bounded (about 2 s of clock64); a timeout sets bit 2 of the
-// error word, stops issuing work, and the CTA still frees its TMEM.
+// Every pipeline wait is bounded by the wait budget (gpga_set_wait_budget;
+// default 2^32 cycles, about 2 s); a timeout sets bit 2 of the error word,
+// stops issuing work, waits with the full default bound for the MMAs already
+// committed, and the CTA still frees its TMEM.
 #include "score_tc.cuh"
 
 namespace gpga {
@@ -100,13 +102,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait (about 2 s at the SM clock): false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity)
+// bounded wait: false once `budget` SM cycles have passed since the
+// wait began (the budget is checked before each try, so budget 0 gives up at
+// once); the default bound, 2^32 cycles, is about 2 s at the SM clock
+constexpr long long WAIT_BOUND = 1ll << 32;
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity,
+                                          long long budget = WAIT_BOUND)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(a, parity))
-        if (clock64() - t0 > (1ll << 32)) return false;
-    return true;
+    for (;;) {
+        if (clock64() - t0 >= budget) return false;
+        if (mbar_try_wait(a, parity)) return true;
+    }
 }
 
 // 128-byte-swizzled, K-major shared-memory operand descriptor (rows of 128
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_mma_kernel(TcWork w, const __nv_bfloat16 *__restrict__ Dhi,
                   const __nv_bfloat16 *__restrict__ Dlo, int Np, int NT, int fix_bits,
-                  const DevState *__restrict__ st)
+                  const DevState *__restrict__ st, long long budget)
 {
     if (st && st->done) return;
     extern __shared__ unsigned char sm_raw[];
@@ -354,7 +361,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (kb + 1 < KB) {
                 // the other stage is free once the MMAs of the previous block are done
                 if (it >= 1) {
-                    if (tid == 0 && !mbar_wait(smem_u32(&mbar[(it - 1) & 1]), ((it - 1) >> 1) & 1))
+                    if (tid == 0 &&
+                        !mbar_wait(smem_u32(&mbar[(it - 1) & 1]), ((it - 1) >> 1) & 1, budget))
                         s_abort = 1;
                     __syncthreads();
                     if (s_abort) {
@@ -368,7 +376,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (s_abort) break;
         // epilogue: wait for the last K-block's MMAs (all earlier ones are done too)
         const int last = it - 1;
-        if (tid == 0 && !mbar_wait(smem_u32(&mbar[last & 1]), (last >> 1) & 1)) s_abort = 1;
+        if (tid == 0 && !mbar_wait(smem_u32(&mbar[last & 1]), (last >> 1) & 1, budget))
+            s_abort = 1;
         __syncthreads();
         if (s_abort) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -406,8 +415,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
     }
-    // on a timeout: flag it, then wait (bounded) for the commits still in
-    // flight before freeing TMEM
+    // on a timeout: flag it, then wait (with the full default bound, whatever
+    // the budget) for the commits still in flight before freeing TMEM
     __syncthreads();
     if (s_abort && tid == 0) {
         atomicOr(w.err, 4);
@@ -482,7 +491,8 @@ int tc_contract(TcWork *w, const __nv_bfloat16 *Dhi, const __nv_bfloat16 *Dlo, i
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    tc_mma_kernel<<<sms, TC_THREADS, TC_SMEM, s>>>(*w, Dhi, Dlo, Np, NT, fix_bits_for(N), st);
+    tc_mma_kernel<<<sms, TC_THREADS, TC_SMEM, s>>>(*w, Dhi, Dlo, Np, NT, fix_bits_for(N), st,
+                                                    wait_budget());
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }

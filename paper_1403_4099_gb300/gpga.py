@@ -28,7 +28,8 @@ EXPORTS = ["gpga_default_params", "gpga_last_error", "cluster_corr", "ga_score",
            "ga_batch_init", "ga_batch_step", "ga_batch_status", "ga_batch_best",
            "ga_batch_tuning", "ga_batch_free", "serve_create", "serve_submit", "serve_tick",
            "serve_result", "serve_stats", "serve_free", "cluster_mst", "ga_island_init",
-           "ga_batch_population", "cluster_corr_ewma", "corr_remove_market", "corr_clean_rmt"]
+           "ga_batch_population", "cluster_corr_ewma", "corr_remove_market", "corr_clean_rmt",
+           "gpga_set_wait_budget"]
 
 
 class GpgaError(RuntimeError):
@@ -79,6 +80,7 @@ def lib() -> ct.CDLL:
         sigs = {
             "gpga_default_params": (i32, [ct.POINTER(Params)]),
             "gpga_last_error": (ct.c_char_p, []),
+            "gpga_set_wait_budget": (i32, [ct.c_longlong]),
             "cluster_corr": (i32, [vp, i32, i32, i32, vp, vp]),
             "ga_score": (i32, [vp, i32, i32, i32, vp, vp, i32, vp]),
             "ga_evolve": (i32, [vp, vp, i32, ct.POINTER(Params), ct.c_uint64, i32, vp, vp, vp, vp]),
@@ -146,6 +148,12 @@ def _dev(t, dtype_name: str):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return ct.c_void_p(t.data_ptr())
+
+
+def set_wait_budget(cycles: int):
+    """Cycles a bounded device wait may spend before it gives up (< 0: the
+    default, 2^32). Process-wide; for kernels launched after the call."""
+    _check(lib().gpga_set_wait_budget(int(cycles)))
 
 
 def default_params(**kw) -> Params:

@@ -211,3 +211,32 @@ def test_serving_admission_by_memory(gpga):
     with pytest.raises(gpga.GpgaError):
         srv.result(0)  # already collected
     srv.close()
+
+
+@pytest.mark.parametrize("Ns", [[160, 23], [23, 160, 64]])
+def test_batch_generation_by_generation_against_oracle(gpga, orc, Ns):
+    """Each run of a fleet, generation by generation, against the oracle
+    directly (not only against the same run alone): the next population is
+    the oracle's operators applied to the run's own population and fitness
+    (bit-exact), and every L is within 1e-4 + 1e-6|L| of the oracle's Eq. 8."""
+    from gpu_util import assert_L_close
+    Cs = _windows(gpga, Ns, rep=90)
+    Ch = [C.cpu().numpy() for C in Cs]
+    seeds = [31 + 5 * k for k in range(len(Ns))]
+    prm = _params(gpga, P=192, max_gens=30, tol=-1.0)
+    b = gpga.Batch(Cs, prm, seeds)
+    ops = [orc.params(prm.P, n, elite=prm.elite, max_gens=prm.max_gens,
+                      stall_gens=prm.stall_gens, tol=prm.tol, pc=prm.pc, pkb=prm.pkb, pm=prm.pm,
+                      scaling=prm.scaling) for n in Ns]
+    cur = [b.population(k) for k in range(len(Ns))]
+    for gen in range(6):
+        refs = []
+        for k in range(len(Ns)):
+            pop, L = cur[k]
+            assert_L_close(L, orc.loglik_batch(pop, Ch[k]), f"run {k} gen {gen}")
+            refs.append(orc.ga_evolve(pop, L, ops[k], seeds[k], gen)[0])
+        b.step(1)
+        cur = [b.population(k) for k in range(len(Ns))]
+        for k in range(len(Ns)):
+            assert np.array_equal(cur[k][0], refs[k]), f"run {k} (N={Ns[k]}) generation {gen + 1}"
+    b.close()

@@ -177,3 +177,51 @@ def test_bad_params_rejected(g, orc):
         with pytest.raises(g.GpgaError) as e:
             g.GA(dev(C), gp, seed=1)
         assert e.value.code == g.ERR_ARG
+
+
+@pytest.fixture(scope="module")
+def n500_C(orc):
+    p = synth.n500()
+    return p, orc.pearson(p.R)
+
+
+@pytest.mark.parametrize("init", ["uniform", "threshold"])
+def test_headline_path_generation_by_generation_n500(g, orc, n500_C, init):
+    """The path the benchmark times, at its own size: gather form, 16-bit
+    labels, the fused generation kernel with the SUS bracket table of the rank
+    prefix, N=500, P=4096, E=10, P_m=0.01/gene. Each device generation equals
+    the oracle's operators applied to the device's own population and fitness
+    (bit-exact), and every device L is within 1e-4 + 1e-6|L| of the oracle's
+    Eq. 8. The threshold start has clusters of well over 8 members, so the
+    warp-wide big-cluster pair sums are exercised as well as the per-lane ones.
+    Then the 8-generation graph the benchmark launches is checked against 8
+    single-generation launches of a twin run."""
+    p, C = n500_C
+    kw = dict(init=g.INIT_THRESHOLD, tau_lo=0.05, tau_hi=0.6) if init == "threshold" else {}
+    gp = _gparams(g, 4096, E=10, max_gens=60, tol=-1.0, pm=0.01, form=g.FORM_GATHER, **kw)
+    seed = 14034099
+    ga = g.GA(dev(C), gp, seed=seed)
+    op = _oparams(orc, gp, 500)
+    pop, L = ga.population()
+    biggest = 0
+    for gen in range(5):
+        assert_L_close(L, orc.loglik_batch(pop, C), f"{init} gen {gen}")
+        biggest = max(biggest, max(np.bincount(row).max() for row in pop[:64]))
+        ref_next, _, _ = orc.ga_evolve(pop, L, op, seed, gen)
+        ga.step(1)
+        pop, L = ga.population()
+        assert np.array_equal(pop, ref_next), f"{init}: generation {gen + 1}"
+    assert_L_close(L, orc.loglik_batch(pop, C), f"{init} gen 5")
+    if init == "threshold":
+        assert biggest > 8
+    # the 8-generation graph against single generations, from the same start
+    twin = g.GA(dev(C), gp, seed=seed)
+    ga.step(8)
+    for _ in range(5 + 8):
+        twin.step(1)
+    pa, La = ga.population()
+    pb, Lb = twin.population()
+    assert np.array_equal(pa, pb) and np.array_equal(La, Lb)
+    assert_L_close(La, orc.loglik_batch(pa, C), f"{init} gen 13")
+    ga.close()
+    twin.close()
