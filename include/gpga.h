@@ -243,8 +243,9 @@ GPGA_API int ga_best(gpga_ga *h, int32_t *labels, double *L, int *generation);
  * the population (the work Eq. 6 needs; gather, plain and tensor forms) and
  * the number of non-singleton clusters summed over the population (tensor
  * form: the columns of the contraction), for generations 0..count-1,
- * count <= cap. Host pointers (each optional). t_ns[0] is taken at the start
- * of ga_init / ga_reset, t_ns[1 + g] at the end of generation g (so t_ns holds
+ * count <= cap. Host pointers (each optional; t_ns needs room for cap + 1
+ * values, the others for cap). t_ns[0] is taken at the start of ga_init /
+ * ga_reset, t_ns[1 + g] at the end of generation g (so t_ns receives
  * count + 1 values). Waits for the stream.
  */
 GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_t *t_ns,

@@ -144,6 +144,7 @@ struct gpga_ga {
     int *diag = nullptr;
     int32_t *canon = nullptr;
     double *Lbest = nullptr;
+    ScoreTab tab{}; // gather form: per-individual score tables (delta scoring)
     TcWork tc{};
     cudaGraphExec_t g1 = nullptr, gU = nullptr;
     int U = 8;
@@ -203,6 +204,14 @@ size_t carve(gpga_ga *h, char *base)
     h->canon = c.take<int32_t>(N);
     h->Lbest = c.take<double>(1);
     if (h->prm.form == GPGA_FORM_TENSOR) tc_carve(&h->tc, h->N, h->Np, h->P, &c.off, c.base);
+    if (h->prm.form == GPGA_FORM_GATHER) {
+        h->tab.ldt = (int)Np;
+        for (int b = 0; b < 2; ++b) {
+            h->tab.d[b] = c.take<long long>(P * Np);
+            h->tab.lf[b] = c.take<long long>(P);
+            h->tab.np[b] = c.take<long long>(P);
+        }
+    }
     return c.off + 256;
 }
 
@@ -216,7 +225,7 @@ int enqueue_score(gpga_ga *h, int sel_off, cudaEvent_t *evs = nullptr)
     if (h->prm.form == GPGA_FORM_GATHER) {
         rc = launch_gather_score<uint16_t>(lab2, h->Np, sel_off, h->P, h->N, h->Np, h->Dfix,
                                            h->diag, h->logtab, h->L, h->err, h->st, h->pairs,
-                                           h->stream);
+                                           h->tab, h->stream);
         if (!rc) rc = mark(h, evs, 2);
         if (!rc) rc = mark(h, evs, 3);
         return rc;
@@ -312,9 +321,9 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs, bool after_kernel)
         // selection, crossover, mutation, replacement and scoring in one kernel
         const bool pdl_gen = after_kernel && !(evs && marked(h, 0));
         if (!rc)
-            rc = launch_gather_generation<uint16_t>(pop2, next2, e, h->perm, prefix, h->Np, h->Dfix,
-                                                    h->diag, h->logtab, h->L, h->st, h->pairs,
-                                                    pdl_gen, h->stream);
+            rc = launch_gather_generation(pop2, next2, e, h->perm, prefix, h->Np, h->Dfix,
+                                          h->diag, h->logtab, h->L, h->st, h->pairs, h->tab,
+                                          pdl_gen, h->stream);
         if (!rc) rc = mark(h, evs, 1);
         if (!rc) rc = mark(h, evs, 2);
         if (!rc) rc = mark(h, evs, 3);
@@ -535,7 +544,7 @@ GPGA_API int ga_score(const int32_t *labels, int P, int N, int ld, const double 
         const int32_t *lab2[2] = {labels, labels};
         if (form == GPGA_FORM_GATHER) {
             rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, Dfix, err + 1, logtab, L, err,
-                                              nullptr, nullptr, s);
+                                              nullptr, nullptr, ScoreTab{}, s);
         } else if (form == GPGA_FORM_TENSOR) {
             rc = tc_contract<int32_t>(&tc, Dhi, Dlo, Np, lab2, ld, 0, P, N, err, nullptr, nullptr,
                                       nullptr, s);
@@ -779,7 +788,7 @@ GPGA_API int ga_history(gpga_ga *h, double *best_L, int32_t *best_labels, int64_
     if (pairs) GPGA_CUDA(cudaMemcpy(pairs, h->pairs, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (clusters)
         GPGA_CUDA(cudaMemcpy(clusters, h->clusters, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-    if (t_ns) GPGA_CUDA(cudaMemcpy(t_ns, h->ts, (size_t)(n + 1 > cap ? cap : n + 1) * sizeof(int64_t),
+    if (t_ns) GPGA_CUDA(cudaMemcpy(t_ns, h->ts, (size_t)(n + 1) * sizeof(int64_t),
                                    cudaMemcpyDeviceToHost));
     return GPGA_OK;
 }

@@ -113,6 +113,12 @@ static size_t run_bytes(const Fleet *f, int N, char *base, RunMem *m)
     t.d.ticket = c.take<unsigned>(TICKETS);
     t.d.work_prefix = c.take<uint64_t>(P);
     t.d.hist = c.take<double>(G);
+    t.d.tab.ldt = (int)Np;
+    for (int b = 0; b < 2; ++b) {
+        t.d.tab.d[b] = c.take<long long>(P * Np);
+        t.d.tab.lf[b] = c.take<long long>(P);
+        t.d.tab.np[b] = c.take<long long>(P);
+    }
     t.canon = c.take<int32_t>(N);
     t.Lbest = c.take<double>(1);
     t.err = c.take<int>(1);
@@ -299,7 +305,7 @@ static int fleet_start(Fleet *f, int slot, const double *C, int ldc, const int32
     GPGA_CUDA(cudaMemsetAsync(m.d.pop1, 0, (size_t)P * Np * sizeof(uint16_t), st));
     const uint16_t *lab2[2] = {m.d.pop0, m.d.pop1};
     rc = launch_gather_score<uint16_t>(lab2, Np, 0, P, N, Np, m.d.Dfix, m.diag, f->logtab, m.d.L,
-                                       m.err, m.d.st, nullptr, st);
+                                       m.err, m.d.st, nullptr, m.d.tab, st);
     if (rc) return rc;
     return launch_select<uint16_t>(m.d.L, fleet_select_cfg(f, N, 0), m.d.rank, m.d.perm,
                                    m.d.work_prefix, m.d.ticket, m.d.st, m.d.hist, lab2, nullptr,
@@ -430,7 +436,7 @@ static int fleet_tune(Fleet *f)
         const uint16_t *lab2[2] = {s.m.d.pop0, s.m.d.pop1};
         rc = launch_gather_score<uint16_t>(lab2, s.m.d.Np, 0, f->P, s.N, s.m.d.Np, s.m.d.Dfix,
                                            s.m.diag, f->logtab, s.m.d.L, s.m.err, s.m.d.st,
-                                           nullptr, f->stream);
+                                           nullptr, s.m.d.tab, f->stream);
     }
     return rc;
 }

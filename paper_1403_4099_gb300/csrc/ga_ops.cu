@@ -457,7 +457,20 @@ __global__ void __launch_bounds__(256)
             const int r = idx / Np, j = idx - r * Np;
             dst[(size_t)(P - m + r) * Np + j] = src[(size_t)r * Np + j];
         }
-        for (int r = threadIdx.x; r < m; r += blockDim.x) b.L[P - m + r] = a.L[r];
+        // the migrants' score tables travel with them
+        const int nb = (g + 1) & 1;
+        const long long *tsrc = a.tab.d[nb];
+        long long *tdst = b.tab.d[nb];
+        const int ldt = a.tab.ldt;
+        for (int idx = threadIdx.x; idx < m * ldt; idx += blockDim.x) {
+            const int r = idx / ldt, j = idx - r * ldt;
+            tdst[(size_t)(P - m + r) * ldt + j] = tsrc[(size_t)r * ldt + j];
+        }
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            b.L[P - m + r] = a.L[r];
+            b.tab.lf[nb][P - m + r] = a.tab.lf[nb][r];
+            b.tab.np[nb][P - m + r] = a.tab.np[nb][r];
+        }
     }
 }
 
@@ -470,11 +483,132 @@ int launch_fleet_migrate(const FleetRun *runs, const FleetHdr *hdr, int P, int e
     return GPGA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// "Isolate fittest individuals" by counting, for rank scaling (whose weights
+// by rank are fixed, so nothing after the ranks needs a second pass): CTA c
+// owns the 32 keys i = 32 c + lane; every CTA holds all P keys in shared
+// memory, and warp w counts, for its lane's key, the fitter keys of slice w
+// of the population: rank_i = #{j < i : k_j >= k_i} + #{j > i : k_j > k_i}
+// (key descending, index ascending; NaN as -inf). The slices' counts add up
+// to the exact rank, so perm[rank_i] = i is written at once: no atomics, no
+// ticket, no CTA waits for another. The CTA that holds rank 0 does the
+// generation's bookkeeping (best, the mean from the fixed-point sum of all
+// fitness values, which every CTA forms from its shared copy, the record of
+// the best configuration and the device clock, the termination test).
+// Stateful use: g = st->gen + gen_off (read only by the CTA that holds rank 0,
+// which is also the only writer of the state).
+// ---------------------------------------------------------------------------
+constexpr int SEL_WARPS = 8;
+
+template <typename LabT>
+__global__ void __launch_bounds__(32 * SEL_WARPS)
+    select_count_kernel(const double *__restrict__ L, SelectCfg cfg, int32_t *__restrict__ perm,
+                        DevState *st, double *__restrict__ hist, const LabT *pop0,
+                        const LabT *pop1, LabT *__restrict__ ring,
+                        unsigned long long *__restrict__ ts)
+{
+    extern __shared__ unsigned long long s_key[]; // P keys
+    __shared__ int s_cnt[SEL_WARPS][32];
+    __shared__ long long s_sum[SEL_WARPS];
+    __shared__ int s_best;
+    if (st && st->done) return; // a run that terminated selects nothing
+    const int P = cfg.P;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    long long fsum = 0;
+    for (int j = tid; j < P; j += blockDim.x) {
+        const double v = L[j];
+        s_key[j] = order_key(v);
+        if (st && isfinite(v)) fsum += __double2ll_rn(v * 1073741824.0);
+    }
+    if (st) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+        if (lane == 0) s_sum[warp] = fsum;
+    }
+    if (tid == 0) s_best = -1;
+    __syncthreads();
+    const int b0 = blockIdx.x * 32, i = b0 + lane;
+    const unsigned long long ki = i < P ? s_key[i] : 0ull;
+    const int per = (P + SEL_WARPS - 1) / SEL_WARPS;
+    const int j0 = min(P, warp * per), j1 = min(P, j0 + per);
+    int c = 0;
+    {
+        // j below the CTA's block: fitter iff k_j >= k_i (lower index wins ties)
+        const int e = min(j1, b0);
+        int j = j0;
+#pragma unroll 8
+        for (; j < e; ++j) c += s_key[j] >= ki ? 1 : 0;
+        // inside the block: per lane
+        const int e2 = min(j1, b0 + 32);
+        for (j = max(j0, b0); j < e2; ++j) {
+            const unsigned long long kj = s_key[j];
+            c += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
+        }
+        // above the block: fitter iff k_j > k_i
+#pragma unroll 8
+        for (j = max(j0, b0 + 32); j < j1; ++j) c += s_key[j] > ki ? 1 : 0;
+    }
+    s_cnt[warp][lane] = c;
+    __syncthreads();
+    if (warp == 0) {
+        int r = 0;
+#pragma unroll
+        for (int w = 0; w < SEL_WARPS; ++w) r += s_cnt[w][lane];
+        if (i < P) {
+            perm[r] = i;
+            if (r == 0) s_best = i;
+        }
+    }
+    __syncthreads();
+    // the next generation kernel (a programmatic dependent) may be scheduled
+    // now; it waits for this grid to complete before it reads anything written here
+    griddep_launch();
+    const int bidx = s_best;
+    if (!st || bidx < 0) return;
+    const int g = st->gen + cfg.gen_off;
+    if (cfg.record && ring) {
+        const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
+        for (int j = tid; j < cfg.N; j += blockDim.x) ring[(size_t)g * cfg.N + j] = src[j];
+    }
+    if (tid == 0) {
+        long long lsum = 0;
+#pragma unroll
+        for (int w = 0; w < SEL_WARPS; ++w) lsum += s_sum[w];
+        double best = L[bidx];
+        if (isnan(best)) best = -INFINITY;
+        st->gen = g;
+        st->best = best;
+        st->best_idx = bidx;
+        hist[g] = best;
+        int done = g >= cfg.max_gens;
+        if (!done && cfg.tol >= 0.0 && cfg.stall_gens > 0 && g >= cfg.stall_gens)
+            done = (best - hist[g - cfg.stall_gens]) <= cfg.tol * fmax(1.0, fabs(best));
+        if (cfg.record && ts) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            ts[1 + g] = t;
+        }
+        st->done = done;
+        st->mean = (double)lsum * 9.313225746154785e-10 / (double)P;
+    }
+}
+
+// selection by counting for rank scaling (one launch, no ticket), else the
+// chunked sort + search with the ticketed last CTA (proportional scaling needs
+// the weights in rank order after all ranks are known)
 template <typename LabT>
 int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *perm,
                   uint64_t *work_prefix, unsigned *ticket, DevState *st, double *hist,
                   const LabT *const *pop2, LabT *ring, unsigned long long *ts, cudaStream_t s)
 {
+    if (cfg.scaling == GPGA_SCALING_RANK) {
+        const int grid = (cfg.P + 31) / 32;
+        const size_t smem = (size_t)cfg.P * sizeof(unsigned long long);
+        select_count_kernel<LabT><<<grid, 32 * SEL_WARPS, smem, s>>>(
+            L, cfg, perm, st, hist, pop2 ? pop2[0] : nullptr, pop2 ? pop2[1] : nullptr, ring, ts);
+        GPGA_LAUNCH_CHECK();
+        return GPGA_OK;
+    }
     const int nc = (cfg.P + RANK_CHUNK - 1) / RANK_CHUNK;
     select_kernel<LabT><<<dim3(nc, nc), RANK_CHUNK, 0, s>>>(
         L, cfg, rank, perm, work_prefix, ticket, st, hist, pop2 ? pop2[0] : nullptr,
@@ -563,7 +697,9 @@ template int launch_evolve<int32_t>(const int32_t *const *, int32_t *const *, co
 
 int prepare_ga_kernels(int maxsmem)
 {
-    (void)maxsmem; // select_kernel uses static shared memory only
+    // select_count_kernel holds all P keys (up to 128 KB at GPGA_MAX_P)
+    if (int rc = raise_smem(select_count_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(select_count_kernel<int32_t>, maxsmem)) return rc;
     return GPGA_OK;
 }
 

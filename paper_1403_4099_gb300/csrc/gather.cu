@@ -8,33 +8,74 @@
 // sweep. D is read as int32 fixed point (2^-30), so every cluster sum is an
 // exact integer sum: independent of the order of the members, which are
 // therefore scattered with plain atomics, and deterministic. One warp per
-// individual; labels, counts and members live in that warp's 8 N-byte slice of
-// shared memory. A cluster of at most 8 members is summed by one lane, a larger one by
-// the whole warp. Eq. 8 then follows in the one-log product form.
+// individual; labels, counts and members live in that warp's slice of shared
+// memory. A cluster of at most 8 members is summed by one lane, a larger one
+// by the whole warp.
+//
+// Eq. 8 is a sum of one term per cluster with n_s >= 2,
+//   L = sum_s T(n_s, d_s),  T(n, d) = K(n) - 1/2 log(c d^(n-1)),  c = n^2 - d,
+// each term evaluated in integer fixed point (Q40) from the exact (n_s, d_s),
+// so L is an exact integer sum of terms that depend on their own cluster only.
+//
+// Delta scoring of children (stateful runs): each individual keeps its table
+// of d_s per label (valid where n_s >= 2), its L in Q40 and its pair count.
+// A child differs from its first parent a in a few genes X (a knowledge-based
+// merge moves one of b's clusters, mutation redraws about N P_m genes). With
+// U_t the members of cluster t that did not move, Out_t the genes of X that
+// left t and In_t those that joined it,
+//   d'_t = d_t + 2 [D(U_t, In_t) - D(U_t, Out_t)] + D(In_t, In_t) - D(Out_t, Out_t),
+// so only the clusters X touches are updated, with sum_t |U_t| (|In_t| +
+// |Out_t|) + |X|^2 gathers, and L' = L + sum_t [T(n'_t, d'_t) - T(n_t, d_t)].
+// All sums are exact integers and T depends on (n, d) alone, so the result is
+// bit-identical to scoring the child from scratch. Children with more than
+// XMAX changed genes (one-point crossovers, mostly) are scored from scratch.
 #include <math.h>
 
 #include "gpga_internal.cuh"
 
 namespace gpga {
 
-// per-warp shared-memory slice for Np padded genes (8 Np bytes), in order:
+// ---------------------------------------------------------------------------
+// Per-warp shared-memory slice for Np padded genes: 8 Np bytes, in order
 //   list  (2 Np bytes) int32 list of the non-singleton clusters, label order,
 //         (start << 16 | n), at most N/2 entries;
 //   cnt   (2 Np bytes) label counts, then cluster starts, then cluster ends;
 //   lab   (2 Np bytes) labels;
-//   mem   (2 Np bytes) gene indices grouped by label.
+//   mem   (2 Np bytes) gene indices grouped by label;
+// then the delta region (delta_bytes(Np)): the changed genes X of a child and
+// the affected clusters (delta path), or the labels of the listed clusters
+// (full path).
 // Counts and starts are 16-bit (N < 65536), two per 32-bit word (label 2w in
 // the low half of word w), updated with 32-bit shared-memory atomics: a half
 // never carries into its neighbour because no count or start exceeds N. After
 // the scatter, cnt and lab (contiguous) are dead and hold the pair sums.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int delta_xmax(int Np) { return Np >= 128 ? 64 : Np / 2; }
+__host__ __device__ inline int delta_amax(int Np) { return 2 * delta_xmax(Np); }
+__host__ __device__ inline size_t delta_bytes(int Np)
+{
+    const size_t b = 6 * (size_t)delta_xmax(Np) + 32 * (size_t)delta_amax(Np);
+    const size_t need = b > (size_t)Np ? b : (size_t)Np;
+    return (need + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 8 + delta_bytes(Np); }
+
+constexpr uint16_t NO_SLOT = 0xffffu;
+
 struct GatherSlice {
     int *list;
     uint32_t *cnt;
     uint16_t *lab;
     uint16_t *mem;
+    // delta region
+    unsigned long long *in_mask, *out_mask; // per affected cluster: bits over X
+    long long *dacc;                        // per affected cluster: change of d
+    unsigned *nnew;                         // per affected cluster: members in the child
+    uint16_t *slab, *um;                    // per affected cluster: label, a member left in place
+    uint16_t *xs, *xa, *xc;                 // per changed gene: index, label in a, label in the child
+    uint16_t *lablist;                      // full path: label of listed cluster c
+    int xmax, amax;
 };
-
-__host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 8; }
 
 __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
 {
@@ -43,6 +84,20 @@ __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
     s.cnt = reinterpret_cast<uint32_t *>(base + (size_t)2 * Np);
     s.lab = reinterpret_cast<uint16_t *>(base + (size_t)4 * Np);
     s.mem = reinterpret_cast<uint16_t *>(base + (size_t)6 * Np);
+    unsigned char *d = base + (size_t)8 * Np;
+    s.xmax = delta_xmax(Np);
+    s.amax = delta_amax(Np);
+    const int A = s.amax, X = s.xmax;
+    s.in_mask = reinterpret_cast<unsigned long long *>(d);
+    s.out_mask = s.in_mask + A;
+    s.dacc = reinterpret_cast<long long *>(s.out_mask + A);
+    s.nnew = reinterpret_cast<unsigned *>(s.dacc + A);
+    s.slab = reinterpret_cast<uint16_t *>(s.nnew + A);
+    s.um = s.slab + A;
+    s.xs = s.um + A;
+    s.xa = s.xs + X;
+    s.xc = s.xa + X;
+    s.lablist = reinterpret_cast<uint16_t *>(d);
     return s;
 }
 
@@ -78,15 +133,36 @@ __device__ __forceinline__ long long small_cluster_sum(const uint16_t *m, int n,
     return s;
 }
 
-// Score one configuration held in sl.lab[0..N) (labels < N, N < 65536).
-// Returns L on all lanes. Dfix: Np x Np int32, D = 1 - C in fixed point
-// 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. pairs_out (optional):
-// += sum_s n_s (n_s - 1) / 2.
-__device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
-                                    const int32_t *__restrict__ Dfix, int diag,
-                                    const long long *__restrict__ ltab,
-                                    const long long *__restrict__ kfix, int lane,
-                                    unsigned long long *pairs_out)
+// T(n, d) = K(n) - 1/2 log(c d^(n-1)) of one cluster (n >= 2) in fixed point
+// 2^-40, from d as the exact fixed-point integer df = d 2^DFIX_BITS: the
+// product c d^(n-1) as a 63-bit mantissa and a binary exponent (logprod_mul,
+// with Eq. 8's domain floors), then e ln 2 + log(m 2^-62) with the table log.
+__device__ __forceinline__ long long cluster_term_q40(int n, long long df,
+                                                      const long long *__restrict__ ltab,
+                                                      const long long *__restrict__ kfix)
+{
+    LogProd a;
+    logprod_mul(a, n, df, DFIX_BITS);
+    const long long ph = __mul64hi(a.e, LN2_Q62);
+    const unsigned long long pl = (unsigned long long)a.e * (unsigned long long)LN2_Q62;
+    const long long elog = (long long)(((unsigned long long)ph << 42) | (pl >> 22));
+    const long long tot = elog + (log_q62(a.m, ltab) >> 22);
+    return (__ldg(kfix + n) >> (KFIX_BITS - 40)) - (tot >> 1);
+}
+
+// L from its Q40 fixed point
+__device__ __forceinline__ double lfix_to_double(long long lf) { return dbl_scaled(lf, 40); }
+
+// Score one configuration held in sl.lab[0..N) (labels < N, N < 65536) from
+// scratch. Returns L in Q40 on all lanes and the pair count sum_s n_s (n_s -
+// 1) / 2 in *npairs_out (all lanes). Dfix: Np x Np int32, D = 1 - C in fixed
+// point 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. trow (optional): the
+// individual's row of the d table, written where n_s >= 2.
+__device__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
+                                     const int32_t *__restrict__ Dfix, int diag,
+                                     const long long *__restrict__ ltab,
+                                     const long long *__restrict__ kfix, int lane,
+                                     long long *__restrict__ trow, long long *npairs_out)
 {
     const unsigned lt = (1u << lane) - 1u;
     const int nwd = (N + 1) >> 1; // words holding the labels 0..N-1
@@ -99,8 +175,9 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
     }
     __syncwarp();
     // cluster starts (exclusive scan of the counts, written over the counts)
-    // and the list of non-singleton clusters, in one pass: lane l takes the 4
-    // consecutive count words 4 l .. 4 l + 3 of each 128-word chunk
+    // and the list of non-singleton clusters with their labels, in one pass:
+    // lane l takes the 4 consecutive count words 4 l .. 4 l + 3 of each
+    // 128-word chunk
     int nlist = 0;
     {
         int carry = 0;
@@ -131,9 +208,15 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
                 if (w0 + q < nwd) {
                     const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
                     sl.cnt[w0 + q] = (uint32_t)run | ((uint32_t)(run + x0) << 16);
-                    if (x0 >= 2) sl.list[li++] = (run << 16) | x0;
+                    if (x0 >= 2) {
+                        sl.lablist[li] = (uint16_t)(2 * (w0 + q));
+                        sl.list[li++] = (run << 16) | x0;
+                    }
                     run += x0;
-                    if (x1 >= 2) sl.list[li++] = (run << 16) | x1;
+                    if (x1 >= 2) {
+                        sl.lablist[li] = (uint16_t)(2 * (w0 + q) + 1);
+                        sl.list[li++] = (run << 16) | x1;
+                    }
                     run += x1;
                 }
             }
@@ -159,16 +242,14 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
     }
     __syncwarp();
     const int *list = sl.list;
-    // Pair sums first, then the terms: the sums of the clusters hold no
-    // dependency on one another, so a lane's loads of successive clusters
-    // overlap instead of waiting behind each cluster's log-product step.
-    // csum (int64 per listed cluster) fills the dead count and label space
-    // (4 Np contiguous bytes) from the front, the list of big clusters (n > 8)
-    // from the back: 8 nlist + 4 nbig <= 4 N bytes.
+    // Pair sums of every listed cluster first, then the terms: the sums hold
+    // no dependency on one another, so a lane's loads of successive clusters
+    // overlap. csum (int64 per listed cluster) fills the dead count and label
+    // space (4 Np contiguous bytes) from the front, the list of big clusters
+    // (n > 8) from the back: 8 nlist + 4 nbig <= 4 N bytes.
     long long *csum = reinterpret_cast<long long *>(sl.cnt);
     int *big_end = reinterpret_cast<int *>(sl.lab + Np);
     int nbig = 0;
-    long long ksum = 0; // sum of K(n_s) in 2^-44, loaded alongside the pair sums
     // small clusters: one lane each, all pair loads of the cluster at once
     for (int base = 0; base < nlist; base += 32) {
         const int c = base + lane;
@@ -179,7 +260,6 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
         }
         if (n >= 2 && n <= SMALL_CLUSTER) {
             const uint16_t *m = sl.mem + (v >> 16);
-            ksum += __ldg(kfix + n);
             csum[c] = n <= 4 ? small_cluster_sum<4>(m, n, Dfix, Np, diag)
                              : small_cluster_sum<SMALL_CLUSTER>(m, n, Dfix, Np, diag);
         }
@@ -213,41 +293,215 @@ __device__ double gather_score_warp(const GatherSlice &sl, int N, int Np,
             for (int a = lane; a < n; a += 32) sum += Dfix[(size_t)m[a] * (Np + 1)];
 #pragma unroll
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) {
-            csum[c] = sum;
-            ksum += __ldg(kfix + n);
-        }
+        if (lane == 0) csum[c] = sum;
     }
     __syncwarp();
-    // the terms, one lane per cluster: two running mantissa products per lane
-    // (alternate clusters), so two independent multiply chains overlap
-    LogProd acc, acc2;
-    acc.k = ksum;
-    long long npairs = 0;
-    for (int c = lane; c < nlist; c += 64) {
+    // the terms, one lane per cluster, summed exactly
+    long long lf = 0, npairs = 0;
+    for (int c = lane; c < nlist; c += 32) {
         const int n = list[c] & 0xffff;
-        logprod_mul(acc, n, csum[c], DFIX_BITS);
+        const long long d = csum[c];
+        lf += cluster_term_q40(n, d, ltab, kfix);
         npairs += n * (n - 1) / 2;
-        if (c + 32 < nlist) {
-            const int n2 = list[c + 32] & 0xffff;
-            logprod_mul(acc2, n2, csum[c + 32], DFIX_BITS);
-            npairs += n2 * (n2 - 1) / 2;
+        if (trow) trow[sl.lablist[c]] = d;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lf += __shfl_xor_sync(0xffffffffu, lf, o);
+        npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    }
+    __syncwarp();
+    *npairs_out = npairs;
+    return lf;
+}
+
+// ---------------------------------------------------------------------------
+// Delta scoring of a child (sl.lab holds it) against its first parent a (row
+// a_row of labels, d table row ta, Lfix lfa, pair count npa): returns false
+// (warp-uniform) when more than xmax genes differ, and then the caller scores
+// the child from scratch. Otherwise writes the child's d table row tc (a copy
+// of a's with the touched clusters updated) and returns its Lfix and pair
+// count through the pointers.
+// ---------------------------------------------------------------------------
+__device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
+                                 const uint16_t *__restrict__ a_row,
+                                 const long long *__restrict__ ta, long long lfa, long long npa,
+                                 long long *__restrict__ tc, const int32_t *__restrict__ Dfix,
+                                 int diag, const long long *__restrict__ ltab,
+                                 const long long *__restrict__ kfix, int lane, long long *lf_out,
+                                 long long *np_out)
+{
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    const int X = sl.xmax;
+    // the genes that differ from a, with both labels (gene pairs, 32-bit loads)
+    int nx = 0;
+    {
+        const uint32_t *a2 = reinterpret_cast<const uint32_t *>(a_row);
+        const uint32_t *c2 = reinterpret_cast<const uint32_t *>(sl.lab);
+        const int npair = (N + 1) >> 1;
+        for (int m0 = 0; m0 < npair && nx <= X; m0 += 32) {
+            const int m = m0 + lane;
+            uint32_t av = 0, cv = 0;
+            if (m < npair) {
+                av = __ldg(a2 + m);
+                cv = c2[m];
+            }
+            const bool d0 = m < npair && ((av ^ cv) & 0xffffu) != 0;
+            const bool d1 = m < npair && 2 * m + 1 < N && ((av ^ cv) >> 16) != 0;
+            const unsigned b0 = __ballot_sync(FULL, d0), b1 = __ballot_sync(FULL, d1);
+            const int p0 = nx + __popc(b0 & lt), p1 = nx + __popc(b0) + __popc(b1 & lt);
+            if (d0 && p0 < X) {
+                sl.xs[p0] = (uint16_t)(2 * m);
+                sl.xa[p0] = (uint16_t)(av & 0xffffu);
+                sl.xc[p0] = (uint16_t)(cv & 0xffffu);
+            }
+            if (d1 && p1 < X) {
+                sl.xs[p1] = (uint16_t)(2 * m + 1);
+                sl.xa[p1] = (uint16_t)(av >> 16);
+                sl.xc[p1] = (uint16_t)(cv >> 16);
+            }
+            nx += __popc(b0) + __popc(b1);
         }
     }
-    mant_mul(acc.m, acc.e, acc2.m, acc2.e); // (adds acc2's exponent too)
-    if (pairs_out) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-        if (lane == 0) atomicAdd(pairs_out, (unsigned long long)npairs);
+    if (nx > X) return false;
+    // the child's table starts as a copy of a's (16-byte vectors, eight loads
+    // in flight per lane); the touched clusters are overwritten below
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(ta);
+        int4 *dst = reinterpret_cast<int4 *>(tc);
+        const int nv = Np >> 1; // Np int64 entries
+#pragma unroll 8
+        for (int v = lane; v < nv; v += 32) dst[v] = __ldg(src + v);
     }
-    const double L = logprod_finish(acc, ltab, nlist);
+    // no label affected yet; bitmap of the changed genes in the list space
+    uint16_t *aslot = reinterpret_cast<uint16_t *>(sl.cnt);
+    uint32_t *isx = reinterpret_cast<uint32_t *>(sl.list);
+    for (int w = lane; w < (Np >> 1); w += 32) reinterpret_cast<uint32_t *>(aslot)[w] = 0xffffffffu;
+    for (int w = lane; w < (Np >> 5); w += 32) isx[w] = 0u;
     __syncwarp();
-    return L;
+    for (int x = lane; x < nx; x += 32) atomicOr(&isx[sl.xs[x] >> 5], 1u << (sl.xs[x] & 31));
+    // the affected clusters: the old and new labels of X, each once
+    int na = 0;
+    for (int base = 0; base < 2 * nx; base += 32) {
+        const int q = base + lane;
+        int lab = -1;
+        if (q < 2 * nx) lab = q < nx ? (int)sl.xa[q] : (int)sl.xc[q - nx];
+        const bool fresh = lab >= 0 && aslot[lab] == NO_SLOT;
+        const unsigned grp = __match_any_sync(FULL, fresh ? lab : -1 - lane);
+        const bool leader = fresh && (__ffs(grp) - 1) == lane;
+        const unsigned lb = __ballot_sync(FULL, leader);
+        if (leader) {
+            const int k = na + __popc(lb & lt);
+            aslot[lab] = (uint16_t)k;
+            sl.slab[k] = (uint16_t)lab;
+            sl.in_mask[k] = 0ull;
+            sl.out_mask[k] = 0ull;
+            sl.dacc[k] = 0;
+            sl.nnew[k] = 0u;
+            sl.um[k] = NO_SLOT;
+        }
+        na += __popc(lb);
+        __syncwarp();
+    }
+    for (int x = lane; x < nx; x += 32) {
+        atomicOr(&sl.out_mask[aslot[sl.xa[x]]], 1ull << x);
+        atomicOr(&sl.in_mask[aslot[sl.xc[x]]], 1ull << x);
+    }
+    __syncwarp();
+    // members of the affected clusters in the child: counted, and those that
+    // stayed in place (U) listed in the member space
+    uint16_t *ulist = sl.mem;
+    int nu = 0;
+    for (int j0 = 0; j0 < N; j0 += 32) {
+        const int j = j0 + lane;
+        int k = NO_SLOT;
+        bool stay = false;
+        if (j < N) {
+            k = aslot[sl.lab[j]];
+            if (k != NO_SLOT) {
+                atomicAdd(&sl.nnew[k], 1u);
+                stay = ((isx[j >> 5] >> (j & 31)) & 1u) == 0u;
+                if (stay) sl.um[k] = (uint16_t)j; // any one of them
+            }
+        }
+        const unsigned bs = __ballot_sync(FULL, stay);
+        if (stay) ulist[nu + __popc(bs & lt)] = (uint16_t)j;
+        nu += __popc(bs);
+    }
+    __syncwarp();
+    // 2 [D(U_t, In_t) - D(U_t, Out_t)]: per member left in place, its row of D
+    // at the genes that joined or left its cluster
+    for (int e = lane; e < nu; e += 32) {
+        const int j = ulist[e];
+        const int k = aslot[sl.lab[j]];
+        const unsigned long long mi = sl.in_mask[k], mo = sl.out_mask[k];
+        unsigned long long m = mi | mo;
+        const int32_t *row = Dfix + (size_t)j * Np;
+        long long s = 0;
+        while (m) {
+            int32_t v[4];
+            unsigned long long bit[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                bit[u] = m & (~m + 1ull);
+                m ^= bit[u];
+                v[u] = bit[u] ? __ldg(row + sl.xs[__ffsll((long long)bit[u]) - 1]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += (bit[u] & mi) ? (long long)v[u] : -(long long)v[u];
+        }
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[k]), (unsigned long long)(2 * s));
+    }
+    // D(In_t, In_t) - D(Out_t, Out_t): per changed gene, its row at the genes
+    // that joined its new cluster with it and at those that left its old one
+    for (int x = lane; x < nx; x += 32) {
+        const int kin = aslot[sl.xc[x]], kout = aslot[sl.xa[x]];
+        const int32_t *row = Dfix + (size_t)sl.xs[x] * Np;
+        long long si = 0, so = 0;
+        for (unsigned long long m = sl.in_mask[kin]; m; m &= m - 1)
+            si += __ldg(row + sl.xs[__ffsll((long long)m) - 1]);
+        for (unsigned long long m = sl.out_mask[kout]; m; m &= m - 1)
+            so += __ldg(row + sl.xs[__ffsll((long long)m) - 1]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kin]), (unsigned long long)si);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kout]), (unsigned long long)(-so));
+    }
+    __syncwarp(); // also orders the table copy above before the writes below
+    // the touched terms: new minus old
+    long long dl = 0, dp = 0;
+    for (int k = lane; k < na; k += 32) {
+        const int t = sl.slab[k];
+        const unsigned long long mi = sl.in_mask[k], mo = sl.out_mask[k];
+        const int nn = (int)sl.nnew[k];
+        const int no = nn - __popcll(mi) + __popcll(mo);
+        long long dold = 0;
+        if (no >= 2) {
+            dold = __ldg(ta + t);
+        } else if (no == 1 && diag) { // a singleton's d is its own D_jj
+            const int m = mo ? (int)sl.xs[__ffsll((long long)mo) - 1] : (int)sl.um[k];
+            dold = Dfix[(size_t)m * (Np + 1)];
+        }
+        const long long dnew = dold + sl.dacc[k];
+        if (nn >= 2) {
+            dl += cluster_term_q40(nn, dnew, ltab, kfix);
+            tc[t] = dnew;
+        }
+        if (no >= 2) dl -= cluster_term_q40(no, dold, ltab, kfix);
+        dp += (long long)(nn * (nn - 1) / 2) - (long long)(no * (no - 1) / 2);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        dl += __shfl_xor_sync(FULL, dl, o);
+        dp += __shfl_xor_sync(FULL, dp, o);
+    }
+    __syncwarp();
+    *lf_out = lfa + dl;
+    *np_out = npa + dp;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
 // Score-only: one warp per individual of lab (stateful: the buffer selected by
-// st->gen + sel_off).
+// st->gen + sel_off, whose score tables are written when tab is given).
 // ---------------------------------------------------------------------------
 template <typename LabT>
 __global__ void __launch_bounds__(256, 4)
@@ -255,14 +509,16 @@ __global__ void __launch_bounds__(256, 4)
                         int Np, const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
                         const double *__restrict__ logtab, double *__restrict__ L,
                         int *__restrict__ err, const DevState *__restrict__ st,
-                        unsigned long long *__restrict__ pairs)
+                        unsigned long long *__restrict__ pairs, ScoreTab tab)
 {
     const LabT *__restrict__ lab = lab0;
     unsigned long long *pairs_g = nullptr;
+    int b = 0;
     if (st) {
         if (st->done) return;
         const int gen = st->gen + sel_off;
-        lab = (gen & 1) ? lab1 : lab0;
+        b = gen & 1;
+        lab = b ? lab1 : lab0;
         if (pairs) pairs_g = pairs + gen;
     }
     extern __shared__ unsigned char smem_g[];
@@ -282,10 +538,18 @@ __global__ void __launch_bounds__(256, 4)
         }
         bad = __any_sync(0xffffffffu, bad);
         __syncwarp();
-        const double v = gather_score_warp(sl, N, Np, Dfix, diag, ltab, ktab, lane, pairs_g);
+        long long npairs = 0;
+        long long *trow = tab.d[b] ? tab.d[b] + (size_t)p * tab.ldt : nullptr;
+        const long long lf =
+            score_full_warp(sl, N, Np, Dfix, diag, ltab, ktab, lane, trow, &npairs);
         if (lane == 0) {
-            L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v;
+            L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : lfix_to_double(lf);
             if (bad && err) atomicOr(err, 1);
+            if (tab.lf[b]) {
+                tab.lf[b][p] = lf;
+                tab.np[b][p] = npairs;
+            }
+            if (pairs_g) atomicAdd(pairs_g, (unsigned long long)npairs);
         }
     }
 }
@@ -293,50 +557,67 @@ __global__ void __launch_bounds__(256, 4)
 // ---------------------------------------------------------------------------
 // Fused generation: warp `slot` builds slot of the next population exactly as
 // the evolve kernel does (elite copy, or SUS parents + crossover + mutation)
-// into global memory and its shared slice, then scores it.
+// into global memory and its shared slice, then scores it: an elite keeps its
+// parent's score; a child is scored by delta from its first parent, or from
+// scratch when too many genes changed. b: the buffer of the current
+// generation g (g & 1); the next one is written to 1 - b.
 // ---------------------------------------------------------------------------
-// one slot of the next population (all lanes of the warp call)
-template <typename LabT>
-__device__ __forceinline__ void generation_slot(const LabT *cur, LabT *nxt, const EvolveCfg &cfg,
-                                                int g, uint32_t k0, uint32_t k1, int slot,
+__device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *nxt,
+                                                const EvolveCfg &cfg, int g, uint32_t k0,
+                                                uint32_t k1, int slot,
                                                 const int32_t *__restrict__ perm,
                                                 const uint64_t *__restrict__ prefix, int Np,
                                                 const int32_t *__restrict__ Dfix, int diag,
                                                 const double *__restrict__ logtab,
-                                                double *__restrict__ L, const GatherSlice &sl,
-                                                int lane, unsigned long long *pairs_out,
+                                                double *__restrict__ L, const ScoreTab &tab,
+                                                const GatherSlice &sl, int lane,
+                                                unsigned long long *pairs_out,
                                                 const SusPre *pre = nullptr)
 {
     const int N = cfg.N, ldp = cfg.ldp;
-    LabT *dst = nxt + (size_t)slot * ldp;
+    const int b = g & 1, nb = b ^ 1;
+    uint16_t *dst = nxt + (size_t)slot * ldp;
+    long long *tc = tab.d[nb] + (size_t)slot * tab.ldt;
+    long long lf, np;
     if (slot < cfg.E) {
-        const LabT *src = cur + (size_t)perm[slot] * ldp;
-        for (int j = lane; j < N; j += 32) {
-            const LabT v = src[j];
-            dst[j] = v;
-            sl.lab[j] = (uint16_t)v;
-        }
+        // elite: labels, table and score of the parent, unchanged
+        const int src_i = perm[slot];
+        const uint16_t *src = cur + (size_t)src_i * ldp;
+        for (int j = lane; j < N; j += 32) dst[j] = src[j];
+        const int4 *ts = reinterpret_cast<const int4 *>(tab.d[b] + (size_t)src_i * tab.ldt);
+        int4 *td = reinterpret_cast<int4 *>(tc);
+#pragma unroll 8
+        for (int v = lane; v < (Np >> 1); v += 32) td[v] = __ldg(ts + v);
+        lf = tab.lf[b][src_i];
+        np = tab.np[b][src_i];
     } else {
         const int k = slot - cfg.E;
-        child_genes<LabT>(cur, ldp, N, cfg, g, k, k0, k1, perm, prefix, nullptr, dst, sl.lab,
-                          lane, pre);
+        const int ia = child_genes<uint16_t>(cur, ldp, N, cfg, g, k, k0, k1, perm, prefix, nullptr,
+                                             dst, sl.lab, lane, pre);
+        const long long *ta = tab.d[b] + (size_t)ia * tab.ldt;
+        if (!score_delta_warp(sl, N, Np, cur + (size_t)ia * ldp, ta, tab.lf[b][ia],
+                              tab.np[b][ia], tc, Dfix, diag,
+                              reinterpret_cast<const long long *>(logtab), kfix_of(logtab), lane,
+                              &lf, &np))
+            lf = score_full_warp(sl, N, Np, Dfix, diag, reinterpret_cast<const long long *>(logtab),
+                                 kfix_of(logtab), lane, tc, &np);
     }
-    __syncwarp();
-    const double v = gather_score_warp(sl, N, Np, Dfix, diag,
-                                       reinterpret_cast<const long long *>(logtab), kfix_of(logtab),
-                                       lane, pairs_out);
-    if (lane == 0) L[slot] = v;
+    if (lane == 0) {
+        L[slot] = lfix_to_double(lf);
+        tab.lf[nb][slot] = lf;
+        tab.np[nb][slot] = np;
+        if (pairs_out) atomicAdd(pairs_out, (unsigned long long)np);
+    }
 }
 
-template <typename LabT>
 __global__ void __launch_bounds__(256, 4)
-    gather_generation_kernel(const LabT *pop0, const LabT *pop1, LabT *next0, LabT *next1,
-                             EvolveCfg cfg, const int32_t *__restrict__ perm,
+    gather_generation_kernel(const uint16_t *pop0, const uint16_t *pop1, uint16_t *next0,
+                             uint16_t *next1, EvolveCfg cfg, const int32_t *__restrict__ perm,
                              const uint64_t *__restrict__ prefix, int Np,
                              const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
-                             const double *__restrict__ logtab,
-                             double *__restrict__ L, const DevState *__restrict__ st,
-                             unsigned long long *__restrict__ pairs)
+                             const double *__restrict__ logtab, double *__restrict__ L,
+                             const DevState *__restrict__ st, unsigned long long *__restrict__ pairs,
+                             ScoreTab tab)
 {
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -355,12 +636,12 @@ __global__ void __launch_bounds__(256, 4)
     griddep_wait();
     if (st->done) return;
     const int g = st->gen;
-    const LabT *cur = (g & 1) ? pop1 : pop0;
-    LabT *nxt = (g & 1) ? next1 : next0;
+    const uint16_t *cur = (g & 1) ? pop1 : pop0;
+    uint16_t *nxt = (g & 1) ? next1 : next0;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
-    generation_slot<LabT>(cur, nxt, cfg, g, st->k0, st->k1, slot, perm, prefix, Np, Dfix,
-                          *diag_flag, logtab, L, sl, lane, pairs ? pairs + g + 1 : nullptr,
-                          use_pre ? &pre : nullptr);
+    generation_slot(cur, nxt, cfg, g, st->k0, st->k1, slot, perm, prefix, Np, Dfix, *diag_flag,
+                    logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr,
+                    use_pre ? &pre : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -394,8 +675,8 @@ __global__ void __launch_bounds__(512, 2)
         uint16_t *nxt = (g & 1) ? r.pop0 : r.pop1;
         const uint64_t *prefix = prop ? r.work_prefix : rank_prefix;
         const GatherSlice sl = gather_slice(slice, r.Np);
-        generation_slot<uint16_t>(cur, nxt, cfg, g, st->k0, st->k1, slot, r.perm, prefix, r.Np,
-                                  r.Dfix, *r.diag, logtab, r.L, sl, lane, nullptr);
+        generation_slot(cur, nxt, cfg, g, st->k0, st->k1, slot, r.perm, prefix, r.Np, r.Dfix,
+                        *r.diag, logtab, r.L, r.tab, sl, lane, nullptr);
         __syncwarp();
     }
 }
@@ -411,35 +692,37 @@ static int warps_for(int Np)
     return nw;
 }
 
+size_t score_tab_row_bytes(int Np) { return (size_t)Np * sizeof(long long); }
+
 template <typename LabT>
 int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, int N, int Np,
                         const int32_t *Dfix, const int *diag_flag, const double *logtab,
                         double *L, int *err, const DevState *st, unsigned long long *pairs,
-                        cudaStream_t s)
+                        const ScoreTab &tab, cudaStream_t s)
 {
     const int nw = warps_for(Np);
     const size_t smem = nw * gather_slice_bytes(Np);
     const int grid = (P + nw - 1) / nw;
     gather_score_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, P, N,
                                                           Np, Dfix, diag_flag, logtab, L, err,
-                                                          st, pairs);
+                                                          st, pairs, tab);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
 
-template <typename LabT>
-int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
-                             const int32_t *perm, const uint64_t *prefix, int Np,
-                             const int32_t *Dfix, const int *diag_flag, const double *logtab,
-                             double *L, const DevState *st, unsigned long long *pairs, bool pdl,
+int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2,
+                             const EvolveCfg &cfg, const int32_t *perm, const uint64_t *prefix,
+                             int Np, const int32_t *Dfix, const int *diag_flag,
+                             const double *logtab, double *L, const DevState *st,
+                             unsigned long long *pairs, const ScoreTab &tab, bool pdl,
                              cudaStream_t s)
 {
     const int nw = warps_for(Np);
     const size_t smem = nw * gather_slice_bytes(Np);
     const int grid = (cfg.P + nw - 1) / nw;
-    GPGA_CUDA(launch_pdl(gather_generation_kernel<LabT>, dim3(grid), dim3(32 * nw), smem, s, pdl,
+    GPGA_CUDA(launch_pdl(gather_generation_kernel, dim3(grid), dim3(32 * nw), smem, s, pdl,
                          pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, Dfix,
-                         diag_flag, logtab, L, st, pairs));
+                         diag_flag, logtab, L, st, pairs, tab));
     return GPGA_OK;
 }
 
@@ -472,23 +755,17 @@ int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const Evo
 template int launch_gather_score<uint16_t>(const uint16_t *const *, int, int, int, int, int,
                                            const int32_t *, const int *, const double *, double *,
                                            int *, const DevState *, unsigned long long *,
-                                           cudaStream_t);
+                                           const ScoreTab &, cudaStream_t);
 template int launch_gather_score<int32_t>(const int32_t *const *, int, int, int, int, int,
                                           const int32_t *, const int *, const double *, double *,
                                           int *, const DevState *, unsigned long long *,
-                                          cudaStream_t);
-template int launch_gather_generation<uint16_t>(const uint16_t *const *, uint16_t *const *,
-                                                const EvolveCfg &, const int32_t *,
-                                                const uint64_t *, int, const int32_t *,
-                                                const int *, const double *, double *,
-                                                const DevState *, unsigned long long *, bool,
-                                                cudaStream_t);
+                                          const ScoreTab &, cudaStream_t);
 
 int prepare_gather_kernels(int maxsmem)
 {
     if (int rc = raise_smem(gather_score_kernel<uint16_t>, maxsmem)) return rc;
     if (int rc = raise_smem(gather_score_kernel<int32_t>, maxsmem)) return rc;
-    if (int rc = raise_smem(gather_generation_kernel<uint16_t>, maxsmem)) return rc;
+    if (int rc = raise_smem(gather_generation_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(fleet_generation_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }

@@ -406,6 +406,20 @@ int launch_init_uniform(LabT *pop, int ldp, int P, int N, int K0, uint32_t k0, u
 // descriptor table lives in device memory and is read by the graphed kernels,
 // so the set of runs can change between graph launches.
 // ---------------------------------------------------------------------------
+// Per-run score tables of the gather form, two buffers by generation parity
+// like the populations. For individual p of buffer b:
+//   d[b][p * ldt + s]  d_s = sum_{i,j in s} D_ij in fixed point 2^-30, valid
+//                      where n_s >= 2 (other entries unspecified)
+//   lf[b][p]           L_c in fixed point 2^-40 (exact sum of per-cluster terms)
+//   np[b][p]           sum_s n_s (n_s - 1) / 2
+// All pointers null: no tables (stateless scoring).
+struct ScoreTab {
+    long long *d[2] = {nullptr, nullptr};
+    long long *lf[2] = {nullptr, nullptr};
+    long long *np[2] = {nullptr, nullptr};
+    int ldt = 0;
+};
+
 struct FleetRun {
     int N, Np;               // genes, padded row length of pop and Dfix
     uint16_t *pop0, *pop1;   // P x Np label buffers (ping-pong by generation parity)
@@ -418,6 +432,7 @@ struct FleetRun {
     uint64_t *work_prefix;   // P: proportional-scaling prefix
     DevState *st;            // the run's state
     double *hist;            // max_gens + 1 best values
+    ScoreTab tab;            // the score tables (row length Np)
 };
 
 struct FleetHdr {
@@ -622,9 +637,10 @@ __device__ __forceinline__ void mutate_child(const EvolveCfg &cfg, int N, int g,
     __syncwarp();
 }
 
-// pre (optional): this child's sus_prefetch, issued earlier by the caller
+// pre (optional): this child's sus_prefetch, issued earlier by the caller.
+// Returns the index of parent a (all lanes).
 template <typename LabT>
-__device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, const EvolveCfg &cfg,
+__device__ __forceinline__ int child_genes(const LabT *cur, int ldp, int N, const EvolveCfg &cfg,
                                             int g, int k, uint32_t k0, uint32_t k1,
                                             const int32_t *__restrict__ perm,
                                             const uint64_t *__restrict__ prefix,
@@ -695,7 +711,7 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
             if (s2) s2[m] = cv;
         }
         mutate_child<LabT>(cfg, N, g, k, k0, k1, dst, lab_s, lane);
-        return;
+        return ia;
     }
     for (int m = lane; m < npair; m += 32) {
         const int j0 = 2 * m, j1 = 2 * m + 1;
@@ -721,6 +737,7 @@ __device__ __forceinline__ void child_genes(const LabT *cur, int ldp, int N, con
         }
     }
     mutate_child<LabT>(cfg, N, g, k, k0, k1, dst, lab_s, lane);
+    return ia;
 }
 
 template <typename LabT>
@@ -728,18 +745,21 @@ int launch_evolve(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &
                   const int32_t *perm, const uint64_t *prefix, int32_t *parents_out,
                   const DevState *st, cudaStream_t s);
 
-// gather form (gather.cu)
+// gather form (gather.cu). tab: the score tables written for the scored
+// buffer (stateful runs), or empty.
 template <typename LabT>
 int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, int N, int Np,
                         const int32_t *Dfix, const int *diag_flag, const double *logtab,
                         double *L, int *err, const DevState *st, unsigned long long *pairs,
-                        cudaStream_t s);
-template <typename LabT>
-int launch_gather_generation(const LabT *const *pop2, LabT *const *next2, const EvolveCfg &cfg,
-                             const int32_t *perm, const uint64_t *prefix, int Np,
-                             const int32_t *Dfix, const int *diag_flag, const double *logtab,
-                             double *L, const DevState *st, unsigned long long *pairs, bool pdl,
+                        const ScoreTab &tab, cudaStream_t s);
+int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2,
+                             const EvolveCfg &cfg, const int32_t *perm, const uint64_t *prefix,
+                             int Np, const int32_t *Dfix, const int *diag_flag,
+                             const double *logtab, double *L, const DevState *st,
+                             unsigned long long *pairs, const ScoreTab &tab, bool pdl,
                              cudaStream_t s);
+// bytes of one row of the d table for padded gene count Np
+size_t score_tab_row_bytes(int Np);
 
 int launch_state_init(DevState *st, unsigned long long *ts0, uint32_t k0, uint32_t k1,
                       cudaStream_t s);

@@ -85,7 +85,7 @@ extern "C" GPGA_API int ga_score_noalloc(const int32_t *labels, int P, int N, in
     if (rc) return rc;
     const int32_t *lab2[2] = {labels, labels};
     rc = launch_gather_score<int32_t>(lab2, ld, 0, P, N, Np, Dfix, err + 1, logtab, L, err,
-                                      nullptr, nullptr, s);
+                                      nullptr, nullptr, ScoreTab{}, s);
     if (rc) return rc;
     int herr = 0;
     GPGA_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
