@@ -168,6 +168,29 @@ __device__ __forceinline__ unsigned long long order_key(double x)
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// the same key from the bit pattern with integer operations only (the FP64
+// pipe runs at a small fraction of the integer rate on this part)
+__device__ __forceinline__ unsigned long long order_key_bits(unsigned long long b)
+{
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    if (mag > 0x7ff0000000000000ull) b = 0xfff0000000000000ull; // NaN -> -inf
+    else if (mag == 0ull) b = 0ull;                            // -0 -> +0
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// trunc(x 2^30) of a finite FP64 bit pattern with |x| < 2^32 as an integer
+// (0 for non-finite values, which the mean leaves out), integer operations only
+__device__ __forceinline__ long long fix30_bits(unsigned long long b)
+{
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0x7ff || e == 0) return 0; // non-finite; zero and subnormals
+    const long long m = (long long)((b & 0x000fffffffffffffull) | 0x0010000000000000ull);
+    const int sh = e - 1075 + 30; // x 2^30 = m 2^(e - 1075 + 30)
+    long long v = sh >= 0 ? (sh < 11 ? (m << sh) : 0x7fffffffffffffffll)
+                          : (sh > -64 ? (m >> -sh) : 0ll);
+    return (b >> 63) ? -v : v;
+}
+
 // strict "fitter than" of (key, index) pairs: key descending, index ascending
 __device__ __forceinline__ bool fitter(unsigned long long ka, int ia, unsigned long long kb, int ib)
 {
@@ -516,9 +539,9 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     long long fsum = 0;
     for (int j = tid; j < P; j += blockDim.x) {
-        const double v = L[j];
-        s_key[j] = order_key(v);
-        if (st && isfinite(v)) fsum += __double2ll_rn(v * 1073741824.0);
+        const unsigned long long u = (unsigned long long)__double_as_longlong(L[j]);
+        s_key[j] = order_key_bits(u);
+        if (st) fsum += fix30_bits(u);
     }
     if (st) {
 #pragma unroll

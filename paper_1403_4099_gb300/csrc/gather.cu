@@ -28,7 +28,7 @@
 // |Out_t|) + |X|^2 gathers, and L' = L + sum_t [T(n'_t, d'_t) - T(n_t, d_t)].
 // All sums are exact integers and T depends on (n, d) alone, so the result is
 // bit-identical to scoring the child from scratch. Children with more than
-// XMAX changed genes (one-point crossovers, mostly) are scored from scratch.
+// DELTA_X changed genes (one-point crossovers, mostly) are scored from scratch.
 #include <math.h>
 
 #include "gpga_internal.cuh"
@@ -50,11 +50,15 @@ namespace gpga {
 // never carries into its neighbour because no count or start exceeds N. After
 // the scatter, cnt and lab (contiguous) are dead and hold the pair sums.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int delta_xmax(int Np) { return Np >= 128 ? 64 : Np / 2; }
-__host__ __device__ inline int delta_amax(int Np) { return 2 * delta_xmax(Np); }
+// at most DELTA_X changed genes (bits of a 32-bit mask) and 2 DELTA_X touched
+// clusters; 22 bytes per touched cluster and 6 per changed gene (1.6 KB), so
+// that the slices of a 4-warp CTA at N = 500 leave room for the 8 CTAs per SM
+// the registers allow (one wave of the 4096 children)
+constexpr int DELTA_X = 32;
+constexpr int DELTA_A = 2 * DELTA_X;
 __host__ __device__ inline size_t delta_bytes(int Np)
 {
-    const size_t b = 6 * (size_t)delta_xmax(Np) + 32 * (size_t)delta_amax(Np);
+    const size_t b = 6 * (size_t)DELTA_X + 22 * (size_t)DELTA_A;
     const size_t need = b > (size_t)Np ? b : (size_t)Np;
     return (need + 15) & ~(size_t)15;
 }
@@ -68,13 +72,12 @@ struct GatherSlice {
     uint16_t *lab;
     uint16_t *mem;
     // delta region
-    unsigned long long *in_mask, *out_mask; // per affected cluster: bits over X
-    long long *dacc;                        // per affected cluster: change of d
-    unsigned *nnew;                         // per affected cluster: members in the child
-    uint16_t *slab, *um;                    // per affected cluster: label, a member left in place
-    uint16_t *xs, *xa, *xc;                 // per changed gene: index, label in a, label in the child
-    uint16_t *lablist;                      // full path: label of listed cluster c
-    int xmax, amax;
+    long long *dacc;            // per affected cluster: change of d
+    unsigned *in_mask, *out_mask; // per affected cluster: bits over X
+    uint16_t *nnew;             // per affected cluster: members in the child
+    uint16_t *slab, *um;        // per affected cluster: label, a member left in place
+    uint16_t *xs, *xa, *xc;     // per changed gene: index, label in a, label in the child
+    uint16_t *lablist;          // full path: label of listed cluster c
 };
 
 __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
@@ -85,18 +88,15 @@ __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
     s.lab = reinterpret_cast<uint16_t *>(base + (size_t)4 * Np);
     s.mem = reinterpret_cast<uint16_t *>(base + (size_t)6 * Np);
     unsigned char *d = base + (size_t)8 * Np;
-    s.xmax = delta_xmax(Np);
-    s.amax = delta_amax(Np);
-    const int A = s.amax, X = s.xmax;
-    s.in_mask = reinterpret_cast<unsigned long long *>(d);
-    s.out_mask = s.in_mask + A;
-    s.dacc = reinterpret_cast<long long *>(s.out_mask + A);
-    s.nnew = reinterpret_cast<unsigned *>(s.dacc + A);
-    s.slab = reinterpret_cast<uint16_t *>(s.nnew + A);
-    s.um = s.slab + A;
-    s.xs = s.um + A;
-    s.xa = s.xs + X;
-    s.xc = s.xa + X;
+    s.dacc = reinterpret_cast<long long *>(d);
+    s.in_mask = reinterpret_cast<unsigned *>(s.dacc + DELTA_A);
+    s.out_mask = s.in_mask + DELTA_A;
+    s.nnew = reinterpret_cast<uint16_t *>(s.out_mask + DELTA_A);
+    s.slab = s.nnew + DELTA_A;
+    s.um = s.slab + DELTA_A;
+    s.xs = s.um + DELTA_A;
+    s.xa = s.xs + DELTA_X;
+    s.xc = s.xa + DELTA_X;
     s.lablist = reinterpret_cast<uint16_t *>(d);
     return s;
 }
@@ -318,7 +318,7 @@ __device__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
 // ---------------------------------------------------------------------------
 // Delta scoring of a child (sl.lab holds it) against its first parent a (row
 // a_row of labels, d table row ta, Lfix lfa, pair count npa): returns false
-// (warp-uniform) when more than xmax genes differ, and then the caller scores
+// (warp-uniform) when more than DELTA_X genes differ, and then the caller scores
 // the child from scratch. Otherwise writes the child's d table row tc (a copy
 // of a's with the touched clusters updated) and returns its Lfix and pair
 // count through the pointers.
@@ -332,7 +332,7 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
                                  long long *np_out)
 {
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
-    const int X = sl.xmax;
+    const int X = DELTA_X;
     // the genes that differ from a, with both labels (gene pairs, 32-bit loads)
     int nx = 0;
     {
@@ -394,18 +394,18 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
             const int k = na + __popc(lb & lt);
             aslot[lab] = (uint16_t)k;
             sl.slab[k] = (uint16_t)lab;
-            sl.in_mask[k] = 0ull;
-            sl.out_mask[k] = 0ull;
+            sl.in_mask[k] = 0u;
+            sl.out_mask[k] = 0u;
             sl.dacc[k] = 0;
-            sl.nnew[k] = 0u;
+            sl.nnew[k] = 0;
             sl.um[k] = NO_SLOT;
         }
         na += __popc(lb);
         __syncwarp();
     }
-    for (int x = lane; x < nx; x += 32) {
-        atomicOr(&sl.out_mask[aslot[sl.xa[x]]], 1ull << x);
-        atomicOr(&sl.in_mask[aslot[sl.xc[x]]], 1ull << x);
+    if (lane < nx) {
+        atomicOr(&sl.out_mask[aslot[sl.xa[lane]]], 1u << lane);
+        atomicOr(&sl.in_mask[aslot[sl.xc[lane]]], 1u << lane);
     }
     __syncwarp();
     // members of the affected clusters in the child: counted, and those that
@@ -419,7 +419,8 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
         if (j < N) {
             k = aslot[sl.lab[j]];
             if (k != NO_SLOT) {
-                atomicAdd(&sl.nnew[k], 1u);
+                // 16-bit counts, two per 32-bit word (no count exceeds N)
+                atomicAdd(reinterpret_cast<unsigned *>(sl.nnew) + (k >> 1), 1u << ((k & 1) << 4));
                 stay = ((isx[j >> 5] >> (j & 31)) & 1u) == 0u;
                 if (stay) sl.um[k] = (uint16_t)j; // any one of them
             }
@@ -434,18 +435,18 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
     for (int e = lane; e < nu; e += 32) {
         const int j = ulist[e];
         const int k = aslot[sl.lab[j]];
-        const unsigned long long mi = sl.in_mask[k], mo = sl.out_mask[k];
-        unsigned long long m = mi | mo;
+        const unsigned mi = sl.in_mask[k], mo = sl.out_mask[k];
+        unsigned m = mi | mo;
         const int32_t *row = Dfix + (size_t)j * Np;
         long long s = 0;
         while (m) {
             int32_t v[4];
-            unsigned long long bit[4];
+            unsigned bit[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                bit[u] = m & (~m + 1ull);
+                bit[u] = m & (~m + 1u);
                 m ^= bit[u];
-                v[u] = bit[u] ? __ldg(row + sl.xs[__ffsll((long long)bit[u]) - 1]) : 0;
+                v[u] = bit[u] ? __ldg(row + sl.xs[__ffs(bit[u]) - 1]) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) s += (bit[u] & mi) ? (long long)v[u] : -(long long)v[u];
@@ -454,14 +455,13 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
     }
     // D(In_t, In_t) - D(Out_t, Out_t): per changed gene, its row at the genes
     // that joined its new cluster with it and at those that left its old one
-    for (int x = lane; x < nx; x += 32) {
+    if (lane < nx) {
+        const int x = lane;
         const int kin = aslot[sl.xc[x]], kout = aslot[sl.xa[x]];
         const int32_t *row = Dfix + (size_t)sl.xs[x] * Np;
         long long si = 0, so = 0;
-        for (unsigned long long m = sl.in_mask[kin]; m; m &= m - 1)
-            si += __ldg(row + sl.xs[__ffsll((long long)m) - 1]);
-        for (unsigned long long m = sl.out_mask[kout]; m; m &= m - 1)
-            so += __ldg(row + sl.xs[__ffsll((long long)m) - 1]);
+        for (unsigned m = sl.in_mask[kin]; m; m &= m - 1) si += __ldg(row + sl.xs[__ffs(m) - 1]);
+        for (unsigned m = sl.out_mask[kout]; m; m &= m - 1) so += __ldg(row + sl.xs[__ffs(m) - 1]);
         atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kin]), (unsigned long long)si);
         atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kout]), (unsigned long long)(-so));
     }
@@ -470,14 +470,14 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
     long long dl = 0, dp = 0;
     for (int k = lane; k < na; k += 32) {
         const int t = sl.slab[k];
-        const unsigned long long mi = sl.in_mask[k], mo = sl.out_mask[k];
+        const unsigned mi = sl.in_mask[k], mo = sl.out_mask[k];
         const int nn = (int)sl.nnew[k];
-        const int no = nn - __popcll(mi) + __popcll(mo);
+        const int no = nn - __popc(mi) + __popc(mo);
         long long dold = 0;
         if (no >= 2) {
             dold = __ldg(ta + t);
         } else if (no == 1 && diag) { // a singleton's d is its own D_jj
-            const int m = mo ? (int)sl.xs[__ffsll((long long)mo) - 1] : (int)sl.um[k];
+            const int m = mo ? (int)sl.xs[__ffs(mo) - 1] : (int)sl.um[k];
             dold = Dfix[(size_t)m * (Np + 1)];
         }
         const long long dnew = dold + sl.dacc[k];
