@@ -857,19 +857,19 @@ GPGA_API int cluster_mst(const double *C, int N, const int32_t *labels, int32_t 
     int rc = prepare_device();
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    int *info = nullptr;
-    GPGA_CUDA(cudaMallocAsync((void **)&info, 2 * sizeof(int), s));
+    int *grp = nullptr;
+    GPGA_CUDA(cudaMallocAsync((void **)&grp, cluster_mst_scratch_ints(N) * sizeof(int), s));
     int hinfo[2] = {0, 0};
-    rc = launch_cluster_mst(C, N, labels, edge_u, edge_v, edge_w, info, s);
+    rc = launch_cluster_mst(C, N, labels, edge_u, edge_v, edge_w, grp, s);
     if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(hinfo, grp, sizeof hinfo, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_error(e, "cluster_mst sync", __FILE__, __LINE__);
     }
-    cudaFreeAsync(info, s);
+    cudaFreeAsync(grp, s);
     if (rc) return rc;
     if (hinfo[0]) return set_error(GPGA_ERR_ARG, "cluster_mst: a label lies outside [0, N)");
-    if (n_edges) *n_edges = hinfo[1];
+    if (n_edges) *n_edges = N - hinfo[1];
     return GPGA_OK;
 }
 

@@ -331,90 +331,11 @@ int corr_run_weighted(const double *R, int T, int N, int ld, double lambda, doub
 
 // ---------------------------------------------------------------------------
 // Market-mode removal (pre-processing upstream of C): the largest eigenpair
-// (lambda_1, v) of C by power iteration from the uniform vector (one CTA, one
-// warp per row, FP64; stops when no component of v moves by more than 1e-14,
-// or after max_iters), then C' = C - lambda_1 v v^T renormalised to unit diagonal:
+// (lambda_1, v) of C by power iteration from the uniform vector (FP64; stops
+// when no component of v moves by more than 1e-14, or after max_iters), then
+// C' = C - lambda_1 v v^T renormalised to unit diagonal:
 // C''_ij = C'_ij / sqrt(C'_ii C'_jj), diagonal 1, clamped to [-1, 1].
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
-    market_power_kernel(const double *__restrict__ C, int N, int max_iters,
-                        double *__restrict__ vout, double *__restrict__ info)
-{
-    extern __shared__ double smk[];
-    double *v = smk, *u = smk + N;
-    __shared__ double s_red[32];
-    __shared__ double s_lam;
-    __shared__ int s_stop;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const double v0 = 1.0 / sqrt((double)N);
-    for (int i = tid; i < N; i += blockDim.x) v[i] = v0;
-    if (tid == 0) {
-        s_lam = 0.0;
-        s_stop = 0;
-    }
-    __syncthreads();
-    int it = 0;
-    for (; it < max_iters; ++it) {
-        // u = C v, one warp per row
-        for (int r = wid; r < N; r += nw) {
-            double a = 0.0;
-            for (int j = lane; j < N; j += 32) a += C[(size_t)r * N + j] * v[j];
-#pragma unroll
-            for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) u[r] = a;
-        }
-        __syncthreads();
-        // lambda = v . u and |u|^2 (fixed-order block reductions)
-        double pl = 0.0, pn = 0.0;
-        for (int i = tid; i < N; i += blockDim.x) {
-            pl += v[i] * u[i];
-            pn += u[i] * u[i];
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            pl += __shfl_xor_sync(0xffffffffu, pl, o);
-            pn += __shfl_xor_sync(0xffffffffu, pn, o);
-        }
-        if (lane == 0) s_red[wid] = pl;
-        __syncthreads();
-        double lam = 0.0;
-        for (int k = 0; k < nw; ++k) lam += s_red[k];
-        __syncthreads();
-        if (lane == 0) s_red[wid] = pn;
-        __syncthreads();
-        double nrm = 0.0;
-        for (int k = 0; k < nw; ++k) nrm += s_red[k];
-        nrm = sqrt(nrm);
-        double dv = 0.0; // largest change of a component of v
-        for (int i = tid; i < N; i += blockDim.x) {
-            const double x = u[i] / nrm;
-            dv = fmax(dv, fabs(x - v[i]));
-            v[i] = x;
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
-        __syncthreads();
-        if (lane == 0) s_red[wid] = dv;
-        __syncthreads();
-        if (tid == 0) {
-            double m = 0.0;
-            for (int k = 0; k < nw; ++k) m = fmax(m, s_red[k]);
-            s_lam = lam;
-            s_stop = m <= 1e-14;
-        }
-        __syncthreads();
-        if (s_stop) {
-            ++it;
-            break;
-        }
-    }
-    for (int i = tid; i < N; i += blockDim.x) vout[i] = v[i];
-    if (tid == 0) {
-        info[0] = s_lam;
-        info[1] = (double)it;
-    }
-}
-
 __global__ void market_diag_kernel(const double *__restrict__ C, int N,
                                    const double *__restrict__ v, const double *__restrict__ info,
                                    double *__restrict__ dg, int *__restrict__ err)
@@ -445,28 +366,144 @@ __global__ void market_clean_kernel(double *__restrict__ C, int N, const double 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same power iteration over the whole GPU, one launch per iteration k
+// (k = 0 .. max_iters): v_0 = 1/sqrt(N), v_k = u_{k-1} / |u_{k-1}|, u_k = C v_k,
+// one warp per row of C. Every CTA forms v_k, v_{k-1}, |u_{k-1}| and
+// lambda_{k-1} = v_{k-1} . u_{k-1} itself (fixed-order sums, so all CTAs agree)
+// and tests iteration k-1: if no component of v moved by more than 1e-14, or
+// k = max_iters, the run stops with lambda_{k-1}, k iterations and v_k (CTA 0
+// writes them and the stop flag; later launches return at once). u rotates
+// through three buffers.
+// ---------------------------------------------------------------------------
+constexpr int MP_THREADS = 256;
+
+__device__ double mp_block_sum(double x, double *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    double a = 0.0;
+    for (int k = 0; k < nw; ++k) a += red[k];
+    return a;
+}
+
+__device__ double mp_block_max(double x, double *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    double a = 0.0;
+    for (int k = 0; k < nw; ++k) a = fmax(a, red[k]);
+    return a;
+}
+
+__global__ void __launch_bounds__(MP_THREADS)
+    market_iter_kernel(const double *__restrict__ C, int N, int k, int max_iters,
+                       double *__restrict__ U, double *__restrict__ vout,
+                       double *__restrict__ info)
+{
+    if (info[2] != 0.0) return;
+    extern __shared__ double vk[]; // N
+    __shared__ double red[MP_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const double *u1 = U + (size_t)((k + 2) % 3) * N; // u_{k-1}
+    const double *u2 = U + (size_t)((k + 1) % 3) * N; // u_{k-2}
+    double *uk = U + (size_t)(k % 3) * N;
+    const double v0 = 1.0 / sqrt((double)N);
+    if (k == 0) {
+        for (int j = tid; j < N; j += blockDim.x) vk[j] = v0;
+    } else {
+        double q = 0.0, q2 = 0.0;
+        for (int j = tid; j < N; j += blockDim.x) {
+            q += u1[j] * u1[j];
+            if (k >= 2) q2 += u2[j] * u2[j];
+        }
+        const double inv1 = 1.0 / sqrt(mp_block_sum(q, red));
+        const double inv2 = k >= 2 ? 1.0 / sqrt(mp_block_sum(q2, red)) : 0.0;
+        double lam = 0.0, dv = 0.0;
+        for (int j = tid; j < N; j += blockDim.x) {
+            const double vprev = k >= 2 ? u2[j] * inv2 : v0; // v_{k-1}
+            const double x = u1[j] * inv1;                   // v_k
+            lam += vprev * u1[j];
+            dv = fmax(dv, fabs(x - vprev));
+            vk[j] = x;
+        }
+        lam = mp_block_sum(lam, red);
+        dv = mp_block_max(dv, red);
+        if (dv <= 1e-14 || k >= max_iters) {
+            if (blockIdx.x == 0) {
+                for (int j = tid; j < N; j += blockDim.x) vout[j] = vk[j];
+                if (tid == 0) {
+                    info[0] = lam;
+                    info[1] = (double)k;
+                    info[2] = 1.0;
+                }
+            }
+            return;
+        }
+    }
+    __syncthreads();
+    for (int r = blockIdx.x * nw + wid; r < N; r += gridDim.x * nw) {
+        double a = 0.0;
+        for (int j = lane; j < N; j += 32) a += C[(size_t)r * N + j] * vk[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) uk[r] = a;
+    }
+}
+
 int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, cudaStream_t s)
 {
-    const size_t bytes = (size_t)N * 2 * sizeof(double) + 2 * sizeof(double) + 256;
+    const size_t bytes = (size_t)N * 5 * sizeof(double) + 4 * sizeof(double) + 256;
     char *ws = nullptr;
     GPGA_CUDA(cudaMallocAsync((void **)&ws, bytes, s));
-    double *v = (double *)ws, *dg = v + N, *info = dg + N;
+    double *v = (double *)ws, *dg = v + N, *U = dg + N, *info = U + 3 * (size_t)N;
     int *err = (int *)(ws + bytes - 64);
-    double hinfo[2] = {0.0, 0.0};
+    double hinfo[3] = {0.0, 0.0, 0.0};
     int herr = 0, rc = GPGA_OK;
     do {
-        if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
+        if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(info, 0, 4 * sizeof(double), s) != cudaSuccess) {
             rc = set_error(GPGA_ERR_CUDA, "corr_remove_market: memset failed");
             break;
         }
-        market_power_kernel<<<1, 1024, (size_t)2 * N * sizeof(double), s>>>(C, N, max_iters, v, info);
+        // one launch per iteration over the whole GPU, the stop flag read back
+        // every 16 launches (the launches after the stop return at once)
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int rows_per_cta = MP_THREADS / 32;
+        int grid = (N + rows_per_cta - 1) / rows_per_cta;
+        if (grid > sms) grid = sms;
+        const size_t smem = (size_t)N * sizeof(double);
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k <= max_iters && e == cudaSuccess;) {
+            const int stop = k + 16 <= max_iters + 1 ? k + 16 : max_iters + 1;
+            for (; k < stop; ++k)
+                market_iter_kernel<<<grid, MP_THREADS, smem, s>>>(C, N, k, max_iters, U, v, info);
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (hinfo[2] != 0.0) break;
+        }
+        if (e != cudaSuccess) {
+            rc = cuda_error(e, "corr_remove_market power iteration", __FILE__, __LINE__);
+            break;
+        }
         market_diag_kernel<<<(N + 255) / 256, 256, 0, s>>>(C, N, v, info, dg, err);
         const size_t total = (size_t)N * N;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         market_clean_kernel<<<blocks, 256, 0, s>>>(C, N, v, info, dg);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo, info, sizeof hinfo, cudaMemcpyDeviceToHost, s);
+        e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_error(e, "corr_remove_market", __FILE__, __LINE__);
@@ -483,7 +520,7 @@ int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, 
 
 int prepare_corr_kernels(int maxsmem)
 {
-    return raise_smem(market_power_kernel, maxsmem);
+    return raise_smem(market_iter_kernel, maxsmem);
 }
 
 } // namespace gpga

@@ -521,7 +521,29 @@ int launch_fleet_migrate(const FleetRun *runs, const FleetHdr *hdr, int P, int e
 // Stateful use: g = st->gen + gen_off (read only by the CTA that holds rank 0,
 // which is also the only writer of the state).
 // ---------------------------------------------------------------------------
-constexpr int SEL_WARPS = 8;
+constexpr int SEL_WARPS = 32;
+
+// count of keys of s_key[j0, j1) (pairs of 16 bytes; j0, j1 even) that are
+// >= ki (ge) or > ki
+template <bool GE>
+__device__ __forceinline__ int count_fitter(const unsigned long long *s_key, int j0, int j1,
+                                            unsigned long long ki)
+{
+    int c = 0;
+    const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(s_key);
+#pragma unroll 4
+    for (int j = j0 >> 1; j < (j1 >> 1); ++j) {
+        const ulonglong2 v = k2[j];
+        if (GE) {
+            c += v.x >= ki ? 1 : 0;
+            c += v.y >= ki ? 1 : 0;
+        } else {
+            c += v.x > ki ? 1 : 0;
+            c += v.y > ki ? 1 : 0;
+        }
+    }
+    return c;
+}
 
 template <typename LabT>
 __global__ void __launch_bounds__(32 * SEL_WARPS)
@@ -530,18 +552,29 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
                         const LabT *pop1, LabT *__restrict__ ring,
                         unsigned long long *__restrict__ ts)
 {
-    extern __shared__ unsigned long long s_key[]; // P keys
+    extern __shared__ unsigned long long s_key[]; // P keys, zero-padded to Pp
     __shared__ int s_cnt[SEL_WARPS][32];
     __shared__ long long s_sum[SEL_WARPS];
     __shared__ int s_best;
     if (st && st->done) return; // a run that terminated selects nothing
-    const int P = cfg.P;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int P = cfg.P, Pp = (P + 2 * SEL_WARPS - 1) & ~(2 * SEL_WARPS - 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
+    // keys (a padding key 0 is below every real key, so it is never fitter),
+    // four loads in flight per thread; the fixed-point sum for the mean
     long long fsum = 0;
-    for (int j = tid; j < P; j += blockDim.x) {
-        const unsigned long long u = (unsigned long long)__double_as_longlong(L[j]);
-        s_key[j] = order_key_bits(u);
-        if (st) fsum += fix30_bits(u);
+    for (int j0 = tid; j0 < Pp; j0 += 4 * nt) {
+        unsigned long long u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q * nt;
+            u[q] = j < P ? (unsigned long long)__double_as_longlong(__ldg(L + j)) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q * nt;
+            if (j < Pp) s_key[j] = j < P ? order_key_bits(u[q]) : 0ull;
+            if (st && j < P) fsum += fix30_bits(u[q]);
+        }
     }
     if (st) {
 #pragma unroll
@@ -552,25 +585,16 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
     __syncthreads();
     const int b0 = blockIdx.x * 32, i = b0 + lane;
     const unsigned long long ki = i < P ? s_key[i] : 0ull;
-    const int per = (P + SEL_WARPS - 1) / SEL_WARPS;
-    const int j0 = min(P, warp * per), j1 = min(P, j0 + per);
-    int c = 0;
-    {
-        // j below the CTA's block: fitter iff k_j >= k_i (lower index wins ties)
-        const int e = min(j1, b0);
-        int j = j0;
-#pragma unroll 8
-        for (; j < e; ++j) c += s_key[j] >= ki ? 1 : 0;
-        // inside the block: per lane
-        const int e2 = min(j1, b0 + 32);
-        for (j = max(j0, b0); j < e2; ++j) {
-            const unsigned long long kj = s_key[j];
-            c += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
-        }
-        // above the block: fitter iff k_j > k_i
-#pragma unroll 8
-        for (j = max(j0, b0 + 32); j < j1; ++j) c += s_key[j] > ki ? 1 : 0;
+    const int per = Pp / SEL_WARPS; // even
+    const int j0 = warp * per, j1 = j0 + per;
+    // j below the CTA's block: fitter iff k_j >= k_i (lower index wins ties);
+    // inside the block: per lane; above it: fitter iff k_j > k_i
+    int c = count_fitter<true>(s_key, j0, min(j1, b0), ki);
+    for (int j = max(j0, b0); j < min(j1, b0 + 32); ++j) {
+        const unsigned long long kj = s_key[j];
+        c += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
     }
+    c += count_fitter<false>(s_key, max(j0, b0 + 32), j1, ki);
     s_cnt[warp][lane] = c;
     __syncthreads();
     if (warp == 0) {
@@ -626,7 +650,8 @@ int launch_select(const double *L, const SelectCfg &cfg, int *rank, int32_t *per
 {
     if (cfg.scaling == GPGA_SCALING_RANK) {
         const int grid = (cfg.P + 31) / 32;
-        const size_t smem = (size_t)cfg.P * sizeof(unsigned long long);
+        const size_t smem = (size_t)((cfg.P + 2 * SEL_WARPS - 1) & ~(2 * SEL_WARPS - 1)) *
+                            sizeof(unsigned long long);
         select_count_kernel<LabT><<<grid, 32 * SEL_WARPS, smem, s>>>(
             L, cfg, perm, st, hist, pop2 ? pop2[0] : nullptr, pop2 ? pop2[1] : nullptr, ring, ts);
         GPGA_LAUNCH_CHECK();

@@ -785,9 +785,11 @@ int fleet_ctas_per_sm(int Np_max, int warps, int *out);
 
 // threshold initialisation (init.cu)
 // per-cluster minimum spanning trees of one configuration (labels device,
-// int32 N); info[0] = 1 on a label outside [0, N), info[1] = edges written
+// int32 N); grp: device scratch of cluster_mst_scratch_ints(N) ints, of
+// which grp[0] = 1 on a label outside [0, N) and grp[1] = the cluster count
+size_t cluster_mst_scratch_ints(int N);
 int launch_cluster_mst(const double *C, int N, const int32_t *labels, int32_t *eu, int32_t *ev,
-                       double *ew, int *info, cudaStream_t s);
+                       double *ew, int *grp, cudaStream_t s);
 int launch_mst(const double *C, int N, int32_t *edge_u, int32_t *edge_v, double *edge_w,
                cudaStream_t s);
 template <typename LabT>

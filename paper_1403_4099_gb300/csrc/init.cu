@@ -183,24 +183,30 @@ __device__ __forceinline__ double corr_dist(const double *C, int N, int a, int b
     return sqrt(2.0 * (1.0 - C[(size_t)u * N + v]));
 }
 
+// ---------------------------------------------------------------------------
+// Per-cluster minimum spanning trees, in two launches:
+//   cluster_group_kernel  (one CTA) labels -> clusters in first-occurrence
+//                         order: sizes, starts and the genes grouped by
+//                         cluster, written to the scratch grp
+//   cluster_prim_kernel   one CTA per cluster (CTAs beyond the cluster count
+//                         return): Prim from the cluster's first gene; a
+//                         cluster of at most 32 genes is done by one warp with
+//                         shuffles only, a larger one by the CTA
+// Scratch grp (int32): [0] bad-label flag, [1] cluster count K, [2 .. 2+N]
+// starts (K + 1 used), [3+N .. 3+2N) genes grouped by cluster.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-    cluster_mst_kernel(const double *__restrict__ C, int N, const int32_t *__restrict__ labels,
-                       int32_t *__restrict__ eu, int32_t *__restrict__ ev,
-                       double *__restrict__ ew, int *__restrict__ info)
+    cluster_group_kernel(int N, const int32_t *__restrict__ labels, int *__restrict__ grp)
 {
-    extern __shared__ double sm_mst[];
-    double *key = sm_mst;                                     // N: Prim keys by member position
-    int *li = reinterpret_cast<int *>(key + N);               // N labels
-    int *first = li + N;                                      // N: label -> first gene
-    int *cid = first + N;                                     // N: gene -> canonical cluster
-    int *cnt = cid + N;                                       // N + 1: sizes, then starts
-    int *mem = cnt + N + 1;                                   // N: genes grouped by cluster
-    int *src = mem + N;                                       // N: Prim parent by position
-    int *intree = src + N;                                    // N
-    __shared__ double s_bk[32];
-    __shared__ int s_bi[32];
+    extern __shared__ int sm_grp[];
+    int *li = sm_grp;          // N labels
+    int *first = li + N;       // N: label -> first gene
+    int *cid = first + N;      // N: gene -> canonical cluster (at first genes)
+    int *cnt = cid + N;        // N + 1: sizes, then starts
+    int *fill = cnt + N + 1;   // N: fill counters
     __shared__ int s_part[32];
     __shared__ int s_bad;
+    int *start = grp + 2, *mem = grp + 3 + N;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int nwarps = nt >> 5;
     if (tid == 0) s_bad = 0;
@@ -214,11 +220,14 @@ __global__ void __launch_bounds__(1024)
         li[i] = v;
         first[i] = N;
         cnt[i] = 0;
-        src[i] = 0; // fill counters of the grouping below
+        fill[i] = 0;
     }
     __syncthreads();
     if (s_bad) {
-        if (tid == 0) info[0] = 1;
+        if (tid == 0) {
+            grp[0] = 1;
+            grp[1] = 0;
+        }
         return;
     }
     for (int i = tid; i < N; i += nt) atomicMin(&first[li[i]], i);
@@ -251,10 +260,7 @@ __global__ void __launch_bounds__(1024)
         if (first[li[i]] == i) cid[i] = run++; // cid of a cluster's first gene
     const int K = s_part[nwarps - 1];
     __syncthreads();
-    for (int i = tid; i < N; i += nt) {
-        const int c = cid[first[li[i]]];
-        atomicAdd(&cnt[c], 1);
-    }
+    for (int i = tid; i < N; i += nt) atomicAdd(&cnt[cid[first[li[i]]]], 1);
     __syncthreads();
     // cluster starts (sequential over K by thread 0: K <= N, integer work)
     if (tid == 0) {
@@ -265,113 +271,180 @@ __global__ void __launch_bounds__(1024)
             acc += n;
         }
         cnt[K] = acc;
+        grp[0] = 0;
+        grp[1] = K;
     }
     __syncthreads();
-    // group the genes by cluster (positions inside a cluster in any order:
-    // Prim's ties go to the lower gene index, not the position)
+    for (int c = tid; c <= K; c += nt) start[c] = cnt[c];
+    // group the genes by cluster, ascending gene index inside a cluster
+    // (Prim's ties go to the lower gene index, not the position, so any order
+    // would do; this one keeps the first gene at position 0)
     for (int i = tid; i < N; i += nt) {
         const int c = cid[first[li[i]]];
-        mem[atomicAdd(&src[c], 1) + cnt[c]] = i;
+        mem[atomicAdd(&fill[c], 1) + cnt[c]] = i;
     }
-    __syncthreads();
-    for (int c = 0; c < K; ++c) {
-        const int st = cnt[c], n = cnt[c + 1] - st;
-        if (n < 2) continue; // (CTA-uniform)
-        const int root = first[li[mem[st]]]; // the cluster's first gene
-        for (int t = tid; t < n; t += nt) {
-            const int g = mem[st + t];
-            key[t] = g == root ? 0.0 : corr_dist(C, N, root, g);
-            src[t] = root;
-            intree[t] = g == root;
-        }
-        __syncthreads();
-        const int ebase = st - c;
+}
+
+// better Prim candidate: smaller key, ties to the lower gene index
+__device__ __forceinline__ bool prim_better(double k, int g, double bk, int bg)
+{
+    return k < bk || (k == bk && g < bg);
+}
+
+__global__ void __launch_bounds__(256)
+    cluster_prim_kernel(const double *__restrict__ C, int N, const int *__restrict__ grp,
+                        int32_t *__restrict__ eu, int32_t *__restrict__ ev,
+                        double *__restrict__ ew)
+{
+    extern __shared__ double sm_prim[];
+    const int c = blockIdx.x;
+    if (grp[0] || c >= grp[1]) return;
+    const int *start = grp + 2, *memg = grp + 3 + N;
+    const int st = start[c], n = start[c + 1] - st;
+    if (n < 2) return;
+    const int *mem = memg + st;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    int root = N;
+    for (int t = 0; t < n; ++t) root = min(root, mem[t]); // the cluster's first gene
+    const int ebase = st - c;
+    if (n <= 32) {
+        // one warp: member t = lane
+        if (wid) return;
+        const int g = lane < n ? mem[lane] : 0x7fffffff;
+        double key = (lane < n && g != root) ? corr_dist(C, N, root, g) : INFINITY;
+        int src = root;
+        bool in = lane >= n || g == root;
         for (int step = 0; step < n - 1; ++step) {
-            double bk = INFINITY;
-            int bg = 0x7fffffff, bt = -1;
-            for (int t = tid; t < n; t += nt) {
-                if (intree[t]) continue;
-                const double k = key[t];
-                const int g = mem[st + t];
-                if (k < bk || (k == bk && g < bg)) {
-                    bk = k;
-                    bg = g;
-                    bt = t;
+            double bk = in ? INFINITY : key;
+            int bg = in ? 0x7fffffff : g, bl = lane;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (prim_better(ok, og, bk, bg)) {
+                    bk = ok;
+                    bg = og;
+                    bl = ol;
                 }
             }
+            const int vs = __shfl_sync(0xffffffffu, src, bl);
+            if (lane == bl) {
+                in = true;
+                eu[ebase + step] = min(vs, g);
+                ev[ebase + step] = max(vs, g);
+                ew[ebase + step] = bk;
+            }
+            if (!in) {
+                const double d = corr_dist(C, N, bg, g);
+                if (d < key) {
+                    key = d;
+                    src = bg;
+                }
+            }
+        }
+        return;
+    }
+    // the CTA: members t = tid, tid + 256, ...
+    double *key = sm_prim;                          // n
+    int *src = reinterpret_cast<int *>(key + n);    // n
+    int *intree = src + n;                          // n
+    __shared__ double s_bk[8];
+    __shared__ int s_bg[8], s_bt[8];
+    __shared__ int s_pick;
+    for (int t = tid; t < n; t += blockDim.x) {
+        const int g = mem[t];
+        key[t] = g == root ? 0.0 : corr_dist(C, N, root, g);
+        src[t] = root;
+        intree[t] = g == root;
+    }
+    __syncthreads();
+    for (int step = 0; step < n - 1; ++step) {
+        double bk = INFINITY;
+        int bg = 0x7fffffff, bt = -1;
+        for (int t = tid; t < n; t += blockDim.x) {
+            if (intree[t]) continue;
+            const double k = key[t];
+            const int g = mem[t];
+            if (prim_better(k, g, bk, bg)) {
+                bk = k;
+                bg = g;
+                bt = t;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+            if (prim_better(ok, og, bk, bg)) {
+                bk = ok;
+                bg = og;
+                bt = ot;
+            }
+        }
+        if (lane == 0) {
+            s_bk[wid] = bk;
+            s_bg[wid] = bg;
+            s_bt[wid] = bt;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            bk = lane < nw ? s_bk[lane] : INFINITY;
+            bg = lane < nw ? s_bg[lane] : 0x7fffffff;
+            bt = lane < nw ? s_bt[lane] : -1;
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
                 const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
                 const int og = __shfl_xor_sync(0xffffffffu, bg, o);
                 const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-                if (ok < bk || (ok == bk && og < bg)) {
+                if (prim_better(ok, og, bk, bg)) {
                     bk = ok;
                     bg = og;
                     bt = ot;
                 }
             }
             if (lane == 0) {
-                s_bk[wid] = bk;
-                s_bi[wid] = bt;
-                s_part[wid] = bg;
+                s_pick = bt;
+                const int a = src[bt], b = mem[bt];
+                eu[ebase + step] = min(a, b);
+                ev[ebase + step] = max(a, b);
+                ew[ebase + step] = bk;
+                intree[bt] = 1;
             }
-            __syncthreads();
-            if (wid == 0) {
-                bk = lane < nwarps ? s_bk[lane] : INFINITY;
-                bt = lane < nwarps ? s_bi[lane] : -1;
-                bg = lane < nwarps ? s_part[lane] : 0x7fffffff;
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
-                    const int og = __shfl_xor_sync(0xffffffffu, bg, o);
-                    const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-                    if (ok < bk || (ok == bk && og < bg)) {
-                        bk = ok;
-                        bg = og;
-                        bt = ot;
-                    }
-                }
-                if (lane == 0) {
-                    s_bi[0] = bt;
-                    const int a = src[bt], b = mem[st + bt];
-                    eu[ebase + step] = min(a, b);
-                    ev[ebase + step] = max(a, b);
-                    ew[ebase + step] = bk;
-                    intree[bt] = 1;
-                }
-            }
-            __syncthreads();
-            const int vt = s_bi[0];
-            const int vg = mem[st + vt];
-            for (int t = tid; t < n; t += nt) {
-                if (intree[t]) continue;
-                const double d = corr_dist(C, N, vg, mem[st + t]);
-                if (d < key[t]) {
-                    key[t] = d;
-                    src[t] = vg;
-                }
-            }
-            __syncthreads();
         }
-    }
-    if (tid == 0) {
-        info[0] = 0;
-        info[1] = N - K;
+        __syncthreads();
+        const int vg = mem[s_pick];
+        for (int t = tid; t < n; t += blockDim.x) {
+            if (intree[t]) continue;
+            const double d = corr_dist(C, N, vg, mem[t]);
+            if (d < key[t]) {
+                key[t] = d;
+                src[t] = vg;
+            }
+        }
+        __syncthreads();
     }
 }
 
+size_t cluster_mst_scratch_ints(int N) { return (size_t)3 + 2 * (size_t)N; }
+
 int launch_cluster_mst(const double *C, int N, const int32_t *labels, int32_t *eu, int32_t *ev,
-                       double *ew, int *info, cudaStream_t s)
+                       double *ew, int *grp, cudaStream_t s)
 {
-    const size_t smem = (size_t)N * sizeof(double) + (size_t)(7 * N + 1) * sizeof(int);
-    cluster_mst_kernel<<<1, 1024, smem, s>>>(C, N, labels, eu, ev, ew, info);
+    const size_t gsmem = (size_t)(5 * N + 1) * sizeof(int);
+    cluster_group_kernel<<<1, 1024, gsmem, s>>>(N, labels, grp);
+    GPGA_LAUNCH_CHECK();
+    const size_t psmem = (size_t)N * (sizeof(double) + 2 * sizeof(int));
+    cluster_prim_kernel<<<N, 256, psmem, s>>>(C, N, grp, eu, ev, ew);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
 
 int prepare_init_kernels(int maxsmem)
 {
-    if (int rc = raise_smem(cluster_mst_kernel, maxsmem)) return rc;
+    if (int rc = raise_smem(cluster_group_kernel, maxsmem)) return rc;
+    if (int rc = raise_smem(cluster_prim_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(mst_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(init_threshold_kernel<uint16_t>, maxsmem)) return rc;
     if (int rc = raise_smem(init_threshold_kernel<int32_t>, maxsmem)) return rc;
