@@ -607,11 +607,17 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
         }
     }
     __syncthreads();
-    // the next generation kernel (a programmatic dependent) may be scheduled
-    // now; it waits for this grid to complete before it reads anything written here
-    griddep_launch();
+    // The next generation kernel (a programmatic dependent) may be scheduled
+    // once every CTA has let it: the CTA that holds rank 0 does so only after
+    // it has written the new generation into the state (the kernel draws its
+    // children for that value before it waits for this grid, and draws them
+    // again if the value it read was stale); everything else it reads after
+    // its wait, when this grid has completed.
     const int bidx = s_best;
-    if (!st || bidx < 0) return;
+    if (!st || bidx < 0) {
+        griddep_launch();
+        return;
+    }
     const int g = st->gen + cfg.gen_off;
     if (cfg.record && ring) {
         const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
@@ -637,7 +643,10 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
         }
         st->done = done;
         st->mean = (double)lsum * 9.313225746154785e-10 / (double)P;
+        __threadfence();
     }
+    __syncthreads();
+    griddep_launch();
 }
 
 // selection by counting for rank scaling (one launch, no ticket), else the

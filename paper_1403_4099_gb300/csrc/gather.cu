@@ -51,14 +51,14 @@ namespace gpga {
 // the scatter, cnt and lab (contiguous) are dead and hold the pair sums.
 // ---------------------------------------------------------------------------
 // at most DELTA_X changed genes (bits of a 32-bit mask) and 2 DELTA_X touched
-// clusters; 22 bytes per touched cluster and 6 per changed gene (1.6 KB), so
+// clusters; 30 bytes per touched cluster and 6 per changed gene (2.1 KB), so
 // that the slices of a 4-warp CTA at N = 500 leave room for the 8 CTAs per SM
 // the registers allow (one wave of the 4096 children)
 constexpr int DELTA_X = 32;
 constexpr int DELTA_A = 2 * DELTA_X;
 __host__ __device__ inline size_t delta_bytes(int Np)
 {
-    const size_t b = 6 * (size_t)DELTA_X + 22 * (size_t)DELTA_A;
+    const size_t b = 6 * (size_t)DELTA_X + 30 * (size_t)DELTA_A;
     const size_t need = b > (size_t)Np ? b : (size_t)Np;
     return (need + 15) & ~(size_t)15;
 }
@@ -72,7 +72,8 @@ struct GatherSlice {
     uint16_t *lab;
     uint16_t *mem;
     // delta region
-    long long *dacc;            // per affected cluster: change of d
+    long long *dacc;            // per affected cluster: change of d, then the new d
+    long long *dold;            // per affected cluster: d in the parent
     unsigned *in_mask, *out_mask; // per affected cluster: bits over X
     uint16_t *nnew;             // per affected cluster: members in the child
     uint16_t *slab, *um;        // per affected cluster: label, a member left in place
@@ -89,7 +90,8 @@ __device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
     s.mem = reinterpret_cast<uint16_t *>(base + (size_t)6 * Np);
     unsigned char *d = base + (size_t)8 * Np;
     s.dacc = reinterpret_cast<long long *>(d);
-    s.in_mask = reinterpret_cast<unsigned *>(s.dacc + DELTA_A);
+    s.dold = s.dacc + DELTA_A;
+    s.in_mask = reinterpret_cast<unsigned *>(s.dold + DELTA_A);
     s.out_mask = s.in_mask + DELTA_A;
     s.nnew = reinterpret_cast<uint16_t *>(s.out_mask + DELTA_A);
     s.slab = s.nnew + DELTA_A;
@@ -133,21 +135,33 @@ __device__ __forceinline__ long long small_cluster_sum(const uint16_t *m, int n,
     return s;
 }
 
-// T(n, d) = K(n) - 1/2 log(c d^(n-1)) of one cluster (n >= 2) in fixed point
-// 2^-40, from d as the exact fixed-point integer df = d 2^DFIX_BITS: the
-// product c d^(n-1) as a 63-bit mantissa and a binary exponent (logprod_mul,
-// with Eq. 8's domain floors), then e ln 2 + log(m 2^-62) with the table log.
-__device__ __forceinline__ long long cluster_term_q40(int n, long long df,
-                                                      const long long *__restrict__ ltab,
-                                                      const long long *__restrict__ kfix)
+// T(n, d) = K(n) - 1/2 [log c + (n - 1) log d] of one cluster (n >= 2) in
+// fixed point 2^-40, from d as the exact fixed-point integer df = d 2^DFIX_BITS,
+// c = n^2 - d, with Eq. 8's domain floors (c >= n 2^-40, d >= n (n - 1) 2^-40,
+// at least one unit). Each of c, d is a 63-bit mantissa m and an exponent e
+// (v = m 2^(e - 62)), log v = log(m 2^-62) + e ln 2 with the table log; the two
+// logs are independent chains, and the bracket is summed exactly in 128 bits
+// (Q62) before the one final shift, so T depends on (n, df) alone.
+__device__ __forceinline__ long long cluster_term(int n, long long df,
+                                                  const long long *__restrict__ ltab,
+                                                  const long long *__restrict__ kfix)
 {
-    LogProd a;
-    logprod_mul(a, n, df, DFIX_BITS);
-    const long long ph = __mul64hi(a.e, LN2_Q62);
-    const unsigned long long pl = (unsigned long long)a.e * (unsigned long long)LN2_Q62;
-    const long long elog = (long long)(((unsigned long long)ph << 42) | (pl >> 22));
-    const long long tot = elog + (log_q62(a.m, ltab) >> 22);
-    return (__ldg(kfix + n) >> (KFIX_BITS - 40)) - (tot >> 1);
+    long long cf = (((long long)n * n) << DFIX_BITS) - df;
+    const int sh = 40 - DFIX_BITS;
+    long long cmin = (long long)n >> sh, dmin = ((long long)n * (n - 1)) >> sh;
+    if (cmin < 1) cmin = 1;
+    if (dmin < 1) dmin = 1;
+    if (cf < cmin) cf = cmin;
+    if (df < dmin) df = dmin;
+    unsigned long long mc, md;
+    long long ec, ed;
+    mant_of(cf, mc, ec);
+    mant_of(df, md, ed);
+    const long long lc = log_q62(mc, ltab), ld = log_q62(md, ltab);
+    const long long n1 = n - 1;
+    const __int128 s = (__int128)lc + (__int128)n1 * ld +
+                       (__int128)((ec - DFIX_BITS) + n1 * (ed - DFIX_BITS)) * LN2_Q62;
+    return (__ldg(kfix + n) >> (KFIX_BITS - 40)) - (long long)(s >> 23);
 }
 
 // L from its Q40 fixed point
@@ -301,7 +315,7 @@ __device__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
     for (int c = lane; c < nlist; c += 32) {
         const int n = list[c] & 0xffff;
         const long long d = csum[c];
-        lf += cluster_term_q40(n, d, ltab, kfix);
+        lf += cluster_term(n, d, ltab, kfix);
         npairs += n * (n - 1) / 2;
         if (trow) trow[sl.lablist[c]] = d;
     }
@@ -316,15 +330,264 @@ __device__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
 }
 
 // ---------------------------------------------------------------------------
-// Delta scoring of a child (sl.lab holds it) against its first parent a (row
-// a_row of labels, d table row ta, Lfix lfa, pair count npa): returns false
-// (warp-uniform) when more than DELTA_X genes differ, and then the caller scores
-// the child from scratch. Otherwise writes the child's d table row tc (a copy
-// of a's with the touched clusters updated) and returns its Lfix and pair
-// count through the pointers.
+// Child construction for the 16-bit populations of the gather form, in blocks
+// of 16 genes (the mutation blocks): lane l owns blocks l, l + 32, ... for the
+// crossover, the mutation and the comparison with parent a, so the changed
+// genes X are found in registers. The result is gene for gene that of
+// child_genes (same draws, same rules); only the work split differs.
 // ---------------------------------------------------------------------------
-__device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
-                                 const uint16_t *__restrict__ a_row,
+// the draws of child k of generation g that depend on neither parent: the rank
+// of this half-warp's SUS pointer (lanes 0-15 parent a, 16-31 parent b) when
+// the fixed rank brackets give it directly (-1: searched later), the crossover
+// words, and the mutations of the lane's first block (gene mask and the first
+// four new labels in gene order; more than four: drawn again when applied)
+struct ChildPlan {
+    int g;
+    int rank;
+    uint32_t x0, x1, x2;
+    uint32_t mmask;
+    uint32_t mlab[2];
+    int mover;
+};
+
+__device__ __forceinline__ ChildPlan plan_child(const EvolveCfg &cfg, int g, int k, uint32_t k0,
+                                                uint32_t k1, const SusPre *pre, int lane)
+{
+    ChildPlan c;
+    c.g = g;
+    c.rank = -1;
+    const int M = cfg.M;
+    if (pre && __all_sync(0xffffffffu, pre->hi - pre->lo <= 16)) {
+        const uint32_t kp = lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M);
+        const uint32_t su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1).x;
+        const uint64_t x = sus_pointer(kp, su, pre->W, (uint32_t)M, cfg.inv_md);
+        const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
+        const bool le = (lane & 15) < pre->hi - pre->lo && pre->cand <= x;
+        c.rank = pre->lo + __popc(__ballot_sync(0xffffffffu, le) & half);
+    }
+    const U4 xw = philox((uint32_t)g, (uint32_t)k, 0u, STREAM_XOVER, k0, k1);
+    c.x0 = xw.x;
+    c.x1 = xw.y;
+    c.x2 = xw.z;
+    c.mmask = 0u;
+    c.mlab[0] = c.mlab[1] = 0u;
+    c.mover = 0;
+    const int len = min(MUT_BLOCK, cfg.N - MUT_BLOCK * lane);
+    if (cfg.thr_pm && len > 0) {
+        int pos = 0, cnt = 0;
+        auto rec = [&](int p, int v) {
+            c.mmask |= 1u << p;
+            if (cnt < 2) c.mlab[0] |= (uint32_t)v << ((cnt & 1) << 4);
+            else if (cnt < 4) c.mlab[1] |= (uint32_t)v << ((cnt & 1) << 4);
+            else c.mover = 1;
+            ++cnt;
+        };
+        for (uint32_t e = 0;; ++e) {
+            const U4 w = philox((uint32_t)g, (uint32_t)k, (uint32_t)lane + 65536u * e, STREAM_MUT,
+                                k0, k1);
+            pos += mutation_skip(w.x, cfg);
+            if (pos >= len) break;
+            rec(pos, draw_below(w.y, (uint32_t)cfg.N));
+            if (++pos >= len) break;
+            pos += mutation_skip(w.z, cfg);
+            if (pos >= len) break;
+            rec(pos, draw_below(w.w, (uint32_t)cfg.N));
+            if (++pos >= len) break;
+        }
+    }
+    return c;
+}
+
+// gene p (0..15, run time) of the block in v (8 words) set to lab; the words
+// are selected with compile-time indices so that v stays in registers
+__device__ __forceinline__ void put_gene(uint32_t v[8], int p, int lab)
+{
+    const uint32_t hsh = (uint32_t)(p & 1) << 4;
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+        if (w == (p >> 1)) v[w] = (v[w] & ~(0xffffu << hsh)) | ((uint32_t)lab << hsh);
+}
+
+// mutations of block blk of child k (g), applied to the 16 genes in v (8 words)
+__device__ __forceinline__ void mutate_block(const EvolveCfg &cfg, int g, int k, uint32_t k0,
+                                             uint32_t k1, int blk, uint32_t v[8])
+{
+    const int len = min(MUT_BLOCK, cfg.N - MUT_BLOCK * blk);
+    if (!cfg.thr_pm || len <= 0) return;
+    auto put = [&](int p, int lab) { put_gene(v, p, lab); };
+    int pos = 0;
+    for (uint32_t e = 0;; ++e) {
+        const U4 w = philox((uint32_t)g, (uint32_t)k, (uint32_t)blk + 65536u * e, STREAM_MUT, k0, k1);
+        pos += mutation_skip(w.x, cfg);
+        if (pos >= len) break;
+        put(pos, draw_below(w.y, (uint32_t)cfg.N));
+        if (++pos >= len) break;
+        pos += mutation_skip(w.z, cfg);
+        if (pos >= len) break;
+        put(pos, draw_below(w.w, (uint32_t)cfg.N));
+        if (++pos >= len) break;
+    }
+}
+
+// Build child k from plan c: SUS parents (perm read here), crossover,
+// mutation; writes the child to dst (global, padded row of Np genes) and
+// sl.lab, and the changed genes X (against parent a) to sl.xs / xa / xc when
+// there are at most DELTA_X of them. Returns the number of changed genes
+// (all lanes) and parent a's index in *ia_out.
+__device__ int build_child(const uint16_t *cur, int ldp, int Np, const EvolveCfg &cfg,
+                           const ChildPlan &c, int k, uint32_t k0, uint32_t k1,
+                           const int32_t *__restrict__ perm, const uint64_t *__restrict__ prefix,
+                           uint16_t *__restrict__ dst, const GatherSlice &sl, int lane,
+                           int *ia_out)
+{
+    const int N = cfg.N, M = cfg.M, g = c.g;
+    const unsigned lt = (1u << lane) - 1u;
+    int par;
+    if (c.rank >= 0) {
+        par = perm[c.rank];
+    } else {
+        const uint32_t kp = lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M);
+        const uint32_t su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1).x;
+        const uint64_t W = __ldg(prefix + cfg.P - 1);
+        par = cfg.sus_tab ? sus_parent_tab(kp, su, W, M, cfg.P, cfg.inv_md, prefix, cfg.sus_tab,
+                                           perm, lane)
+                          : sus_parent_half(kp, su, W, M, cfg.P, cfg.inv_md, prefix, perm, lane);
+    }
+    const int ia = __shfl_sync(0xffffffffu, par, 0);
+    const int ib = __shfl_sync(0xffffffffu, par, 16);
+    *ia_out = ia;
+    const uint16_t *__restrict__ a = cur + (size_t)ia * ldp;
+    const uint16_t *__restrict__ b = cur + (size_t)ib * ldp;
+    int mode = 0, cut = N, q = 0;
+    if ((uint64_t)c.x0 < cfg.thr_pc) {
+        if ((uint64_t)c.x1 < cfg.thr_pkb) {
+            mode = 2;
+            q = draw_below(c.x2, (uint32_t)N);
+        } else {
+            mode = 1;
+            cut = 1 + draw_below(c.x2, (uint32_t)(N - 1));
+        }
+    }
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(a);
+    const uint4 *b4 = reinterpret_cast<const uint4 *>(b);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    uint4 *s4 = reinterpret_cast<uint4 *>(sl.lab);
+    const int nblk = Np / MUT_BLOCK;
+    int nx = 0;
+    for (int blk = lane; blk - lane < nblk; blk += 32) {
+        const bool act = blk < nblk;
+        uint4 av[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        uint4 bv[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        int aq = 0, bq = 0;
+        // every load of the block (and the anchor genes) issued together
+        if (act) {
+            av[0] = __ldg(a4 + 2 * blk);
+            av[1] = __ldg(a4 + 2 * blk + 1);
+            if (mode) {
+                bv[0] = __ldg(b4 + 2 * blk);
+                bv[1] = __ldg(b4 + 2 * blk + 1);
+            }
+        }
+        if (mode == 2) {
+            aq = __ldg(a + q);
+            bq = __ldg(b + q);
+        }
+        const uint32_t aw[8] = {av[0].x, av[0].y, av[0].z, av[0].w, av[1].x, av[1].y, av[1].z, av[1].w};
+        const uint32_t bw[8] = {bv[0].x, bv[0].y, bv[0].z, bv[0].w, bv[1].x, bv[1].y, bv[1].z, bv[1].w};
+        uint32_t v[8];
+        const int base = MUT_BLOCK * blk;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int j0 = base + 2 * w, j1 = j0 + 1;
+            const int a0 = (int)(aw[w] & 0xffffu), a1 = (int)(aw[w] >> 16);
+            const int b0 = (int)(bw[w] & 0xffffu), b1 = (int)(bw[w] >> 16);
+            int c0 = a0, c1 = a1;
+            if (mode == 1) {
+                if (j0 >= cut) c0 = b0;
+                if (j1 >= cut) c1 = b1;
+            } else if (mode == 2) {
+                if (b0 == bq) c0 = aq;
+                if (b1 == bq) c1 = aq;
+            }
+            v[w] = (uint32_t)c0 | ((uint32_t)c1 << 16);
+        }
+        // mutation: the planned draws of the first block, others drawn here
+        if (act) {
+            if (blk == lane && !c.mover) {
+                uint32_t mm = c.mmask;
+                int cnt = 0;
+                while (mm) {
+                    const int p = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const uint32_t lw = cnt < 2 ? c.mlab[0] : c.mlab[1];
+                    const int lab = (int)((lw >> ((cnt & 1) << 4)) & 0xffffu);
+                    ++cnt;
+                    put_gene(v, p, lab);
+                }
+            } else {
+                mutate_block(cfg, g, k, k0, k1, blk, v);
+            }
+        }
+        // genes past N are zero; the changed genes
+        uint32_t diff = 0u;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int j0 = base + 2 * w;
+            if (j0 >= N) v[w] = 0u;
+            else if (j0 + 1 >= N) v[w] &= 0xffffu;
+            const uint32_t x = v[w] ^ aw[w];
+            if (j0 < N && (x & 0xffffu)) diff |= 1u << (2 * w);
+            if (j0 + 1 < N && (x >> 16)) diff |= 1u << (2 * w + 1);
+        }
+        if (!act) diff = 0u;
+        // positions of this lane's changed genes in the list (warp scan)
+        const int cnt = __popc(diff);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int pos = nx + incl - cnt;
+        if (diff) {
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                if ((diff >> p) & 1u) {
+                    if (pos < DELTA_X) {
+                        const int hsh = (p & 1) << 4;
+                        sl.xs[pos] = (uint16_t)(base + p);
+                        sl.xa[pos] = (uint16_t)((aw[p >> 1] >> hsh) & 0xffffu);
+                        sl.xc[pos] = (uint16_t)((v[p >> 1] >> hsh) & 0xffffu);
+                    }
+                    ++pos;
+                }
+            }
+        }
+        nx += __shfl_sync(0xffffffffu, incl, 31);
+        if (act) {
+            const uint4 o0 = make_uint4(v[0], v[1], v[2], v[3]), o1 = make_uint4(v[4], v[5], v[6], v[7]);
+            d4[2 * blk] = o0;
+            d4[2 * blk + 1] = o1;
+            s4[2 * blk] = o0;
+            s4[2 * blk + 1] = o1;
+        }
+    }
+    (void)lt;
+    __syncwarp();
+    return nx;
+}
+
+// ---------------------------------------------------------------------------
+// Delta scoring of a child (sl.lab holds it, sl.xs / xa / xc its nx <=
+// DELTA_X changed genes) against its first parent a (d table row ta, Lfix
+// lfa, pair count npa): writes the child's d table row tc (a's row with the
+// touched clusters updated) and returns its Lfix and pair count. REG: the
+// table row (Np <= 512) passes through registers, eight 16-byte loads per
+// lane issued before the affected clusters are found and stored once they
+// are (the parent's d of those clusters taken from them on the way).
+// ---------------------------------------------------------------------------
+template <bool REG>
+__device__ void score_delta_warp(const GatherSlice &sl, int N, int Np, int nx,
                                  const long long *__restrict__ ta, long long lfa, long long npa,
                                  long long *__restrict__ tc, const int32_t *__restrict__ Dfix,
                                  int diag, const long long *__restrict__ ltab,
@@ -332,46 +595,17 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
                                  long long *np_out)
 {
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
-    const int X = DELTA_X;
-    // the genes that differ from a, with both labels (gene pairs, 32-bit loads)
-    int nx = 0;
-    {
-        const uint32_t *a2 = reinterpret_cast<const uint32_t *>(a_row);
-        const uint32_t *c2 = reinterpret_cast<const uint32_t *>(sl.lab);
-        const int npair = (N + 1) >> 1;
-        for (int m0 = 0; m0 < npair && nx <= X; m0 += 32) {
-            const int m = m0 + lane;
-            uint32_t av = 0, cv = 0;
-            if (m < npair) {
-                av = __ldg(a2 + m);
-                cv = c2[m];
-            }
-            const bool d0 = m < npair && ((av ^ cv) & 0xffffu) != 0;
-            const bool d1 = m < npair && 2 * m + 1 < N && ((av ^ cv) >> 16) != 0;
-            const unsigned b0 = __ballot_sync(FULL, d0), b1 = __ballot_sync(FULL, d1);
-            const int p0 = nx + __popc(b0 & lt), p1 = nx + __popc(b0) + __popc(b1 & lt);
-            if (d0 && p0 < X) {
-                sl.xs[p0] = (uint16_t)(2 * m);
-                sl.xa[p0] = (uint16_t)(av & 0xffffu);
-                sl.xc[p0] = (uint16_t)(cv & 0xffffu);
-            }
-            if (d1 && p1 < X) {
-                sl.xs[p1] = (uint16_t)(2 * m + 1);
-                sl.xa[p1] = (uint16_t)(av >> 16);
-                sl.xc[p1] = (uint16_t)(cv >> 16);
-            }
-            nx += __popc(b0) + __popc(b1);
-        }
-    }
-    if (nx > X) return false;
-    // the child's table starts as a copy of a's (16-byte vectors, eight loads
-    // in flight per lane); the touched clusters are overwritten below
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(ta);
-        int4 *dst = reinterpret_cast<int4 *>(tc);
-        const int nv = Np >> 1; // Np int64 entries
+    const longlong2 *ta2 = reinterpret_cast<const longlong2 *>(ta);
+    longlong2 *tc2 = reinterpret_cast<longlong2 *>(tc);
+    const int nv = Np >> 1; // 16-byte vectors of the row (two labels each)
+    longlong2 tv[8];
+    if (REG) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (lane + 32 * i < nv) tv[i] = __ldg(ta2 + lane + 32 * i);
+    } else {
 #pragma unroll 8
-        for (int v = lane; v < nv; v += 32) dst[v] = __ldg(src + v);
+        for (int v = lane; v < nv; v += 32) tc2[v] = __ldg(ta2 + v);
     }
     // no label affected yet; bitmap of the changed genes in the list space
     uint16_t *aslot = reinterpret_cast<uint16_t *>(sl.cnt);
@@ -379,7 +613,7 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
     for (int w = lane; w < (Np >> 1); w += 32) reinterpret_cast<uint32_t *>(aslot)[w] = 0xffffffffu;
     for (int w = lane; w < (Np >> 5); w += 32) isx[w] = 0u;
     __syncwarp();
-    for (int x = lane; x < nx; x += 32) atomicOr(&isx[sl.xs[x] >> 5], 1u << (sl.xs[x] & 31));
+    if (lane < nx) atomicOr(&isx[sl.xs[lane] >> 5], 1u << (sl.xs[lane] & 31));
     // the affected clusters: the old and new labels of X, each once
     int na = 0;
     for (int base = 0; base < 2 * nx; base += 32) {
@@ -397,6 +631,7 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
             sl.in_mask[k] = 0u;
             sl.out_mask[k] = 0u;
             sl.dacc[k] = 0;
+            sl.dold[k] = 0;
             sl.nnew[k] = 0;
             sl.um[k] = NO_SLOT;
         }
@@ -408,64 +643,107 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
         atomicOr(&sl.in_mask[aslot[sl.xc[lane]]], 1u << lane);
     }
     __syncwarp();
-    // members of the affected clusters in the child: counted, and those that
-    // stayed in place (U) listed in the member space
-    uint16_t *ulist = sl.mem;
-    int nu = 0;
-    for (int j0 = 0; j0 < N; j0 += 32) {
-        const int j = j0 + lane;
-        int k = NO_SLOT;
-        bool stay = false;
-        if (j < N) {
-            k = aslot[sl.lab[j]];
-            if (k != NO_SLOT) {
-                // 16-bit counts, two per 32-bit word (no count exceeds N)
-                atomicAdd(reinterpret_cast<unsigned *>(sl.nnew) + (k >> 1), 1u << ((k & 1) << 4));
-                stay = ((isx[j >> 5] >> (j & 31)) & 1u) == 0u;
-                if (stay) sl.um[k] = (uint16_t)j; // any one of them
+    if (REG) {
+        // the row arrives: the parent's d of the affected clusters to shared
+        // memory, and the row stored to the child unchanged (the touched
+        // clusters are overwritten at the end)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int v = lane + 32 * i;
+            if (v < nv) {
+                const int k0 = aslot[2 * v], k1 = aslot[2 * v + 1];
+                if (k0 != NO_SLOT) sl.dold[k0] = tv[i].x;
+                if (k1 != NO_SLOT) sl.dold[k1] = tv[i].y;
+                tc2[v] = tv[i];
             }
         }
-        const unsigned bs = __ballot_sync(FULL, stay);
-        if (stay) ulist[nu + __popc(bs & lt)] = (uint16_t)j;
-        nu += __popc(bs);
+    }
+    // members of the affected clusters in the child, two genes per lane and
+    // step: counted, and those that stayed in place (U) listed in the member space
+    uint16_t *ulist = sl.mem;
+    const uint32_t *lab2 = reinterpret_cast<const uint32_t *>(sl.lab);
+    unsigned *nn2 = reinterpret_cast<unsigned *>(sl.nnew);
+    int nu = 0;
+#pragma unroll 2
+    for (int j0 = 0; j0 < N; j0 += 64) {
+        const int j = j0 + 2 * lane;
+        int ka = NO_SLOT, kb = NO_SLOT;
+        bool sa = false, sb = false;
+        if (j < N) {
+            const uint32_t w = lab2[j >> 1];
+            const uint32_t xb = isx[j >> 5] >> (j & 31);
+            ka = aslot[w & 0xffffu];
+            if (j + 1 < N) kb = aslot[w >> 16];
+            if (ka != NO_SLOT) {
+                atomicAdd(nn2 + (ka >> 1), 1u << ((ka & 1) << 4));
+                sa = (xb & 1u) == 0u;
+                if (sa) sl.um[ka] = (uint16_t)j; // any one of them
+            }
+            if (kb != NO_SLOT) {
+                atomicAdd(nn2 + (kb >> 1), 1u << ((kb & 1) << 4));
+                sb = (xb & 2u) == 0u;
+                if (sb) sl.um[kb] = (uint16_t)(j + 1);
+            }
+        }
+        const unsigned ba = __ballot_sync(FULL, sa), bb = __ballot_sync(FULL, sb);
+        const int pa = nu + __popc(ba & lt) + __popc(bb & lt);
+        if (sa) ulist[pa] = (uint16_t)j;
+        if (sb) ulist[pa + (sa ? 1 : 0)] = (uint16_t)(j + 1);
+        nu += __popc(ba) + __popc(bb);
     }
     __syncwarp();
     // 2 [D(U_t, In_t) - D(U_t, Out_t)]: per member left in place, its row of D
-    // at the genes that joined or left its cluster
-    for (int e = lane; e < nu; e += 32) {
-        const int j = ulist[e];
-        const int k = aslot[sl.lab[j]];
-        const unsigned mi = sl.in_mask[k], mo = sl.out_mask[k];
-        unsigned m = mi | mo;
-        const int32_t *row = Dfix + (size_t)j * Np;
-        long long s = 0;
-        while (m) {
-            int32_t v[4];
-            unsigned bit[4];
+    // at the genes that joined or left its cluster; two members per lane and
+    // step, four gathers each in flight
+    for (int e0 = lane; e0 < nu; e0 += 64) {
+        int jj[2], kk[2];
+        unsigned mi[2], mm[2];
+        long long s[2] = {0, 0};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                bit[u] = m & (~m + 1u);
-                m ^= bit[u];
-                v[u] = bit[u] ? __ldg(row + sl.xs[__ffs(bit[u]) - 1]) : 0;
+        for (int h = 0; h < 2; ++h) {
+            const int e = e0 + 32 * h;
+            jj[h] = e < nu ? (int)ulist[e] : 0;
+            kk[h] = e < nu ? (int)aslot[sl.lab[jj[h]]] : 0;
+            mi[h] = e < nu ? sl.in_mask[kk[h]] : 0u;
+            mm[h] = e < nu ? (mi[h] | sl.out_mask[kk[h]]) : 0u;
+        }
+        while (mm[0] | mm[1]) {
+            int32_t val[2][4];
+            unsigned bit[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int32_t *row = Dfix + (size_t)jj[h] * Np;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    bit[h][u] = mm[h] & (~mm[h] + 1u);
+                    mm[h] ^= bit[h][u];
+                    val[h][u] = bit[h][u] ? __ldg(row + sl.xs[__ffs(bit[h][u]) - 1]) : 0;
+                }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s += (bit[u] & mi) ? (long long)v[u] : -(long long)v[u];
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    s[h] += (bit[h][u] & mi[h]) ? (long long)val[h][u] : -(long long)val[h][u];
         }
-        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[k]), (unsigned long long)(2 * s));
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (e0 + 32 * h < nu)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kk[h]]),
+                          (unsigned long long)(2 * s[h]));
     }
     // D(In_t, In_t) - D(Out_t, Out_t): per changed gene, its row at the genes
     // that joined its new cluster with it and at those that left its old one
     if (lane < nx) {
-        const int x = lane;
-        const int kin = aslot[sl.xc[x]], kout = aslot[sl.xa[x]];
-        const int32_t *row = Dfix + (size_t)sl.xs[x] * Np;
+        const int kin = aslot[sl.xc[lane]], kout = aslot[sl.xa[lane]];
+        const int32_t *row = Dfix + (size_t)sl.xs[lane] * Np;
         long long si = 0, so = 0;
         for (unsigned m = sl.in_mask[kin]; m; m &= m - 1) si += __ldg(row + sl.xs[__ffs(m) - 1]);
         for (unsigned m = sl.out_mask[kout]; m; m &= m - 1) so += __ldg(row + sl.xs[__ffs(m) - 1]);
         atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kin]), (unsigned long long)si);
         atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kout]), (unsigned long long)(-so));
     }
-    __syncwarp(); // also orders the table copy above before the writes below
+    __syncwarp(); // also orders the table copy before the writes below
     // the touched terms: new minus old
     long long dl = 0, dp = 0;
     for (int k = lane; k < na; k += 32) {
@@ -475,18 +753,17 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
         const int no = nn - __popc(mi) + __popc(mo);
         long long dold = 0;
         if (no >= 2) {
-            dold = __ldg(ta + t);
+            dold = REG ? sl.dold[k] : __ldg(ta + t);
         } else if (no == 1 && diag) { // a singleton's d is its own D_jj
             const int m = mo ? (int)sl.xs[__ffs(mo) - 1] : (int)sl.um[k];
             dold = Dfix[(size_t)m * (Np + 1)];
         }
         const long long dnew = dold + sl.dacc[k];
-        if (nn >= 2) {
-            dl += cluster_term_q40(nn, dnew, ltab, kfix);
-            tc[t] = dnew;
-        }
-        if (no >= 2) dl -= cluster_term_q40(no, dold, ltab, kfix);
+        const long long tn = nn >= 2 ? cluster_term(nn, dnew, ltab, kfix) : 0;
+        const long long to = no >= 2 ? cluster_term(no, dold, ltab, kfix) : 0;
+        dl += tn - to;
         dp += (long long)(nn * (nn - 1) / 2) - (long long)(no * (no - 1) / 2);
+        if (nn >= 2) tc[t] = dnew;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -496,7 +773,6 @@ __device__ bool score_delta_warp(const GatherSlice &sl, int N, int Np,
     __syncwarp();
     *lf_out = lfa + dl;
     *np_out = npa + dp;
-    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -560,24 +836,26 @@ __global__ void __launch_bounds__(256, 4)
 // into global memory and its shared slice, then scores it: an elite keeps its
 // parent's score; a child is scored by delta from its first parent, or from
 // scratch when too many genes changed. b: the buffer of the current
-// generation g (g & 1); the next one is written to 1 - b.
+// generation g (g & 1); the next one is written to 1 - b. plan: the child's
+// draws for generation g (slot >= E).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *nxt,
-                                                const EvolveCfg &cfg, int g, uint32_t k0,
-                                                uint32_t k1, int slot,
+                                                const EvolveCfg &cfg, const ChildPlan &plan,
+                                                uint32_t k0, uint32_t k1, int slot,
                                                 const int32_t *__restrict__ perm,
                                                 const uint64_t *__restrict__ prefix, int Np,
                                                 const int32_t *__restrict__ Dfix, int diag,
                                                 const double *__restrict__ logtab,
                                                 double *__restrict__ L, const ScoreTab &tab,
                                                 const GatherSlice &sl, int lane,
-                                                unsigned long long *pairs_out,
-                                                const SusPre *pre = nullptr)
+                                                unsigned long long *pairs_out)
 {
     const int N = cfg.N, ldp = cfg.ldp;
-    const int b = g & 1, nb = b ^ 1;
+    const int b = plan.g & 1, nb = b ^ 1;
     uint16_t *dst = nxt + (size_t)slot * ldp;
     long long *tc = tab.d[nb] + (size_t)slot * tab.ldt;
+    const long long *ltab = reinterpret_cast<const long long *>(logtab);
+    const long long *kfix = kfix_of(logtab);
     long long lf, np;
     if (slot < cfg.E) {
         // elite: labels, table and score of the parent, unchanged
@@ -592,15 +870,21 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
         np = tab.np[b][src_i];
     } else {
         const int k = slot - cfg.E;
-        const int ia = child_genes<uint16_t>(cur, ldp, N, cfg, g, k, k0, k1, perm, prefix, nullptr,
-                                             dst, sl.lab, lane, pre);
+        int ia;
+        const int nx = build_child(cur, ldp, Np, cfg, plan, k, k0, k1, perm, prefix, dst, sl, lane,
+                                   &ia);
+        const long long lfa = tab.lf[b][ia], npa = tab.np[b][ia];
         const long long *ta = tab.d[b] + (size_t)ia * tab.ldt;
-        if (!score_delta_warp(sl, N, Np, cur + (size_t)ia * ldp, ta, tab.lf[b][ia],
-                              tab.np[b][ia], tc, Dfix, diag,
-                              reinterpret_cast<const long long *>(logtab), kfix_of(logtab), lane,
-                              &lf, &np))
-            lf = score_full_warp(sl, N, Np, Dfix, diag, reinterpret_cast<const long long *>(logtab),
-                                 kfix_of(logtab), lane, tc, &np);
+        if (nx <= DELTA_X) {
+            if (Np <= 512)
+                score_delta_warp<true>(sl, N, Np, nx, ta, lfa, npa, tc, Dfix, diag, ltab, kfix,
+                                       lane, &lf, &np);
+            else
+                score_delta_warp<false>(sl, N, Np, nx, ta, lfa, npa, tc, Dfix, diag, ltab, kfix,
+                                        lane, &lf, &np);
+        } else {
+            lf = score_full_warp(sl, N, Np, Dfix, diag, ltab, kfix, lane, tc, &np);
+        }
     }
     if (lane == 0) {
         L[slot] = lfix_to_double(lf);
@@ -610,38 +894,47 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     }
 }
 
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(128, 7)
     gather_generation_kernel(const uint16_t *pop0, const uint16_t *pop1, uint16_t *next0,
                              uint16_t *next1, EvolveCfg cfg, const int32_t *__restrict__ perm,
                              const uint64_t *__restrict__ prefix, int Np,
                              const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
                              const double *__restrict__ logtab, double *__restrict__ L,
-                             const DevState *__restrict__ st, unsigned long long *__restrict__ pairs,
-                             ScoreTab tab)
+                             const DevState *__restrict__ st,
+                             unsigned long long *__restrict__ pairs, ScoreTab tab)
 {
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int slot = blockIdx.x * nw + warp;
     if (slot >= cfg.P) return;
-    // the SUS loads that depend on no generation (fixed tables written at the
-    // start of the run), issued before the wait below
+    // the run's Philox key (written when the run started, long before)
+    const uint32_t k0 = st->k0, k1 = st->k1;
+    // Everything of the child that depends on neither parent, drawn before the
+    // wait below for the generation read from the state now (the selection
+    // writes it before it lets this kernel be scheduled; if the value read is
+    // stale, the draws are made again after the wait): the SUS brackets of
+    // the fixed rank prefix and the pointer's rank, the crossover words, the
+    // mutations of the lane's first block.
     SusPre pre;
     const bool use_pre = cfg.sus_tab != nullptr && slot >= cfg.E;
     if (use_pre) pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
-    // launched as a programmatic dependent of the selection (which lets it be
-    // scheduled while its last CTA finishes): wait for that grid before reading
-    // perm and the state. (Letting the selection in turn be scheduled early,
-    // from here, measured slower: its waiting CTAs cost the generation more
-    // than the launch gap they hide.)
+    const int g_hint = *reinterpret_cast<volatile const int *>(&st->gen);
+    ChildPlan plan;
+    if (slot >= cfg.E)
+        plan = plan_child(cfg, g_hint, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
+    // launched as a programmatic dependent of the selection: wait for that grid
+    // before reading perm and the state
     griddep_wait();
     if (st->done) return;
     const int g = st->gen;
+    if (slot >= cfg.E && g != plan.g)
+        plan = plan_child(cfg, g, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
+    plan.g = g;
     const uint16_t *cur = (g & 1) ? pop1 : pop0;
     uint16_t *nxt = (g & 1) ? next1 : next0;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
-    generation_slot(cur, nxt, cfg, g, st->k0, st->k1, slot, perm, prefix, Np, Dfix, *diag_flag,
-                    logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr,
-                    use_pre ? &pre : nullptr);
+    generation_slot(cur, nxt, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix, *diag_flag, logtab,
+                    L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -650,7 +943,7 @@ __global__ void __launch_bounds__(256, 4)
 // first); the CTAs stride over the items. Runs whose state is done are
 // skipped. Per slot the work is exactly that of gather_generation_kernel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(256, 3)
     fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
                             EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
                             const double *__restrict__ logtab, int Np_max, int prop)
@@ -675,7 +968,16 @@ __global__ void __launch_bounds__(512, 2)
         uint16_t *nxt = (g & 1) ? r.pop0 : r.pop1;
         const uint64_t *prefix = prop ? r.work_prefix : rank_prefix;
         const GatherSlice sl = gather_slice(slice, r.Np);
-        generation_slot(cur, nxt, cfg, g, st->k0, st->k1, slot, r.perm, prefix, r.Np, r.Dfix,
+        ChildPlan plan;
+        plan.g = g;
+        if (slot >= cfg.E) {
+            SusPre pre;
+            const bool use_pre = !prop && cfg.sus_tab != nullptr;
+            if (use_pre)
+                pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
+            plan = plan_child(cfg, g, slot - cfg.E, st->k0, st->k1, use_pre ? &pre : nullptr, lane);
+        }
+        generation_slot(cur, nxt, cfg, plan, st->k0, st->k1, slot, r.perm, prefix, r.Np, r.Dfix,
                         *r.diag, logtab, r.L, r.tab, sl, lane, nullptr);
         __syncwarp();
     }
@@ -728,7 +1030,7 @@ int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2
 
 int fleet_max_warps(int Np_max)
 {
-    int nw = 16;
+    int nw = 8; // the kernel's launch bounds: 256 threads (80 registers each)
     while (nw > 1 && nw * gather_slice_bytes(Np_max) > (size_t)200 * 1024) nw >>= 1;
     return nw;
 }
@@ -744,7 +1046,7 @@ int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const Evo
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
                             int warps, int ctas, int prop, cudaStream_t s, bool pdl)
 {
-    if (warps < 1 || warps > 16 || ctas < 1)
+    if (warps < 1 || warps > 8 || ctas < 1)
         return set_error(GPGA_ERR_ARG, "fleet generation: %d warps x %d CTAs", warps, ctas);
     const size_t smem = warps * gather_slice_bytes(Np_max);
     GPGA_CUDA(launch_pdl(fleet_generation_kernel, dim3(ctas), dim3(32 * warps), smem, s, pdl, runs,
