@@ -308,7 +308,7 @@ int enqueue_generation(gpga_ga *h, cudaEvent_t *evs, bool after_kernel)
     e.thr_pc = prob_threshold(h->prm.pc);
     e.thr_pkb = prob_threshold(h->prm.pkb);
     set_mutation(&e, h->prm.pm);
-    e.inv_md = 1.0 / ((double)h->M * 4294967296.0);
+    set_sus_divisor(&e, h->M);
     e.k0 = h->k0;
     e.k1 = h->k1;
     e.gen = 0;
@@ -622,7 +622,7 @@ GPGA_API int ga_evolve(const int32_t *pop, const double *L, int N, const gpga_pa
         e.thr_pc = prob_threshold(p->pc);
         e.thr_pkb = prob_threshold(p->pkb);
         set_mutation(&e, p->pm);
-        e.inv_md = 1.0 / ((double)M * 4294967296.0);
+        set_sus_divisor(&e, M);
         e.k0 = sc.k0;
         e.k1 = sc.k1;
         e.gen = generation;

@@ -165,7 +165,7 @@ static EvolveCfg fleet_evolve_cfg(const Fleet *f)
     e.thr_pc = prob_threshold(f->prm.pc);
     e.thr_pkb = prob_threshold(f->prm.pkb);
     set_mutation(&e, f->prm.pm);
-    e.inv_md = 1.0 / ((double)f->M * 4294967296.0);
+    set_sus_divisor(&e, f->M);
     e.k0 = 0;
     e.k1 = 0;
     e.gen = 0;

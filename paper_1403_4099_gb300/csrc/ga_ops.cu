@@ -17,6 +17,19 @@ uint64_t prob_threshold(double p)
     return (uint64_t)floor(p * 4294967296.0);
 }
 
+void set_sus_divisor(EvolveCfg *cfg, int M)
+{
+    int l = 0;
+    while ((1ll << l) < (long long)M) ++l; // l = ceil(log2 M)
+    const int s = 60 + l;
+    // magic = ceil(2^s / M) < 2^61, by long division in 128 bits
+    const unsigned __int128 num = (unsigned __int128)1 << s;
+    unsigned __int128 q = num / (unsigned)M;
+    if (q * (unsigned)M != num) q += 1;
+    cfg->m_magic = (uint64_t)q;
+    cfg->m_shift = s;
+}
+
 void set_mutation(EvolveCfg *cfg, double pm)
 {
     cfg->thr_pm = prob_threshold(pm);
@@ -142,6 +155,7 @@ __global__ void state_init_kernel(DevState *st, unsigned long long *ts0, uint32_
     st->lsum = 0;
     st->best = 0.0;
     st->mean = 0.0;
+    st->gnext = 0;
     if (ts0) {
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -607,17 +621,11 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
         }
     }
     __syncthreads();
-    // The next generation kernel (a programmatic dependent) may be scheduled
-    // once every CTA has let it: the CTA that holds rank 0 does so only after
-    // it has written the new generation into the state (the kernel draws its
-    // children for that value before it waits for this grid, and draws them
-    // again if the value it read was stale); everything else it reads after
-    // its wait, when this grid has completed.
+    // the next generation kernel (a programmatic dependent) may be scheduled
+    // now; it waits for this grid to complete before it reads anything written here
+    griddep_launch();
     const int bidx = s_best;
-    if (!st || bidx < 0) {
-        griddep_launch();
-        return;
-    }
+    if (!st || bidx < 0) return;
     const int g = st->gen + cfg.gen_off;
     if (cfg.record && ring) {
         const LabT *src = ((g & 1) ? pop1 : pop0) + (size_t)bidx * cfg.ldp;
@@ -643,10 +651,7 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
         }
         st->done = done;
         st->mean = (double)lsum * 9.313225746154785e-10 / (double)P;
-        __threadfence();
     }
-    __syncthreads();
-    griddep_launch();
 }
 
 // selection by counting for rank scaling (one launch, no ticket), else the

@@ -360,7 +360,7 @@ __device__ __forceinline__ ChildPlan plan_child(const EvolveCfg &cfg, int g, int
     if (pre && __all_sync(0xffffffffu, pre->hi - pre->lo <= 16)) {
         const uint32_t kp = lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M);
         const uint32_t su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1).x;
-        const uint64_t x = sus_pointer(kp, su, pre->W, (uint32_t)M, cfg.inv_md);
+        const uint64_t x = sus_pointer(kp, su, pre->W, cfg.m_magic, cfg.m_shift);
         const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
         const bool le = (lane & 15) < pre->hi - pre->lo && pre->cand <= x;
         c.rank = pre->lo + __popc(__ballot_sync(0xffffffffu, le) & half);
@@ -449,9 +449,10 @@ __device__ int build_child(const uint16_t *cur, int ldp, int Np, const EvolveCfg
         const uint32_t kp = lane < 16 ? (uint32_t)k : (uint32_t)((k + M / 2) % M);
         const uint32_t su = philox((uint32_t)g, 0u, 0u, STREAM_SUS, k0, k1).x;
         const uint64_t W = __ldg(prefix + cfg.P - 1);
-        par = cfg.sus_tab ? sus_parent_tab(kp, su, W, M, cfg.P, cfg.inv_md, prefix, cfg.sus_tab,
-                                           perm, lane)
-                          : sus_parent_half(kp, su, W, M, cfg.P, cfg.inv_md, prefix, perm, lane);
+        par = cfg.sus_tab ? sus_parent_tab(kp, su, W, M, cfg.P, cfg.m_magic, cfg.m_shift, prefix,
+                                           cfg.sus_tab, perm, lane)
+                          : sus_parent_half(kp, su, W, M, cfg.P, cfg.m_magic, cfg.m_shift, prefix,
+                                            perm, lane);
     }
     const int ia = __shfl_sync(0xffffffffu, par, 0);
     const int ib = __shfl_sync(0xffffffffu, par, 16);
@@ -900,8 +901,8 @@ __global__ void __launch_bounds__(128, 7)
                              const uint64_t *__restrict__ prefix, int Np,
                              const int32_t *__restrict__ Dfix, const int *__restrict__ diag_flag,
                              const double *__restrict__ logtab, double *__restrict__ L,
-                             const DevState *__restrict__ st,
-                             unsigned long long *__restrict__ pairs, ScoreTab tab)
+                             DevState *__restrict__ st, unsigned long long *__restrict__ pairs,
+                             ScoreTab tab)
 {
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -918,7 +919,7 @@ __global__ void __launch_bounds__(128, 7)
     SusPre pre;
     const bool use_pre = cfg.sus_tab != nullptr && slot >= cfg.E;
     if (use_pre) pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
-    const int g_hint = *reinterpret_cast<volatile const int *>(&st->gen);
+    const int g_hint = *reinterpret_cast<volatile const int *>(&st->gnext);
     ChildPlan plan;
     if (slot >= cfg.E)
         plan = plan_child(cfg, g_hint, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
@@ -927,6 +928,7 @@ __global__ void __launch_bounds__(128, 7)
     griddep_wait();
     if (st->done) return;
     const int g = st->gen;
+    if (slot == 0 && lane == 0) st->gnext = g + 1;
     if (slot >= cfg.E && g != plan.g)
         plan = plan_child(cfg, g, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
     plan.g = g;
@@ -1015,7 +1017,7 @@ int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, in
 int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2,
                              const EvolveCfg &cfg, const int32_t *perm, const uint64_t *prefix,
                              int Np, const int32_t *Dfix, const int *diag_flag,
-                             const double *logtab, double *L, const DevState *st,
+                             const double *logtab, double *L, DevState *st,
                              unsigned long long *pairs, const ScoreTab &tab, bool pdl,
                              cudaStream_t s)
 {

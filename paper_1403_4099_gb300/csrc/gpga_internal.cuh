@@ -113,6 +113,10 @@ struct DevState {
     double mean;  // population mean L
     uint32_t k0, k1; // Philox key (the run's seed), read by the graphed kernels
     long long lsum;  // fixed-point (2^-30) sum of the generation's fitness, for the mean
+    int gnext;       // the generation the next generation kernel starts from, as a hint
+                     // it may read before its grid wait (written by the generation
+                     // kernel after its wait, and at the start of a run)
+    int pad_;
 };
 
 // label storage traits: the handle stores labels as uint16 (N <= 65535), the
@@ -456,7 +460,8 @@ constexpr int MUT_BLOCK = 16;
 
 struct EvolveCfg {
     int P, E, M, N, ldp;
-    double inv_md; // 1 / (M 2^32), for the SUS pointer estimate
+    uint64_t m_magic; // exact division by M of values below 2^60 (set_sus_divisor)
+    int m_shift;
     uint64_t thr_pc, thr_pkb, thr_pm;
     uint32_t k0, k1;
     int gen; // stateless generation (when st == nullptr)
@@ -466,6 +471,8 @@ struct EvolveCfg {
 
 // fill cfg->thr_pm and cfg->gap for mutation probability pm (host)
 void set_mutation(EvolveCfg *cfg, double pm);
+// fill cfg->m_magic / m_shift for the M pointers of SUS (host)
+void set_sus_divisor(EvolveCfg *cfg, int M);
 
 // prefix: inclusive prefix of the scaled weights by rank (RANK: the fixed
 // table; PROP: the work prefix written by finalize); parents_out optional
@@ -487,30 +494,21 @@ void set_mutation(EvolveCfg *cfg, double pm);
 // stream gene pairs. Writes dst (global) and, if given, lab_s (shared).
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
-// SUS pointer x_k = floor((k 2^32 + u) W / (M 2^32)), exact: an FP64 estimate
-// (off by at most a unit or two) corrected against the exact 128-bit numerator
-// A = (k 2^32 + u) W and divisor D = M 2^32 (no integer division).
-// inv_md = 1 / (M 2^32) rounded.
+// SUS pointer x_k = floor((k 2^32 + u) W / (M 2^32)), exact, on the integer
+// pipe: y = (k 2^32 + u) W as a 128-bit product, Y = floor(y / 2^32) (< 2^60
+// for k < M <= 2^14 and W <= P 2^32 <= 2^46), x_k = floor(Y / M) by the
+// multiply-shift division of set_sus_divisor: magic = ceil(2^(60 + l) / M),
+// l = ceil(log2 M), x = (Y magic) >> (60 + l), exact for every Y < 2^60
+// because the error term Y (magic M - 2^(60 + l)) / (M 2^(60 + l)) stays below 1/M.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t W, uint32_t M,
-                                                double inv_md)
+__device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t W, uint64_t magic,
+                                                int shift)
 {
-    typedef unsigned __int128 u128;
     const uint64_t num = ((uint64_t)k << 32) | u;
-    const u128 A = (u128)num * W;
-    const u128 D = (u128)M << 32;
-    double est = (double)num * (double)W * inv_md;
-    uint64_t x = est > 0.0 ? (uint64_t)est : 0ull;
-    u128 X = (u128)x * D;
-    while (X > A) {
-        --x;
-        X -= D;
-    }
-    while (A - X >= D) {
-        ++x;
-        X += D;
-    }
-    return x;
+    const uint64_t ylo = num * W, yhi = __umul64hi(num, W);
+    const uint64_t Y = (yhi << 32) | (ylo >> 32);
+    const uint64_t plo = Y * magic, phi = __umul64hi(Y, magic);
+    return shift >= 64 ? (phi >> (shift - 64)) : ((phi << (64 - shift)) | (plo >> shift));
 }
 
 // Parent of SUS pointer k for each half-warp (lanes 0-15 and 16-31 may ask
@@ -519,11 +517,11 @@ __device__ __forceinline__ uint64_t sus_pointer(uint32_t k, uint32_t u, uint64_t
 // and counts those <= x_k: three dependent loads for P = 4096 instead of
 // twelve), then perm[r]. All lanes of the warp call; returns the half's parent.
 __device__ __forceinline__ int sus_parent_half(uint32_t k, uint32_t u, uint64_t W, int M, int P,
-                                               double inv_md,
+                                               uint64_t magic, int shift,
                                                const uint64_t *__restrict__ prefix,
                                                const int32_t *__restrict__ perm, int lane)
 {
-    const uint64_t x = sus_pointer(k, u, W, (uint32_t)M, inv_md);
+    const uint64_t x = sus_pointer(k, u, W, magic, shift);
     const int l = lane & 15;
     const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
     int top = 1;
@@ -547,19 +545,20 @@ __device__ __forceinline__ int sus_parent_half(uint32_t k, uint32_t u, uint64_t 
 // replaces the 16-ary search. A wider bracket (very few pointers for the
 // ranks) takes the general search.
 __device__ __forceinline__ int sus_parent_tab(uint32_t k, uint32_t u, uint64_t W, int M, int P,
-                                              double inv_md, const uint64_t *__restrict__ prefix,
+                                              uint64_t magic, int shift,
+                                              const uint64_t *__restrict__ prefix,
                                               const int32_t *__restrict__ tab,
                                               const int32_t *__restrict__ perm, int lane)
 {
     const int lo = __ldg(tab + k), hi = __ldg(tab + k + 1);
     if (__all_sync(0xffffffffu, hi - lo <= 16)) {
-        const uint64_t x = sus_pointer(k, u, W, (uint32_t)M, inv_md);
+        const uint64_t x = sus_pointer(k, u, W, magic, shift);
         const int l = lane & 15;
         const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
         const bool le = l < hi - lo && __ldg(prefix + lo + l) <= x;
         return perm[lo + __popc(__ballot_sync(0xffffffffu, le) & half)];
     }
-    return sus_parent_half(k, u, W, M, P, inv_md, prefix, perm, lane);
+    return sus_parent_half(k, u, W, M, P, magic, shift, prefix, perm, lane);
 }
 
 // The loads of sus_parent_tab that do not depend on the generation: the bracket
@@ -655,14 +654,15 @@ __device__ __forceinline__ int child_genes(const LabT *cur, int ldp, int N, cons
     int par;
     if (pre && __all_sync(0xffffffffu, pre->hi - pre->lo <= 16)) {
         // sus_parent_tab with its loads already in registers
-        const uint64_t x = sus_pointer(kp, su.x, W, (uint32_t)M, cfg.inv_md);
+        const uint64_t x = sus_pointer(kp, su.x, W, cfg.m_magic, cfg.m_shift);
         const unsigned half = lane < 16 ? 0x0000ffffu : 0xffff0000u;
         const bool le = (lane & 15) < pre->hi - pre->lo && pre->cand <= x;
         par = perm[pre->lo + __popc(__ballot_sync(0xffffffffu, le) & half)];
     } else {
-        par = cfg.sus_tab ? sus_parent_tab(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix, cfg.sus_tab,
-                                           perm, lane)
-                          : sus_parent_half(kp, su.x, W, M, cfg.P, cfg.inv_md, prefix, perm, lane);
+        par = cfg.sus_tab ? sus_parent_tab(kp, su.x, W, M, cfg.P, cfg.m_magic, cfg.m_shift, prefix,
+                                           cfg.sus_tab, perm, lane)
+                          : sus_parent_half(kp, su.x, W, M, cfg.P, cfg.m_magic, cfg.m_shift, prefix,
+                                            perm, lane);
     }
     const int ia = __shfl_sync(0xffffffffu, par, 0);
     const int ib = __shfl_sync(0xffffffffu, par, 16);
@@ -755,7 +755,7 @@ int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, in
 int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2,
                              const EvolveCfg &cfg, const int32_t *perm, const uint64_t *prefix,
                              int Np, const int32_t *Dfix, const int *diag_flag,
-                             const double *logtab, double *L, const DevState *st,
+                             const double *logtab, double *L, DevState *st,
                              unsigned long long *pairs, const ScoreTab &tab, bool pdl,
                              cudaStream_t s);
 // bytes of one row of the d table for padded gene count Np
