@@ -172,7 +172,7 @@ __device__ __forceinline__ double lfix_to_double(long long lf) { return dbl_scal
 // 1) / 2 in *npairs_out (all lanes). Dfix: Np x Np int32, D = 1 - C in fixed
 // point 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. trow (optional): the
 // individual's row of the d table, written where n_s >= 2.
-__device__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
+__device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
                                      const int32_t *__restrict__ Dfix, int diag,
                                      const long long *__restrict__ ltab,
                                      const long long *__restrict__ kfix, int lane,
@@ -350,8 +350,9 @@ struct ChildPlan {
     int mover;
 };
 
-__device__ __forceinline__ ChildPlan plan_child(const EvolveCfg &cfg, int g, int k, uint32_t k0,
-                                                uint32_t k1, const SusPre *pre, int lane)
+__device__ __forceinline__ ChildPlan plan_child(const EvolveCfg &cfg, int N, int g, int k,
+                                                uint32_t k0, uint32_t k1, const SusPre *pre,
+                                                int lane)
 {
     ChildPlan c;
     c.g = g;
@@ -372,7 +373,7 @@ __device__ __forceinline__ ChildPlan plan_child(const EvolveCfg &cfg, int g, int
     c.mmask = 0u;
     c.mlab[0] = c.mlab[1] = 0u;
     c.mover = 0;
-    const int len = min(MUT_BLOCK, cfg.N - MUT_BLOCK * lane);
+    const int len = min(MUT_BLOCK, N - MUT_BLOCK * lane);
     if (cfg.thr_pm && len > 0) {
         int pos = 0, cnt = 0;
         auto rec = [&](int p, int v) {
@@ -387,44 +388,36 @@ __device__ __forceinline__ ChildPlan plan_child(const EvolveCfg &cfg, int g, int
                                 k0, k1);
             pos += mutation_skip(w.x, cfg);
             if (pos >= len) break;
-            rec(pos, draw_below(w.y, (uint32_t)cfg.N));
+            rec(pos, draw_below(w.y, (uint32_t)N));
             if (++pos >= len) break;
             pos += mutation_skip(w.z, cfg);
             if (pos >= len) break;
-            rec(pos, draw_below(w.w, (uint32_t)cfg.N));
+            rec(pos, draw_below(w.w, (uint32_t)N));
             if (++pos >= len) break;
         }
     }
     return c;
 }
 
-// gene p (0..15, run time) of the block in v (8 words) set to lab; the words
-// are selected with compile-time indices so that v stays in registers
-__device__ __forceinline__ void put_gene(uint32_t v[8], int p, int lab)
+// mutations of block blk of child k (g), written into the block's 16 labels
+// in shared memory (the lane's own block: no other lane touches it)
+__device__ __forceinline__ void mutate_block_smem(const EvolveCfg &cfg, int N, int g, int k,
+                                                  uint32_t k0, uint32_t k1, int blk,
+                                                  uint16_t *lab_s)
 {
-    const uint32_t hsh = (uint32_t)(p & 1) << 4;
-#pragma unroll
-    for (int w = 0; w < 8; ++w)
-        if (w == (p >> 1)) v[w] = (v[w] & ~(0xffffu << hsh)) | ((uint32_t)lab << hsh);
-}
-
-// mutations of block blk of child k (g), applied to the 16 genes in v (8 words)
-__device__ __forceinline__ void mutate_block(const EvolveCfg &cfg, int g, int k, uint32_t k0,
-                                             uint32_t k1, int blk, uint32_t v[8])
-{
-    const int len = min(MUT_BLOCK, cfg.N - MUT_BLOCK * blk);
+    const int len = min(MUT_BLOCK, N - MUT_BLOCK * blk);
     if (!cfg.thr_pm || len <= 0) return;
-    auto put = [&](int p, int lab) { put_gene(v, p, lab); };
+    uint16_t *b = lab_s + MUT_BLOCK * blk;
     int pos = 0;
     for (uint32_t e = 0;; ++e) {
         const U4 w = philox((uint32_t)g, (uint32_t)k, (uint32_t)blk + 65536u * e, STREAM_MUT, k0, k1);
         pos += mutation_skip(w.x, cfg);
         if (pos >= len) break;
-        put(pos, draw_below(w.y, (uint32_t)cfg.N));
+        b[pos] = (uint16_t)draw_below(w.y, (uint32_t)N);
         if (++pos >= len) break;
         pos += mutation_skip(w.z, cfg);
         if (pos >= len) break;
-        put(pos, draw_below(w.w, (uint32_t)cfg.N));
+        b[pos] = (uint16_t)draw_below(w.w, (uint32_t)N);
         if (++pos >= len) break;
     }
 }
@@ -434,13 +427,14 @@ __device__ __forceinline__ void mutate_block(const EvolveCfg &cfg, int g, int k,
 // sl.lab, and the changed genes X (against parent a) to sl.xs / xa / xc when
 // there are at most DELTA_X of them. Returns the number of changed genes
 // (all lanes) and parent a's index in *ia_out.
-__device__ int build_child(const uint16_t *cur, int ldp, int Np, const EvolveCfg &cfg,
+__device__ __forceinline__ int build_child(const uint16_t *cur, int N, int ldp, int Np,
+                                           const EvolveCfg &cfg,
                            const ChildPlan &c, int k, uint32_t k0, uint32_t k1,
                            const int32_t *__restrict__ perm, const uint64_t *__restrict__ prefix,
                            uint16_t *__restrict__ dst, const GatherSlice &sl, int lane,
                            int *ia_out)
 {
-    const int N = cfg.N, M = cfg.M, g = c.g;
+    const int M = cfg.M, g = c.g;
     const unsigned lt = (1u << lane) - 1u;
     int par;
     if (c.rank >= 0) {
@@ -512,21 +506,33 @@ __device__ int build_child(const uint16_t *cur, int ldp, int Np, const EvolveCfg
             }
             v[w] = (uint32_t)c0 | ((uint32_t)c1 << 16);
         }
-        // mutation: the planned draws of the first block, others drawn here
+        // mutation: the planned draws of the first block (positions known at
+        // compile time after unrolling, so v stays in registers); other blocks,
+        // and a first block with more than four mutations, drawn here through
+        // the lane's own labels in shared memory
         if (act) {
             if (blk == lane && !c.mover) {
-                uint32_t mm = c.mmask;
-                int cnt = 0;
-                while (mm) {
-                    const int p = __ffs(mm) - 1;
-                    mm &= mm - 1;
-                    const uint32_t lw = cnt < 2 ? c.mlab[0] : c.mlab[1];
-                    const int lab = (int)((lw >> ((cnt & 1) << 4)) & 0xffffu);
-                    ++cnt;
-                    put_gene(v, p, lab);
+                const uint32_t mm = c.mmask;
+                if (mm) {
+                    int cnt = 0;
+#pragma unroll
+                    for (int p = 0; p < 16; ++p) {
+                        if ((mm >> p) & 1u) {
+                            const uint32_t lw = cnt < 2 ? c.mlab[0] : c.mlab[1];
+                            const uint32_t lab = (lw >> ((cnt & 1) << 4)) & 0xffffu;
+                            ++cnt;
+                            const uint32_t hsh = (uint32_t)(p & 1) << 4;
+                            v[p >> 1] = (v[p >> 1] & ~(0xffffu << hsh)) | (lab << hsh);
+                        }
+                    }
                 }
-            } else {
-                mutate_block(cfg, g, k, k0, k1, blk, v);
+            } else if (cfg.thr_pm) {
+                s4[2 * blk] = make_uint4(v[0], v[1], v[2], v[3]);
+                s4[2 * blk + 1] = make_uint4(v[4], v[5], v[6], v[7]);
+                mutate_block_smem(cfg, N, g, k, k0, k1, blk, sl.lab);
+                const uint4 r0 = s4[2 * blk], r1 = s4[2 * blk + 1];
+                v[0] = r0.x; v[1] = r0.y; v[2] = r0.z; v[3] = r0.w;
+                v[4] = r1.x; v[5] = r1.y; v[6] = r1.z; v[7] = r1.w;
             }
         }
         // genes past N are zero; the changed genes
@@ -588,7 +594,7 @@ __device__ int build_child(const uint16_t *cur, int ldp, int Np, const EvolveCfg
 // are (the parent's d of those clusters taken from them on the way).
 // ---------------------------------------------------------------------------
 template <bool REG>
-__device__ void score_delta_warp(const GatherSlice &sl, int N, int Np, int nx,
+__device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, int Np, int nx,
                                  const long long *__restrict__ ta, long long lfa, long long npa,
                                  long long *__restrict__ tc, const int32_t *__restrict__ Dfix,
                                  int diag, const long long *__restrict__ ltab,
@@ -838,9 +844,12 @@ __global__ void __launch_bounds__(256, 4)
 // parent's score; a child is scored by delta from its first parent, or from
 // scratch when too many genes changed. b: the buffer of the current
 // generation g (g & 1); the next one is written to 1 - b. plan: the child's
-// draws for generation g (slot >= E).
+// draws for generation g (slot >= E). REG_OK: table rows may pass through
+// registers (the single-run kernel; the fleet kernel streams them, which
+// keeps its item loop within its registers).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *nxt,
+template <bool REG_OK>
+__device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *nxt, int N, int ldp,
                                                 const EvolveCfg &cfg, const ChildPlan &plan,
                                                 uint32_t k0, uint32_t k1, int slot,
                                                 const int32_t *__restrict__ perm,
@@ -851,7 +860,6 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
                                                 const GatherSlice &sl, int lane,
                                                 unsigned long long *pairs_out)
 {
-    const int N = cfg.N, ldp = cfg.ldp;
     const int b = plan.g & 1, nb = b ^ 1;
     uint16_t *dst = nxt + (size_t)slot * ldp;
     long long *tc = tab.d[nb] + (size_t)slot * tab.ldt;
@@ -872,12 +880,12 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     } else {
         const int k = slot - cfg.E;
         int ia;
-        const int nx = build_child(cur, ldp, Np, cfg, plan, k, k0, k1, perm, prefix, dst, sl, lane,
-                                   &ia);
+        const int nx = build_child(cur, N, ldp, Np, cfg, plan, k, k0, k1, perm, prefix, dst, sl,
+                                   lane, &ia);
         const long long lfa = tab.lf[b][ia], npa = tab.np[b][ia];
         const long long *ta = tab.d[b] + (size_t)ia * tab.ldt;
         if (nx <= DELTA_X) {
-            if (Np <= 512)
+            if (REG_OK && Np <= 512)
                 score_delta_warp<true>(sl, N, Np, nx, ta, lfa, npa, tc, Dfix, diag, ltab, kfix,
                                        lane, &lf, &np);
             else
@@ -922,7 +930,7 @@ __global__ void __launch_bounds__(128, 7)
     const int g_hint = *reinterpret_cast<volatile const int *>(&st->gnext);
     ChildPlan plan;
     if (slot >= cfg.E)
-        plan = plan_child(cfg, g_hint, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
+        plan = plan_child(cfg, cfg.N, g_hint, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
     // launched as a programmatic dependent of the selection: wait for that grid
     // before reading perm and the state
     griddep_wait();
@@ -930,13 +938,13 @@ __global__ void __launch_bounds__(128, 7)
     const int g = st->gen;
     if (slot == 0 && lane == 0) st->gnext = g + 1;
     if (slot >= cfg.E && g != plan.g)
-        plan = plan_child(cfg, g, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
+        plan = plan_child(cfg, cfg.N, g, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
     plan.g = g;
     const uint16_t *cur = (g & 1) ? pop1 : pop0;
     uint16_t *nxt = (g & 1) ? next1 : next0;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
-    generation_slot(cur, nxt, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix, *diag_flag, logtab,
-                    L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr);
+    generation_slot<true>(cur, nxt, cfg.N, cfg.ldp, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix,
+                    *diag_flag, logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -963,24 +971,22 @@ __global__ void __launch_bounds__(256, 3)
         const DevState *st = r.st;
         if (st->done) continue;
         const int g = st->gen;
-        EvolveCfg cfg = base;
-        cfg.N = r.N;
-        cfg.ldp = r.Np;
         const uint16_t *cur = (g & 1) ? r.pop1 : r.pop0;
         uint16_t *nxt = (g & 1) ? r.pop0 : r.pop1;
         const uint64_t *prefix = prop ? r.work_prefix : rank_prefix;
         const GatherSlice sl = gather_slice(slice, r.Np);
         ChildPlan plan;
         plan.g = g;
-        if (slot >= cfg.E) {
+        if (slot >= base.E) {
             SusPre pre;
-            const bool use_pre = !prop && cfg.sus_tab != nullptr;
+            const bool use_pre = !prop && base.sus_tab != nullptr;
             if (use_pre)
-                pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
-            plan = plan_child(cfg, g, slot - cfg.E, st->k0, st->k1, use_pre ? &pre : nullptr, lane);
+                pre = sus_prefetch((uint32_t)(slot - base.E), base.M, P, prefix, base.sus_tab, lane);
+            plan = plan_child(base, r.N, g, slot - base.E, st->k0, st->k1, use_pre ? &pre : nullptr,
+                              lane);
         }
-        generation_slot(cur, nxt, cfg, plan, st->k0, st->k1, slot, r.perm, prefix, r.Np, r.Dfix,
-                        *r.diag, logtab, r.L, r.tab, sl, lane, nullptr);
+        generation_slot<false>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot, r.perm, prefix, r.Np,
+                        r.Dfix, *r.diag, logtab, r.L, r.tab, sl, lane, nullptr);
         __syncwarp();
     }
 }
