@@ -496,8 +496,8 @@ __global__ void __launch_bounds__(256)
         }
         // the migrants' score tables travel with them
         const int nb = (g + 1) & 1;
-        const long long *tsrc = a.tab.d[nb];
-        long long *tdst = b.tab.d[nb];
+        const long long *tsrc = a.tab.dbuf(nb);
+        long long *tdst = b.tab.dbuf(nb);
         const int ldt = a.tab.ldt;
         for (int idx = threadIdx.x; idx < m * ldt; idx += blockDim.x) {
             const int r = idx / ldt, j = idx - r * ldt;
@@ -505,8 +505,8 @@ __global__ void __launch_bounds__(256)
         }
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
             b.L[P - m + r] = a.L[r];
-            b.tab.lf[nb][P - m + r] = a.tab.lf[nb][r];
-            b.tab.np[nb][P - m + r] = a.tab.np[nb][r];
+            b.tab.lfbuf(nb)[P - m + r] = a.tab.lfbuf(nb)[r];
+            b.tab.npbuf(nb)[P - m + r] = a.tab.npbuf(nb)[r];
         }
     }
 }

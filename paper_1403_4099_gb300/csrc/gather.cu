@@ -66,40 +66,59 @@ __host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np
 
 constexpr uint16_t NO_SLOT = 0xffffu;
 
+// the slice of one warp: its base and Np; the regions are computed on use
+// (a struct of pointers would be kept in local memory)
 struct GatherSlice {
-    int *list;
-    uint32_t *cnt;
-    uint16_t *lab;
-    uint16_t *mem;
-    // delta region
-    long long *dacc;            // per affected cluster: change of d, then the new d
-    long long *dold;            // per affected cluster: d in the parent
-    unsigned *in_mask, *out_mask; // per affected cluster: bits over X
-    uint16_t *nnew;             // per affected cluster: members in the child
-    uint16_t *slab, *um;        // per affected cluster: label, a member left in place
-    uint16_t *xs, *xa, *xc;     // per changed gene: index, label in a, label in the child
-    uint16_t *lablist;          // full path: label of listed cluster c
+    unsigned char *base;
+    int Np;
+    __device__ __forceinline__ int *list() const { return reinterpret_cast<int *>(base); }
+    __device__ __forceinline__ uint32_t *cnt() const
+    {
+        return reinterpret_cast<uint32_t *>(base + (size_t)2 * Np);
+    }
+    __device__ __forceinline__ uint16_t *lab() const
+    {
+        return reinterpret_cast<uint16_t *>(base + (size_t)4 * Np);
+    }
+    __device__ __forceinline__ uint16_t *mem() const
+    {
+        return reinterpret_cast<uint16_t *>(base + (size_t)6 * Np);
+    }
+    // delta region: per affected cluster the change of d (then the new d),
+    // the parent's d, the bits over X of the genes that joined / left it, its
+    // member count in the child, its label and a member left in place; per
+    // changed gene its index and its labels in a and in the child; in the
+    // full path, the labels of the listed clusters
+    __device__ __forceinline__ long long *dacc() const
+    {
+        return reinterpret_cast<long long *>(base + (size_t)8 * Np);
+    }
+    __device__ __forceinline__ long long *dold() const { return dacc() + DELTA_A; }
+    __device__ __forceinline__ unsigned *in_mask() const
+    {
+        return reinterpret_cast<unsigned *>(dold() + DELTA_A);
+    }
+    __device__ __forceinline__ unsigned *out_mask() const { return in_mask() + DELTA_A; }
+    __device__ __forceinline__ uint16_t *nnew() const
+    {
+        return reinterpret_cast<uint16_t *>(out_mask() + DELTA_A);
+    }
+    __device__ __forceinline__ uint16_t *slab() const { return nnew() + DELTA_A; }
+    __device__ __forceinline__ uint16_t *um() const { return slab() + DELTA_A; }
+    __device__ __forceinline__ uint16_t *xs() const { return um() + DELTA_A; }
+    __device__ __forceinline__ uint16_t *xa() const { return xs() + DELTA_X; }
+    __device__ __forceinline__ uint16_t *xc() const { return xa() + DELTA_X; }
+    __device__ __forceinline__ uint16_t *lablist() const
+    {
+        return reinterpret_cast<uint16_t *>(base + (size_t)8 * Np);
+    }
 };
 
-__device__ inline GatherSlice gather_slice(unsigned char *base, int Np)
+__device__ __forceinline__ GatherSlice gather_slice(unsigned char *base, int Np)
 {
     GatherSlice s;
-    s.list = reinterpret_cast<int *>(base);
-    s.cnt = reinterpret_cast<uint32_t *>(base + (size_t)2 * Np);
-    s.lab = reinterpret_cast<uint16_t *>(base + (size_t)4 * Np);
-    s.mem = reinterpret_cast<uint16_t *>(base + (size_t)6 * Np);
-    unsigned char *d = base + (size_t)8 * Np;
-    s.dacc = reinterpret_cast<long long *>(d);
-    s.dold = s.dacc + DELTA_A;
-    s.in_mask = reinterpret_cast<unsigned *>(s.dold + DELTA_A);
-    s.out_mask = s.in_mask + DELTA_A;
-    s.nnew = reinterpret_cast<uint16_t *>(s.out_mask + DELTA_A);
-    s.slab = s.nnew + DELTA_A;
-    s.um = s.slab + DELTA_A;
-    s.xs = s.um + DELTA_A;
-    s.xa = s.xs + DELTA_X;
-    s.xc = s.xa + DELTA_X;
-    s.lablist = reinterpret_cast<uint16_t *>(d);
+    s.base = base;
+    s.Np = Np;
     return s;
 }
 
@@ -167,7 +186,7 @@ __device__ __forceinline__ long long cluster_term(int n, long long df,
 // L from its Q40 fixed point
 __device__ __forceinline__ double lfix_to_double(long long lf) { return dbl_scaled(lf, 40); }
 
-// Score one configuration held in sl.lab[0..N) (labels < N, N < 65536) from
+// Score one configuration held in sl.lab()[0..N) (labels < N, N < 65536) from
 // scratch. Returns L in Q40 on all lanes and the pair count sum_s n_s (n_s -
 // 1) / 2 in *npairs_out (all lanes). Dfix: Np x Np int32, D = 1 - C in fixed
 // point 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. trow (optional): the
@@ -181,11 +200,11 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
     const unsigned lt = (1u << lane) - 1u;
     const int nwd = (N + 1) >> 1; // words holding the labels 0..N-1
     // histogram
-    for (int w = lane; w < nwd; w += 32) sl.cnt[w] = 0u;
+    for (int w = lane; w < nwd; w += 32) sl.cnt()[w] = 0u;
     __syncwarp();
     for (int i = lane; i < N; i += 32) {
-        const int s = sl.lab[i];
-        atomicAdd(&sl.cnt[s >> 1], 1u << ((s & 1) << 4));
+        const int s = sl.lab()[i];
+        atomicAdd(&sl.cnt()[s >> 1], 1u << ((s & 1) << 4));
     }
     __syncwarp();
     // cluster starts (exclusive scan of the counts, written over the counts)
@@ -201,7 +220,7 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
             int tot = 0, nns = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                c2[q] = w0 + q < nwd ? sl.cnt[w0 + q] : 0u;
+                c2[q] = w0 + q < nwd ? sl.cnt()[w0 + q] : 0u;
                 const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
                 tot += x0 + x1;
                 nns += (x0 >= 2) + (x1 >= 2);
@@ -221,15 +240,15 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
             for (int q = 0; q < 4; ++q) {
                 if (w0 + q < nwd) {
                     const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
-                    sl.cnt[w0 + q] = (uint32_t)run | ((uint32_t)(run + x0) << 16);
+                    sl.cnt()[w0 + q] = (uint32_t)run | ((uint32_t)(run + x0) << 16);
                     if (x0 >= 2) {
-                        sl.lablist[li] = (uint16_t)(2 * (w0 + q));
-                        sl.list[li++] = (run << 16) | x0;
+                        sl.lablist()[li] = (uint16_t)(2 * (w0 + q));
+                        sl.list()[li++] = (run << 16) | x0;
                     }
                     run += x0;
                     if (x1 >= 2) {
-                        sl.lablist[li] = (uint16_t)(2 * (w0 + q) + 1);
-                        sl.list[li++] = (run << 16) | x1;
+                        sl.lablist()[li] = (uint16_t)(2 * (w0 + q) + 1);
+                        sl.list()[li++] = (run << 16) | x1;
                     }
                     run += x1;
                 }
@@ -245,24 +264,24 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
         int sv[4];
         uint32_t old[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sv[u] = i0 + 32 * u < N ? (int)sl.lab[i0 + 32 * u] : -1;
+        for (int u = 0; u < 4; ++u) sv[u] = i0 + 32 * u < N ? (int)sl.lab()[i0 + 32 * u] : -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            old[u] = sv[u] >= 0 ? atomicAdd(&sl.cnt[sv[u] >> 1], 1u << ((sv[u] & 1) << 4)) : 0u;
+            old[u] = sv[u] >= 0 ? atomicAdd(&sl.cnt()[sv[u] >> 1], 1u << ((sv[u] & 1) << 4)) : 0u;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (sv[u] >= 0)
-                sl.mem[(old[u] >> ((sv[u] & 1) << 4)) & 0xffffu] = (uint16_t)(i0 + 32 * u);
+                sl.mem()[(old[u] >> ((sv[u] & 1) << 4)) & 0xffffu] = (uint16_t)(i0 + 32 * u);
     }
     __syncwarp();
-    const int *list = sl.list;
+    const int *list = sl.list();
     // Pair sums of every listed cluster first, then the terms: the sums hold
     // no dependency on one another, so a lane's loads of successive clusters
     // overlap. csum (int64 per listed cluster) fills the dead count and label
     // space (4 Np contiguous bytes) from the front, the list of big clusters
     // (n > 8) from the back: 8 nlist + 4 nbig <= 4 N bytes.
-    long long *csum = reinterpret_cast<long long *>(sl.cnt);
-    int *big_end = reinterpret_cast<int *>(sl.lab + Np);
+    long long *csum = reinterpret_cast<long long *>(sl.cnt());
+    int *big_end = reinterpret_cast<int *>(sl.lab() + Np);
     int nbig = 0;
     // small clusters: one lane each, all pair loads of the cluster at once
     for (int base = 0; base < nlist; base += 32) {
@@ -273,7 +292,7 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
             n = v & 0xffff;
         }
         if (n >= 2 && n <= SMALL_CLUSTER) {
-            const uint16_t *m = sl.mem + (v >> 16);
+            const uint16_t *m = sl.mem() + (v >> 16);
             csum[c] = n <= 4 ? small_cluster_sum<4>(m, n, Dfix, Np, diag)
                              : small_cluster_sum<SMALL_CLUSTER>(m, n, Dfix, Np, diag);
         }
@@ -286,7 +305,7 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
     for (int q = 0; q < nbig; ++q) {
         const int c = big_end[-1 - q];
         const int v = list[c];
-        const uint16_t *m = sl.mem + (v >> 16);
+        const uint16_t *m = sl.mem() + (v >> 16);
         const int n = v & 0xffff;
         long long sum = 0;
         for (int a = lane; a < n - 1; a += 32) {
@@ -317,7 +336,7 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
         const long long d = csum[c];
         lf += cluster_term(n, d, ltab, kfix);
         npairs += n * (n - 1) / 2;
-        if (trow) trow[sl.lablist[c]] = d;
+        if (trow) trow[sl.lablist()[c]] = d;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -424,7 +443,7 @@ __device__ __forceinline__ void mutate_block_smem(const EvolveCfg &cfg, int N, i
 
 // Build child k from plan c: SUS parents (perm read here), crossover,
 // mutation; writes the child to dst (global, padded row of Np genes) and
-// sl.lab, and the changed genes X (against parent a) to sl.xs / xa / xc when
+// sl.lab(), and the changed genes X (against parent a) to sl.xs() / xa / xc when
 // there are at most DELTA_X of them. Returns the number of changed genes
 // (all lanes) and parent a's index in *ia_out.
 __device__ __forceinline__ int build_child(const uint16_t *cur, int N, int ldp, int Np,
@@ -466,7 +485,7 @@ __device__ __forceinline__ int build_child(const uint16_t *cur, int N, int ldp, 
     const uint4 *a4 = reinterpret_cast<const uint4 *>(a);
     const uint4 *b4 = reinterpret_cast<const uint4 *>(b);
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-    uint4 *s4 = reinterpret_cast<uint4 *>(sl.lab);
+    uint4 *s4 = reinterpret_cast<uint4 *>(sl.lab());
     const int nblk = Np / MUT_BLOCK;
     int nx = 0;
     for (int blk = lane; blk - lane < nblk; blk += 32) {
@@ -529,7 +548,7 @@ __device__ __forceinline__ int build_child(const uint16_t *cur, int N, int ldp, 
             } else if (cfg.thr_pm) {
                 s4[2 * blk] = make_uint4(v[0], v[1], v[2], v[3]);
                 s4[2 * blk + 1] = make_uint4(v[4], v[5], v[6], v[7]);
-                mutate_block_smem(cfg, N, g, k, k0, k1, blk, sl.lab);
+                mutate_block_smem(cfg, N, g, k, k0, k1, blk, sl.lab());
                 const uint4 r0 = s4[2 * blk], r1 = s4[2 * blk + 1];
                 v[0] = r0.x; v[1] = r0.y; v[2] = r0.z; v[3] = r0.w;
                 v[4] = r1.x; v[5] = r1.y; v[6] = r1.z; v[7] = r1.w;
@@ -562,9 +581,9 @@ __device__ __forceinline__ int build_child(const uint16_t *cur, int N, int ldp, 
                 if ((diff >> p) & 1u) {
                     if (pos < DELTA_X) {
                         const int hsh = (p & 1) << 4;
-                        sl.xs[pos] = (uint16_t)(base + p);
-                        sl.xa[pos] = (uint16_t)((aw[p >> 1] >> hsh) & 0xffffu);
-                        sl.xc[pos] = (uint16_t)((v[p >> 1] >> hsh) & 0xffffu);
+                        sl.xs()[pos] = (uint16_t)(base + p);
+                        sl.xa()[pos] = (uint16_t)((aw[p >> 1] >> hsh) & 0xffffu);
+                        sl.xc()[pos] = (uint16_t)((v[p >> 1] >> hsh) & 0xffffu);
                     }
                     ++pos;
                 }
@@ -585,7 +604,7 @@ __device__ __forceinline__ int build_child(const uint16_t *cur, int N, int ldp, 
 }
 
 // ---------------------------------------------------------------------------
-// Delta scoring of a child (sl.lab holds it, sl.xs / xa / xc its nx <=
+// Delta scoring of a child (sl.lab() holds it, sl.xs() / xa / xc its nx <=
 // DELTA_X changed genes) against its first parent a (d table row ta, Lfix
 // lfa, pair count npa): writes the child's d table row tc (a's row with the
 // touched clusters updated) and returns its Lfix and pair count. REG: the
@@ -615,18 +634,18 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
         for (int v = lane; v < nv; v += 32) tc2[v] = __ldg(ta2 + v);
     }
     // no label affected yet; bitmap of the changed genes in the list space
-    uint16_t *aslot = reinterpret_cast<uint16_t *>(sl.cnt);
-    uint32_t *isx = reinterpret_cast<uint32_t *>(sl.list);
+    uint16_t *aslot = reinterpret_cast<uint16_t *>(sl.cnt());
+    uint32_t *isx = reinterpret_cast<uint32_t *>(sl.list());
     for (int w = lane; w < (Np >> 1); w += 32) reinterpret_cast<uint32_t *>(aslot)[w] = 0xffffffffu;
     for (int w = lane; w < (Np >> 5); w += 32) isx[w] = 0u;
     __syncwarp();
-    if (lane < nx) atomicOr(&isx[sl.xs[lane] >> 5], 1u << (sl.xs[lane] & 31));
+    if (lane < nx) atomicOr(&isx[sl.xs()[lane] >> 5], 1u << (sl.xs()[lane] & 31));
     // the affected clusters: the old and new labels of X, each once
     int na = 0;
     for (int base = 0; base < 2 * nx; base += 32) {
         const int q = base + lane;
         int lab = -1;
-        if (q < 2 * nx) lab = q < nx ? (int)sl.xa[q] : (int)sl.xc[q - nx];
+        if (q < 2 * nx) lab = q < nx ? (int)sl.xa()[q] : (int)sl.xc()[q - nx];
         const bool fresh = lab >= 0 && aslot[lab] == NO_SLOT;
         const unsigned grp = __match_any_sync(FULL, fresh ? lab : -1 - lane);
         const bool leader = fresh && (__ffs(grp) - 1) == lane;
@@ -634,20 +653,20 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
         if (leader) {
             const int k = na + __popc(lb & lt);
             aslot[lab] = (uint16_t)k;
-            sl.slab[k] = (uint16_t)lab;
-            sl.in_mask[k] = 0u;
-            sl.out_mask[k] = 0u;
-            sl.dacc[k] = 0;
-            sl.dold[k] = 0;
-            sl.nnew[k] = 0;
-            sl.um[k] = NO_SLOT;
+            sl.slab()[k] = (uint16_t)lab;
+            sl.in_mask()[k] = 0u;
+            sl.out_mask()[k] = 0u;
+            sl.dacc()[k] = 0;
+            sl.dold()[k] = 0;
+            sl.nnew()[k] = 0;
+            sl.um()[k] = NO_SLOT;
         }
         na += __popc(lb);
         __syncwarp();
     }
     if (lane < nx) {
-        atomicOr(&sl.out_mask[aslot[sl.xa[lane]]], 1u << lane);
-        atomicOr(&sl.in_mask[aslot[sl.xc[lane]]], 1u << lane);
+        atomicOr(&sl.out_mask()[aslot[sl.xa()[lane]]], 1u << lane);
+        atomicOr(&sl.in_mask()[aslot[sl.xc()[lane]]], 1u << lane);
     }
     __syncwarp();
     if (REG) {
@@ -659,17 +678,17 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
             const int v = lane + 32 * i;
             if (v < nv) {
                 const int k0 = aslot[2 * v], k1 = aslot[2 * v + 1];
-                if (k0 != NO_SLOT) sl.dold[k0] = tv[i].x;
-                if (k1 != NO_SLOT) sl.dold[k1] = tv[i].y;
+                if (k0 != NO_SLOT) sl.dold()[k0] = tv[i].x;
+                if (k1 != NO_SLOT) sl.dold()[k1] = tv[i].y;
                 tc2[v] = tv[i];
             }
         }
     }
     // members of the affected clusters in the child, two genes per lane and
     // step: counted, and those that stayed in place (U) listed in the member space
-    uint16_t *ulist = sl.mem;
-    const uint32_t *lab2 = reinterpret_cast<const uint32_t *>(sl.lab);
-    unsigned *nn2 = reinterpret_cast<unsigned *>(sl.nnew);
+    uint16_t *ulist = sl.mem();
+    const uint32_t *lab2 = reinterpret_cast<const uint32_t *>(sl.lab());
+    unsigned *nn2 = reinterpret_cast<unsigned *>(sl.nnew());
     int nu = 0;
 #pragma unroll 2
     for (int j0 = 0; j0 < N; j0 += 64) {
@@ -684,12 +703,12 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
             if (ka != NO_SLOT) {
                 atomicAdd(nn2 + (ka >> 1), 1u << ((ka & 1) << 4));
                 sa = (xb & 1u) == 0u;
-                if (sa) sl.um[ka] = (uint16_t)j; // any one of them
+                if (sa) sl.um()[ka] = (uint16_t)j; // any one of them
             }
             if (kb != NO_SLOT) {
                 atomicAdd(nn2 + (kb >> 1), 1u << ((kb & 1) << 4));
                 sb = (xb & 2u) == 0u;
-                if (sb) sl.um[kb] = (uint16_t)(j + 1);
+                if (sb) sl.um()[kb] = (uint16_t)(j + 1);
             }
         }
         const unsigned ba = __ballot_sync(FULL, sa), bb = __ballot_sync(FULL, sb);
@@ -710,9 +729,9 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
         for (int h = 0; h < 2; ++h) {
             const int e = e0 + 32 * h;
             jj[h] = e < nu ? (int)ulist[e] : 0;
-            kk[h] = e < nu ? (int)aslot[sl.lab[jj[h]]] : 0;
-            mi[h] = e < nu ? sl.in_mask[kk[h]] : 0u;
-            mm[h] = e < nu ? (mi[h] | sl.out_mask[kk[h]]) : 0u;
+            kk[h] = e < nu ? (int)aslot[sl.lab()[jj[h]]] : 0;
+            mi[h] = e < nu ? sl.in_mask()[kk[h]] : 0u;
+            mm[h] = e < nu ? (mi[h] | sl.out_mask()[kk[h]]) : 0u;
         }
         while (mm[0] | mm[1]) {
             int32_t val[2][4];
@@ -724,7 +743,7 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
                 for (int u = 0; u < 4; ++u) {
                     bit[h][u] = mm[h] & (~mm[h] + 1u);
                     mm[h] ^= bit[h][u];
-                    val[h][u] = bit[h][u] ? __ldg(row + sl.xs[__ffs(bit[h][u]) - 1]) : 0;
+                    val[h][u] = bit[h][u] ? __ldg(row + sl.xs()[__ffs(bit[h][u]) - 1]) : 0;
                 }
             }
 #pragma unroll
@@ -736,36 +755,36 @@ __device__ __forceinline__ void score_delta_warp(const GatherSlice &sl, int N, i
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             if (e0 + 32 * h < nu)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kk[h]]),
+                atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc()[kk[h]]),
                           (unsigned long long)(2 * s[h]));
     }
     // D(In_t, In_t) - D(Out_t, Out_t): per changed gene, its row at the genes
     // that joined its new cluster with it and at those that left its old one
     if (lane < nx) {
-        const int kin = aslot[sl.xc[lane]], kout = aslot[sl.xa[lane]];
-        const int32_t *row = Dfix + (size_t)sl.xs[lane] * Np;
+        const int kin = aslot[sl.xc()[lane]], kout = aslot[sl.xa()[lane]];
+        const int32_t *row = Dfix + (size_t)sl.xs()[lane] * Np;
         long long si = 0, so = 0;
-        for (unsigned m = sl.in_mask[kin]; m; m &= m - 1) si += __ldg(row + sl.xs[__ffs(m) - 1]);
-        for (unsigned m = sl.out_mask[kout]; m; m &= m - 1) so += __ldg(row + sl.xs[__ffs(m) - 1]);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kin]), (unsigned long long)si);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc[kout]), (unsigned long long)(-so));
+        for (unsigned m = sl.in_mask()[kin]; m; m &= m - 1) si += __ldg(row + sl.xs()[__ffs(m) - 1]);
+        for (unsigned m = sl.out_mask()[kout]; m; m &= m - 1) so += __ldg(row + sl.xs()[__ffs(m) - 1]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc()[kin]), (unsigned long long)si);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&sl.dacc()[kout]), (unsigned long long)(-so));
     }
     __syncwarp(); // also orders the table copy before the writes below
     // the touched terms: new minus old
     long long dl = 0, dp = 0;
     for (int k = lane; k < na; k += 32) {
-        const int t = sl.slab[k];
-        const unsigned mi = sl.in_mask[k], mo = sl.out_mask[k];
-        const int nn = (int)sl.nnew[k];
+        const int t = sl.slab()[k];
+        const unsigned mi = sl.in_mask()[k], mo = sl.out_mask()[k];
+        const int nn = (int)sl.nnew()[k];
         const int no = nn - __popc(mi) + __popc(mo);
         long long dold = 0;
         if (no >= 2) {
-            dold = REG ? sl.dold[k] : __ldg(ta + t);
+            dold = REG ? sl.dold()[k] : __ldg(ta + t);
         } else if (no == 1 && diag) { // a singleton's d is its own D_jj
-            const int m = mo ? (int)sl.xs[__ffs(mo) - 1] : (int)sl.um[k];
+            const int m = mo ? (int)sl.xs()[__ffs(mo) - 1] : (int)sl.um()[k];
             dold = Dfix[(size_t)m * (Np + 1)];
         }
-        const long long dnew = dold + sl.dacc[k];
+        const long long dnew = dold + sl.dacc()[k];
         const long long tn = nn >= 2 ? cluster_term(nn, dnew, ltab, kfix) : 0;
         const long long to = no >= 2 ? cluster_term(no, dold, ltab, kfix) : 0;
         dl += tn - to;
@@ -817,20 +836,20 @@ __global__ void __launch_bounds__(256, 4)
             const int v = (int)lp[i];
             const bool ok = v >= 0 && v < N;
             bad |= !ok;
-            sl.lab[i] = (uint16_t)(ok ? v : 0);
+            sl.lab()[i] = (uint16_t)(ok ? v : 0);
         }
         bad = __any_sync(0xffffffffu, bad);
         __syncwarp();
         long long npairs = 0;
-        long long *trow = tab.d[b] ? tab.d[b] + (size_t)p * tab.ldt : nullptr;
+        long long *trow = tab.dbuf(b) ? tab.dbuf(b) + (size_t)p * tab.ldt : nullptr;
         const long long lf =
             score_full_warp(sl, N, Np, Dfix, diag, ltab, ktab, lane, trow, &npairs);
         if (lane == 0) {
             L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : lfix_to_double(lf);
             if (bad && err) atomicOr(err, 1);
-            if (tab.lf[b]) {
-                tab.lf[b][p] = lf;
-                tab.np[b][p] = npairs;
+            if (tab.lfbuf(b)) {
+                tab.lfbuf(b)[p] = lf;
+                tab.npbuf(b)[p] = npairs;
             }
             if (pairs_g) atomicAdd(pairs_g, (unsigned long long)npairs);
         }
@@ -862,7 +881,7 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
 {
     const int b = plan.g & 1, nb = b ^ 1;
     uint16_t *dst = nxt + (size_t)slot * ldp;
-    long long *tc = tab.d[nb] + (size_t)slot * tab.ldt;
+    long long *tc = tab.dbuf(nb) + (size_t)slot * tab.ldt;
     const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *kfix = kfix_of(logtab);
     long long lf, np;
@@ -871,19 +890,19 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
         const int src_i = perm[slot];
         const uint16_t *src = cur + (size_t)src_i * ldp;
         for (int j = lane; j < N; j += 32) dst[j] = src[j];
-        const int4 *ts = reinterpret_cast<const int4 *>(tab.d[b] + (size_t)src_i * tab.ldt);
+        const int4 *ts = reinterpret_cast<const int4 *>(tab.dbuf(b) + (size_t)src_i * tab.ldt);
         int4 *td = reinterpret_cast<int4 *>(tc);
 #pragma unroll 8
         for (int v = lane; v < (Np >> 1); v += 32) td[v] = __ldg(ts + v);
-        lf = tab.lf[b][src_i];
-        np = tab.np[b][src_i];
+        lf = tab.lfbuf(b)[src_i];
+        np = tab.npbuf(b)[src_i];
     } else {
         const int k = slot - cfg.E;
         int ia;
         const int nx = build_child(cur, N, ldp, Np, cfg, plan, k, k0, k1, perm, prefix, dst, sl,
                                    lane, &ia);
-        const long long lfa = tab.lf[b][ia], npa = tab.np[b][ia];
-        const long long *ta = tab.d[b] + (size_t)ia * tab.ldt;
+        const long long lfa = tab.lfbuf(b)[ia], npa = tab.npbuf(b)[ia];
+        const long long *ta = tab.dbuf(b) + (size_t)ia * tab.ldt;
         if (nx <= DELTA_X) {
             if (REG_OK && Np <= 512)
                 score_delta_warp<true>(sl, N, Np, nx, ta, lfa, npa, tc, Dfix, diag, ltab, kfix,
@@ -897,8 +916,8 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     }
     if (lane == 0) {
         L[slot] = lfix_to_double(lf);
-        tab.lf[nb][slot] = lf;
-        tab.np[nb][slot] = np;
+        tab.lfbuf(nb)[slot] = lf;
+        tab.npbuf(nb)[slot] = np;
         if (pairs_out) atomicAdd(pairs_out, (unsigned long long)np);
     }
 }

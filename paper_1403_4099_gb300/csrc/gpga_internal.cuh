@@ -422,6 +422,11 @@ struct ScoreTab {
     long long *lf[2] = {nullptr, nullptr};
     long long *np[2] = {nullptr, nullptr};
     int ldt = 0;
+    // buffer b selected without a run-time array index (which would keep the
+    // kernel-parameter copy of this struct in local memory)
+    __host__ __device__ __forceinline__ long long *dbuf(int b) const { return b ? d[1] : d[0]; }
+    __host__ __device__ __forceinline__ long long *lfbuf(int b) const { return b ? lf[1] : lf[0]; }
+    __host__ __device__ __forceinline__ long long *npbuf(int b) const { return b ? np[1] : np[0]; }
 };
 
 struct FleetRun {

@@ -247,8 +247,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // 1024-byte aligned stage buffers
     const uint32_t raw = smem_u32(sm_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
-    unsigned char *stage_ptr[2] = {sm_raw + pad, sm_raw + pad + STAGE_BYTES};
-    const uint32_t stage_addr[2] = {raw + pad, raw + pad + STAGE_BYTES};
+    // stage s at a byte offset s * STAGE_BYTES (selected arithmetically: a
+    // run-time index into a local array would live in local memory)
+    unsigned char *const stage0 = sm_raw + pad;
+    const uint32_t stage0_addr = raw + pad;
 
     const int ncols = (int)*w.ncols;
     const int nct = (ncols + TC_ACC * TC_M - 1) / (TC_ACC * TC_M);
@@ -294,7 +296,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         // D tiles of K-block kb into stage s (all threads; one commit group)
         auto copy_d = [&](int kb, int s) {
-            const uint32_t bh = stage_addr[s] + TC_ACC * A_BYTES, bl = bh + B_BYTES;
+            const uint32_t bh = stage0_addr + (uint32_t)s * STAGE_BYTES + TC_ACC * A_BYTES,
+                           bl = bh + B_BYTES;
             for (int q = tid; q < NT * 8; q += TC_THREADS) {
                 const int row = q >> 3, ch = q & 7;
                 const int gi = n0 + row;
@@ -312,8 +315,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         copy_d(0, it & 1);
         for (int kb = 0; kb < KB; ++kb, ++it) {
             const int s = it & 1;
-            unsigned char *A = stage_ptr[s];
-            const uint32_t Aaddr = stage_addr[s];
+            unsigned char *A = stage0 + (size_t)s * STAGE_BYTES;
+            const uint32_t Aaddr = stage0_addr + (uint32_t)s * STAGE_BYTES;
             const uint32_t Bh = Aaddr + TC_ACC * A_BYTES, Bl = Bh + B_BYTES;
             // one-hot rows from the membership bits (thread = column of each
             // accumulator's tile)
