@@ -204,7 +204,7 @@ size_t carve(gpga_ga *h, char *base)
     h->canon = c.take<int32_t>(N);
     h->Lbest = c.take<double>(1);
     if (h->prm.form == GPGA_FORM_TENSOR) tc_carve(&h->tc, h->N, h->Np, h->P, &c.off, c.base);
-    if (h->prm.form == GPGA_FORM_GATHER) {
+    if (h->prm.form == GPGA_FORM_GATHER && uses_delta(h->N)) {
         h->tab.ldt = (int)Np;
         for (int b = 0; b < 2; ++b) {
             h->tab.d[b] = c.take<long long>(P * Np);

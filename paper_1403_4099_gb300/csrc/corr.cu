@@ -1,5 +1,7 @@
 // corr.cu -- Pearson correlation prelude, Eq. 7 (Sec. 2.1; the standardisation
 // below Eq. 2): C_ij = <z_i, z_j> / sqrt(|z_i|^2 |z_j|^2), z = R - column mean.
+// Unit weights (cluster_corr) run the tensor-core path of corr_tc.cu; this
+// file holds the weighted (EWMA) path and the market-mode removal.
 //
 // Passes over R (T x N FP64, row-major, leading dim ld):
 //   1. column sums over T-slabs (FP64 partials, fixed order) -> means, finiteness
@@ -262,6 +264,9 @@ int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s)
 int corr_run_weighted(const double *R, int T, int N, int ld, double lambda, double *C,
                       cudaStream_t s)
 {
+    // unit weights (plain Pearson): the integer statistics and the tcgen05
+    // contraction of corr_tc.cu; below, the FP64 / FP32 path of the EWMA weights
+    if (lambda == 1.0) return corr_run_tc(R, T, N, ld, C, s);
     const bool weighted = lambda != 1.0;
     const int Np = pad_n(N);
     const int nslab_c = (T + T_SLAB - 1) / T_SLAB;
@@ -520,6 +525,7 @@ int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, 
 
 int prepare_corr_kernels(int maxsmem)
 {
+    if (int rc = prepare_corr_tc_kernels(maxsmem)) return rc;
     return raise_smem(market_iter_kernel, maxsmem);
 }
 

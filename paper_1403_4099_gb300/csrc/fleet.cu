@@ -113,11 +113,14 @@ static size_t run_bytes(const Fleet *f, int N, char *base, RunMem *m)
     t.d.ticket = c.take<unsigned>(TICKETS);
     t.d.work_prefix = c.take<uint64_t>(P);
     t.d.hist = c.take<double>(G);
-    t.d.tab.ldt = (int)Np;
-    for (int b = 0; b < 2; ++b) {
-        t.d.tab.d[b] = c.take<long long>(P * Np);
-        t.d.tab.lf[b] = c.take<long long>(P);
-        t.d.tab.np[b] = c.take<long long>(P);
+    t.d.tab = ScoreTab{};
+    if (uses_delta(N)) {
+        t.d.tab.ldt = (int)Np;
+        for (int b = 0; b < 2; ++b) {
+            t.d.tab.d[b] = c.take<long long>(P * Np);
+            t.d.tab.lf[b] = c.take<long long>(P);
+            t.d.tab.np[b] = c.take<long long>(P);
+        }
     }
     t.canon = c.take<int32_t>(N);
     t.Lbest = c.take<double>(1);
@@ -256,6 +259,7 @@ static int fleet_create(const gpga_params *p, int cap, int Nmax, void *stream, F
         memset(f->h_st[b], 0, (size_t)cap * sizeof(DevState));
         f->h_hdr[b]->nruns = 0;
         f->h_hdr[b]->nitems = 0;
+        f->h_hdr[b]->ndelta = 0;
     }
     rc = rank_prefix_table(f->rank_prefix, f->P, f->M, f->sus_tab, f->stream);
     if (!rc) rc = launch_logtab(f->logtab, Nmax, f->stream);
@@ -344,8 +348,12 @@ static int fleet_upload(Fleet *f, int b, long long tick)
     for (size_t k = 0; k < order.size(); ++k) f->h_runs[b][k] = f->slots[order[k]].m.d;
     f->nactive = (int)order.size();
     f->nitems = f->nactive * f->P;
+    int nd = 0; // runs with score tables: a prefix of the table (decreasing N)
+    for (int i : order)
+        if (uses_delta(f->slots[i].N)) ++nd;
     f->h_hdr[b]->nruns = f->nactive;
     f->h_hdr[b]->nitems = f->nitems;
+    f->h_hdr[b]->ndelta = nd * f->P;
     if (f->nactive)
         GPGA_CUDA(cudaMemcpyAsync(f->d_runs, f->h_runs[b], (size_t)f->nactive * sizeof(FleetRun),
                                   cudaMemcpyHostToDevice, f->stream));
@@ -359,9 +367,17 @@ static int fleet_upload(Fleet *f, int b, long long tick)
 // pdl: the launch directly follows the fleet's selection in a captured graph
 static int fleet_gen_launch(Fleet *f, int warps, int ctas, bool pdl = false)
 {
+    const int prop = f->prm.scaling == GPGA_SCALING_PROP;
+    // runs with score tables (a fleet that may hold N >= DELTA_MIN_N) first
+    if (uses_delta(f->Nmax)) {
+        int rc = launch_fleet_generation_delta(f->d_runs, f->d_hdr, fleet_evolve_cfg(f),
+                                               f->rank_prefix, f->logtab, f->Np_max, prop,
+                                               f->stream);
+        if (rc) return rc;
+        pdl = false; // the next launch follows a kernel of its own
+    }
     return launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
-                                   f->logtab, f->Np_max, warps, ctas,
-                                   f->prm.scaling == GPGA_SCALING_PROP, f->stream, pdl);
+                                   f->logtab, f->Np_max, warps, ctas, prop, f->stream, pdl);
 }
 
 // Autotuner: warps per CTA (individuals per CTA) and grid shape of the fused

@@ -191,6 +191,7 @@ __device__ __forceinline__ double lfix_to_double(long long lf) { return dbl_scal
 // 1) / 2 in *npairs_out (all lanes). Dfix: Np x Np int32, D = 1 - C in fixed
 // point 2^-DFIX_BITS; diag: nonzero if some D_ii != 0. trow (optional): the
 // individual's row of the d table, written where n_s >= 2.
+template <bool PROD>
 __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int N, int Np,
                                      const int32_t *__restrict__ Dfix, int diag,
                                      const long long *__restrict__ ltab,
@@ -283,6 +284,7 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
     long long *csum = reinterpret_cast<long long *>(sl.cnt());
     int *big_end = reinterpret_cast<int *>(sl.lab() + Np);
     int nbig = 0;
+    long long ksum = 0; // product form: sum of K(n_s) in 2^-44, loaded alongside the pair sums
     // small clusters: one lane each, all pair loads of the cluster at once
     for (int base = 0; base < nlist; base += 32) {
         const int c = base + lane;
@@ -293,6 +295,7 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
         }
         if (n >= 2 && n <= SMALL_CLUSTER) {
             const uint16_t *m = sl.mem() + (v >> 16);
+            if (PROD) ksum += __ldg(kfix + n);
             csum[c] = n <= 4 ? small_cluster_sum<4>(m, n, Dfix, Np, diag)
                              : small_cluster_sum<SMALL_CLUSTER>(m, n, Dfix, Np, diag);
         }
@@ -326,9 +329,37 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
             for (int a = lane; a < n; a += 32) sum += Dfix[(size_t)m[a] * (Np + 1)];
 #pragma unroll
         for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) csum[c] = sum;
+        if (lane == 0) {
+            csum[c] = sum;
+            if (PROD) ksum += __ldg(kfix + n);
+        }
     }
     __syncwarp();
+    if (PROD) {
+        // Eq. 8 as one log of the product of the clusters' factors c d^(n-1):
+        // one lane per cluster, two running products per lane (alternate
+        // clusters) so that two multiply chains overlap
+        LogProd acc, acc2;
+        acc.k = ksum;
+        long long npairs = 0;
+        for (int c = lane; c < nlist; c += 64) {
+            const int n = list[c] & 0xffff;
+            logprod_mul(acc, n, csum[c], DFIX_BITS);
+            npairs += n * (n - 1) / 2;
+            if (c + 32 < nlist) {
+                const int n2 = list[c + 32] & 0xffff;
+                logprod_mul(acc2, n2, csum[c + 32], DFIX_BITS);
+                npairs += n2 * (n2 - 1) / 2;
+            }
+        }
+        mant_mul(acc.m, acc.e, acc2.m, acc2.e); // (adds acc2's exponent too)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        const long long lq = logprod_finish_q40(acc, ltab, nlist);
+        __syncwarp();
+        *npairs_out = npairs;
+        return lq;
+    }
     // the terms, one lane per cluster, summed exactly
     long long lf = 0, npairs = 0;
     for (int c = lane; c < nlist; c += 32) {
@@ -843,7 +874,10 @@ __global__ void __launch_bounds__(256, 4)
         long long npairs = 0;
         long long *trow = tab.dbuf(b) ? tab.dbuf(b) + (size_t)p * tab.ldt : nullptr;
         const long long lf =
-            score_full_warp(sl, N, Np, Dfix, diag, ltab, ktab, lane, trow, &npairs);
+            uses_delta(N) ? score_full_warp<false>(sl, N, Np, Dfix, diag, ltab, ktab, lane, trow,
+                                                   &npairs)
+                          : score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, ktab, lane, nullptr,
+                                                  &npairs);
         if (lane == 0) {
             L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : lfix_to_double(lf);
             if (bad && err) atomicOr(err, 1);
@@ -867,7 +901,7 @@ __global__ void __launch_bounds__(256, 4)
 // registers (the single-run kernel; the fleet kernel streams them, which
 // keeps its item loop within its registers).
 // ---------------------------------------------------------------------------
-template <bool REG_OK>
+template <bool REG_OK, bool DELTA_OK = true>
 __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *nxt, int N, int ldp,
                                                 const EvolveCfg &cfg, const ChildPlan &plan,
                                                 uint32_t k0, uint32_t k1, int slot,
@@ -877,14 +911,40 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
                                                 const double *__restrict__ logtab,
                                                 double *__restrict__ L, const ScoreTab &tab,
                                                 const GatherSlice &sl, int lane,
-                                                unsigned long long *pairs_out)
+                                                unsigned long long *pairs_out,
+                                                const SusPre *pre = nullptr)
 {
     const int b = plan.g & 1, nb = b ^ 1;
     uint16_t *dst = nxt + (size_t)slot * ldp;
-    long long *tc = tab.dbuf(nb) + (size_t)slot * tab.ldt;
     const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *kfix = kfix_of(logtab);
     long long lf, np;
+    if (!DELTA_OK || !tab.dbuf(0)) {
+        // no score tables (N < DELTA_MIN_N): the child is built by the pair
+        // loop of child_genes and scored from scratch in the product form
+        if (slot < cfg.E) {
+            const uint16_t *src = cur + (size_t)perm[slot] * ldp;
+            for (int j = lane; j < N; j += 32) {
+                const uint16_t v = src[j];
+                dst[j] = v;
+                sl.lab()[j] = v;
+            }
+        } else {
+            EvolveCfg c2 = cfg;
+            c2.N = N;
+            c2.ldp = ldp;
+            child_genes<uint16_t>(cur, ldp, N, c2, plan.g, slot - cfg.E, k0, k1, perm, prefix,
+                                  nullptr, dst, sl.lab(), lane, pre);
+        }
+        __syncwarp();
+        lf = score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np);
+        if (lane == 0) {
+            L[slot] = lfix_to_double(lf);
+            if (pairs_out) atomicAdd(pairs_out, (unsigned long long)np);
+        }
+        return;
+    }
+    long long *tc = tab.dbuf(nb) + (size_t)slot * tab.ldt;
     if (slot < cfg.E) {
         // elite: labels, table and score of the parent, unchanged
         const int src_i = perm[slot];
@@ -911,7 +971,7 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
                 score_delta_warp<false>(sl, N, Np, nx, ta, lfa, npa, tc, Dfix, diag, ltab, kfix,
                                         lane, &lf, &np);
         } else {
-            lf = score_full_warp(sl, N, Np, Dfix, diag, ltab, kfix, lane, tc, &np);
+            lf = score_full_warp<false>(sl, N, Np, Dfix, diag, ltab, kfix, lane, tc, &np);
         }
     }
     if (lane == 0) {
@@ -946,9 +1006,11 @@ __global__ void __launch_bounds__(128, 7)
     SusPre pre;
     const bool use_pre = cfg.sus_tab != nullptr && slot >= cfg.E;
     if (use_pre) pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
+    const bool delta = tab.dbuf(0) != nullptr;
     const int g_hint = *reinterpret_cast<volatile const int *>(&st->gnext);
     ChildPlan plan;
-    if (slot >= cfg.E)
+    plan.g = g_hint;
+    if (delta && slot >= cfg.E)
         plan = plan_child(cfg, cfg.N, g_hint, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
     // launched as a programmatic dependent of the selection: wait for that grid
     // before reading perm and the state
@@ -956,14 +1018,15 @@ __global__ void __launch_bounds__(128, 7)
     if (st->done) return;
     const int g = st->gen;
     if (slot == 0 && lane == 0) st->gnext = g + 1;
-    if (slot >= cfg.E && g != plan.g)
+    if (delta && slot >= cfg.E && g != plan.g)
         plan = plan_child(cfg, cfg.N, g, slot - cfg.E, k0, k1, use_pre ? &pre : nullptr, lane);
     plan.g = g;
     const uint16_t *cur = (g & 1) ? pop1 : pop0;
     uint16_t *nxt = (g & 1) ? next1 : next0;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
     generation_slot<true>(cur, nxt, cfg.N, cfg.ldp, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix,
-                    *diag_flag, logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr);
+                          *diag_flag, logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr,
+                          use_pre ? &pre : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -971,11 +1034,15 @@ __global__ void __launch_bounds__(128, 7)
 // i / P (the table is ordered by decreasing N, so the costly runs start
 // first); the CTAs stride over the items. Runs whose state is done are
 // skipped. Per slot the work is exactly that of gather_generation_kernel.
+// DELTA: the items [0, ndelta) of the runs with score tables; otherwise the
+// items [ndelta, nitems) of the runs without (two kernels, so that the
+// compact code of the tableless runs keeps its registers and occupancy).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3)
-    fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
-                            EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
-                            const double *__restrict__ logtab, int Np_max, int prop)
+template <bool DELTA>
+__device__ __forceinline__ void fleet_items(const FleetRun *__restrict__ runs,
+                                            const FleetHdr *__restrict__ hdr, const EvolveCfg &base,
+                                            const uint64_t *__restrict__ rank_prefix,
+                                            const double *__restrict__ logtab, int Np_max, int prop)
 {
     // may be launched as a programmatic dependent of the fleet's selection:
     // wait for that grid before reading any run's state, permutation or prefix
@@ -983,8 +1050,9 @@ __global__ void __launch_bounds__(256, 3)
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max);
-    const int nitems = hdr->nitems, P = base.P;
-    for (int item = blockIdx.x * nw + warp; item < nitems; item += gridDim.x * nw) {
+    const int P = base.P;
+    const int i0 = DELTA ? 0 : hdr->ndelta, i1 = DELTA ? hdr->ndelta : hdr->nitems;
+    for (int item = i0 + blockIdx.x * nw + warp; item < i1; item += gridDim.x * nw) {
         const int ri = item / P, slot = item - ri * P;
         const FleetRun &r = runs[ri];
         const DevState *st = r.st;
@@ -996,18 +1064,34 @@ __global__ void __launch_bounds__(256, 3)
         const GatherSlice sl = gather_slice(slice, r.Np);
         ChildPlan plan;
         plan.g = g;
-        if (slot >= base.E) {
-            SusPre pre;
-            const bool use_pre = !prop && base.sus_tab != nullptr;
-            if (use_pre)
-                pre = sus_prefetch((uint32_t)(slot - base.E), base.M, P, prefix, base.sus_tab, lane);
+        SusPre pre;
+        const bool use_pre = slot >= base.E && !prop && base.sus_tab != nullptr;
+        if (use_pre)
+            pre = sus_prefetch((uint32_t)(slot - base.E), base.M, P, prefix, base.sus_tab, lane);
+        if (DELTA && slot >= base.E)
             plan = plan_child(base, r.N, g, slot - base.E, st->k0, st->k1, use_pre ? &pre : nullptr,
                               lane);
-        }
-        generation_slot<false>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot, r.perm, prefix, r.Np,
-                        r.Dfix, *r.diag, logtab, r.L, r.tab, sl, lane, nullptr);
+        generation_slot<false, DELTA>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot,
+                                      r.perm, prefix, r.Np, r.Dfix, *r.diag, logtab, r.L, r.tab,
+                                      sl, lane, nullptr, use_pre ? &pre : nullptr);
         __syncwarp();
     }
+}
+
+__global__ void __launch_bounds__(512, 2)
+    fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
+                            EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
+                            const double *__restrict__ logtab, int Np_max, int prop)
+{
+    fleet_items<false>(runs, hdr, base, rank_prefix, logtab, Np_max, prop);
+}
+
+__global__ void __launch_bounds__(128, 6)
+    fleet_delta_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
+                       EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
+                       const double *__restrict__ logtab, int Np_max, int prop)
+{
+    fleet_items<true>(runs, hdr, base, rank_prefix, logtab, Np_max, prop);
 }
 
 // warps per CTA of the single-run gather kernels: 4 (measured at N=500,
@@ -1057,7 +1141,7 @@ int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2
 
 int fleet_max_warps(int Np_max)
 {
-    int nw = 8; // the kernel's launch bounds: 256 threads (80 registers each)
+    int nw = 16;
     while (nw > 1 && nw * gather_slice_bytes(Np_max) > (size_t)200 * 1024) nw >>= 1;
     return nw;
 }
@@ -1073,11 +1157,29 @@ int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const Evo
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
                             int warps, int ctas, int prop, cudaStream_t s, bool pdl)
 {
-    if (warps < 1 || warps > 8 || ctas < 1)
+    if (warps < 1 || warps > 16 || ctas < 1)
         return set_error(GPGA_ERR_ARG, "fleet generation: %d warps x %d CTAs", warps, ctas);
     const size_t smem = warps * gather_slice_bytes(Np_max);
     GPGA_CUDA(launch_pdl(fleet_generation_kernel, dim3(ctas), dim3(32 * warps), smem, s, pdl, runs,
                          hdr, cfg, rank_prefix, logtab, Np_max, prop));
+    return GPGA_OK;
+}
+
+int launch_fleet_generation_delta(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
+                                  const uint64_t *rank_prefix, const double *logtab, int Np_max,
+                                  int prop, cudaStream_t s)
+{
+    const int warps = 4;
+    const size_t smem = warps * gather_slice_bytes(Np_max);
+    int dev = 0, sms = 152, occ = 1;
+    GPGA_CUDA(cudaGetDevice(&dev));
+    GPGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GPGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fleet_delta_kernel, 32 * warps,
+                                                            smem));
+    if (occ < 1) return set_error(GPGA_ERR_ARG, "fleet: no room for the delta kernel at Np=%d", Np_max);
+    fleet_delta_kernel<<<sms * occ, 32 * warps, smem, s>>>(runs, hdr, cfg, rank_prefix, logtab,
+                                                           Np_max, prop);
+    GPGA_LAUNCH_CHECK();
     return GPGA_OK;
 }
 
@@ -1096,6 +1198,7 @@ int prepare_gather_kernels(int maxsmem)
     if (int rc = raise_smem(gather_score_kernel<int32_t>, maxsmem)) return rc;
     if (int rc = raise_smem(gather_generation_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(fleet_generation_kernel, maxsmem)) return rc;
+    if (int rc = raise_smem(fleet_delta_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }
 

@@ -132,6 +132,15 @@ template <> struct LabPair<int32_t> {
 // padded gene count: multiple of 64 (tensor-form K tiles, 32-row pair tiles)
 inline int pad_n(int N) { return (N + 63) & ~63; }
 
+// The gather form scores configurations of N >= DELTA_MIN_N genes as a sum of
+// per-cluster fixed-point terms, which lets a GA run keep per-individual
+// score tables and score most children by delta from a parent; smaller N
+// (where a full scoring is cheap) use the one-log product form without
+// tables. The choice depends on N alone, so every call path (single run,
+// fleet, stateless scoring) gives the same L for the same configuration.
+constexpr int DELTA_MIN_N = 192;
+__host__ __device__ inline bool uses_delta(int N) { return N >= DELTA_MIN_N; }
+
 // fixed-point scale (bits) for the order-independent per-cluster sums of
 // FP32 row sums: |row sum| <= 2 N, n_s <= N, so 2 N^2 2^bits < 2^62
 int fix_bits_for(int N);
@@ -297,7 +306,27 @@ constexpr long long LN2_Q62 = 3196577161300663915ll; // round(ln 2 2^62)
 
 // combine the lanes' partial products (fixed xor butterfly: every lane ends
 // with the same value) and return L = k 2^-44 - 1/2 (e ln 2 + log(m 2^-62)),
-// evaluated in fixed point Q40 (absolute error ~1e-12)
+// evaluated in fixed point Q40 (absolute error ~1e-12), as that integer
+__device__ __forceinline__ long long logprod_finish_q40(LogProd a,
+                                                        const long long *__restrict__ ltab,
+                                                        int nclusters)
+{
+    if (nclusters == 0) return 0; // all singletons: Eq. 8 is an empty sum
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, a.m, o);
+        const long long e2 = __shfl_xor_sync(0xffffffffu, a.e, o);
+        const long long k2 = __shfl_xor_sync(0xffffffffu, a.k, o);
+        mant_mul(a.m, a.e, m2, e2);
+        a.k += k2;
+    }
+    const long long ph = __mul64hi(a.e, LN2_Q62);
+    const unsigned long long pl = (unsigned long long)a.e * (unsigned long long)LN2_Q62;
+    const long long elog = (long long)(((unsigned long long)ph << 42) | (pl >> 22));
+    const long long tot = elog + (log_q62(a.m, ltab) >> 22);
+    return (a.k >> (KFIX_BITS - 40)) - (tot >> 1);
+}
+
 __device__ __forceinline__ double logprod_finish(LogProd a, const long long *__restrict__ ltab,
                                                  int nclusters)
 {
@@ -447,6 +476,9 @@ struct FleetRun {
 struct FleetHdr {
     int nruns;  // active descriptors 0 .. nruns-1
     int nitems; // nruns * P work items of the generation kernel
+    int ndelta; // the first ndelta items belong to runs with score tables (N >=
+                // DELTA_MIN_N; the table is sorted by decreasing N)
+    int pad_;
 };
 
 // rank (chunked sort + search, grid) + finalize (perm, stats, termination,
@@ -778,6 +810,11 @@ int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectC
 int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
                             int warps, int ctas, int prop, cudaStream_t s, bool pdl = false);
+// the same for the items of runs with score tables (delta scoring): a fixed
+// shape of 4-warp CTAs, one wave of resident CTAs striding over those items
+int launch_fleet_generation_delta(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
+                                  const uint64_t *rank_prefix, const double *logtab, int Np_max,
+                                  int prop, cudaStream_t s);
 // island migration over the fleet's runs (ring by table position): every
 // `every` generations, the m elites of each run replace the last m children
 // of the next run
@@ -806,6 +843,9 @@ int launch_init_threshold(LabT *pop, int ldp, int P, int N, const int32_t *edge_
 // host launchers (corr.cu)
 // ---------------------------------------------------------------------------
 int corr_run(const double *R, int T, int N, int ld, double *C, cudaStream_t s);
+// unit weights on the tensor cores (corr_tc.cu)
+int corr_run_tc(const double *R, int T, int N, int ld, double *C, cudaStream_t s);
+int prepare_corr_tc_kernels(int maxsmem);
 // EWMA-weighted Pearson: rows weighted lambda^(T-1-t) in the means, the
 // variances and the cross products (lambda = 1: plain Pearson)
 int corr_run_weighted(const double *R, int T, int N, int ld, double lambda, double *C,
