@@ -483,10 +483,15 @@ def run_e2e(args, ranks, R_host, dev, form, G):
 
 
 RECOVER_CONFIGS = (
-    # name, planted workload, P, E, generation cap
-    ("small16_p64", "small16", 64, 2, 2000),
-    ("n100_p1024", "n100", 1024, 10, 3000),
-    ("n500_p4096", "n500", 4096, 10, 5000),
+    # name, planted workload, P, E, generation cap, initial label range K0 (0: N)
+    ("small16_p64", "small16", 64, 2, 2000, 0),
+    ("n100_p1024", "n100", 1024, 10, 3000, 0),
+    ("n500_p4096", "n500", 4096, 10, 5000, 0),
+    # the same GA from labels uniform in [0, round(sqrt(N))) instead of [0, N)
+    # (the reading of "create initial population" allows a smaller label
+    # range; sqrt(N) is a generic choice, not the planted cluster count)
+    ("n100_p1024_k0_10", "n100", 1024, 10, 3000, 10),
+    ("n500_p4096_k0_22", "n500", 4096, 10, 5000, 22),
 )
 RECOVER_SEEDS = (101, 202, 303)
 
@@ -523,14 +528,14 @@ def run_recover(args, ranks, planted, dev, form):
     stream = torch.cuda.Stream(device=dev)
     out = {"uniform_init": {}}
     with torch.cuda.stream(stream):
-        for name, wl, Pw, Ew, cap in RECOVER_CONFIGS:
+        for name, wl, Pw, Ew, cap, K0 in RECOVER_CONFIGS:
             pl = planted if wl == "n500" else getattr(synth, wl)()
             Rw = torch.from_numpy(pl.R).to(dev)
             Nw = pl.R.shape[1]
             Cw = torch.empty((Nw, Nw), dtype=torch.float64, device=dev)
             gpga.cluster_corr(Rw, Cw, stream)
             prm = gpga.default_params(P=Pw, elite=Ew, max_gens=cap, stall_gens=50, tol=-1.0,
-                                      pm=0.01, form=form, record=1)
+                                      pm=0.01, form=form, record=1, init_labels=K0)
             ga = gpga.GA(Cw, prm, seed=1, stream=stream)
             runs = []
             for sd in RECOVER_SEEDS:
@@ -546,6 +551,7 @@ def run_recover(args, ranks, planted, dev, form):
             ok = [r["ms"] for r in runs if r["ms"] is not None]
             out["uniform_init"][name] = {
                 "N": Nw, "P": Pw, "elite": Ew, "generation_cap": cap,
+                "initial_labels": K0 or Nw,
                 "recovered": f"{len(ok)}/{len(runs)}",
                 "median_ms": float(np.median(ok)) if ok else None,
                 "runs": runs}

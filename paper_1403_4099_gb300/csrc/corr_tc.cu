@@ -15,8 +15,10 @@
 //   4. gram_tc:  S = Z^T Z on 128 x 128 upper-triangle tiles, the T range
 //                split over CTAs: six BF16 products (hi hi, hi mid, mid hi,
 //                hi lo, lo hi, mid mid; the dropped ones are below 2^-24 of
-//                each product) accumulated in FP32 in tensor memory, per-split
-//                partial tiles in FP32;
+//                each product) accumulated in FP32 in tensor memory, the
+//                K-blocks of a CTA taken in turn by four accumulators (the
+//                accumulation error grows with an accumulator's magnitude and
+//                step count), per-split partial tiles in FP32;
 //   5. gram_diag / gram_out: the partials added as exact fixed-point
 //                integers in a fixed order, C_ij = S_ij / sqrt(S_ii S_jj)
 //                (FP64), diagonal 1, clamped to [-1, 1], both triangles.
@@ -35,7 +37,8 @@ constexpr int G_OP_BYTES = G_TILE * G_KB * 2; // one operand plane of a K-block:
 constexpr int G_STAGE = 6 * G_OP_BYTES;       // A hi/mid/lo + B hi/mid/lo: 96 KB
 constexpr int G_SMEM = 2 * G_STAGE + 1024;
 constexpr int G_THREADS = 128;
-constexpr int G_TMEM_COLS = 128;
+constexpr int G_NACC = 4;                      // accumulators, K-blocks taken in turn
+constexpr int G_TMEM_COLS = G_NACC * G_TILE;   // 512 columns
 constexpr int CT_ROWS = 256; // rows of R per column-statistics CTA
 
 // bits needed for T (T < 2^B)
@@ -284,7 +287,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
                 for (int p = 0; p < 6; ++p) {
                     const uint64_t ad = sw128_desc(sa + (uint32_t)pa[p] * G_OP_BYTES + 32 * kk);
                     const uint64_t bd = sw128_desc(sa + (uint32_t)(3 + pb[p]) * G_OP_BYTES + 32 * kk);
-                    mma_bf16(tmem, ad, bd, idesc, (kb > kb0 || kk || p) ? 1u : 0u);
+                    const int q = kb - kb0;
+                    mma_bf16(tmem + (uint32_t)((q % G_NACC) * G_TILE), ad, bd, idesc,
+                             (q >= G_NACC || kk || p) ? 1u : 0u);
                 }
             mma_commit(smem_u32(&mbar[s]));
         }
@@ -309,30 +314,41 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         __syncthreads();
     }
     if (!s_abort) {
+        // the used accumulators added in FP32 (each holds a quarter of the
+        // K-blocks, which keeps the accumulation error of the tensor cores,
+        // relative to the accumulator's magnitude and step count, small)
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int row = warp * 32 + (tid & 31);
+        const int nacc = min(G_NACC, kb1 - kb0);
         float *drow = dst + (size_t)row * G_TILE;
 #pragma unroll 1
         for (int q = 0; q < G_TILE / 32; ++q) {
-            uint32_t v[32];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
-                "%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                  "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                  "=r"(v[30]), "=r"(v[31])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + 32u * q));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float acc[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+#pragma unroll 1
+            for (int a = 0; a < nacc; ++a) {
+                uint32_t v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                    "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, "
+                    "%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+                      "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
+                      "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * G_TILE) + 32u * q));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < 32; ++c) acc[c] += __uint_as_float(v[c]);
+            }
             float4 *o = reinterpret_cast<float4 *>(drow + 32 * q);
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                o[c] = make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
-                                   __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
+                o[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
         }
     }
     __syncthreads();
