@@ -138,7 +138,7 @@ inline int pad_n(int N) { return (N + 63) & ~63; }
 // (where a full scoring is cheap) use the one-log product form without
 // tables. The choice depends on N alone, so every call path (single run,
 // fleet, stateless scoring) gives the same L for the same configuration.
-constexpr int DELTA_MIN_N = 192;
+constexpr int DELTA_MIN_N = 448;
 __host__ __device__ inline bool uses_delta(int N) { return N >= DELTA_MIN_N; }
 
 // fixed-point scale (bits) for the order-independent per-cluster sums of
