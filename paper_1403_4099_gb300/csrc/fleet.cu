@@ -71,6 +71,10 @@ struct Fleet {
     int dev = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // side stream and fork / join events: the generation kernel of the runs
+    // with score tables runs beside the one of the other runs
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     gpga_params prm{};
     int P = 0, E = 0, M = 0;
     int cap = 0, Nmax = 0, Np_max = 0;
@@ -190,6 +194,9 @@ static void fleet_destroy(Fleet *f)
         if (f->h_hdr[b]) cudaFreeHost(f->h_hdr[b]);
         if (f->h_st[b]) cudaFreeHost(f->h_st[b]);
     }
+    if (f->side) cudaStreamDestroy(f->side);
+    if (f->fork) cudaEventDestroy(f->fork);
+    if (f->join) cudaEventDestroy(f->join);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
     delete f;
 }
@@ -368,16 +375,27 @@ static int fleet_upload(Fleet *f, int b, long long tick)
 static int fleet_gen_launch(Fleet *f, int warps, int ctas, bool pdl = false)
 {
     const int prop = f->prm.scaling == GPGA_SCALING_PROP;
-    // runs with score tables (a fleet that may hold N >= DELTA_MIN_N) first
-    if (uses_delta(f->Nmax)) {
-        int rc = launch_fleet_generation_delta(f->d_runs, f->d_hdr, fleet_evolve_cfg(f),
-                                               f->rank_prefix, f->logtab, f->Np_max, prop,
-                                               f->stream);
-        if (rc) return rc;
-        pdl = false; // the next launch follows a kernel of its own
+    if (!uses_delta(f->Nmax))
+        return launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
+                                       f->logtab, f->Np_max, warps, ctas, prop, f->stream, pdl);
+    // a fleet that may hold runs with score tables (N >= DELTA_MIN_N): their
+    // items on the side stream, beside the other runs' items (fork / join)
+    if (!f->side) {
+        GPGA_CUDA(cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking));
+        GPGA_CUDA(cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming));
+        GPGA_CUDA(cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming));
     }
-    return launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
-                                   f->logtab, f->Np_max, warps, ctas, prop, f->stream, pdl);
+    GPGA_CUDA(cudaEventRecord(f->fork, f->stream));
+    GPGA_CUDA(cudaStreamWaitEvent(f->side, f->fork, 0));
+    int rc = launch_fleet_generation_delta(f->d_runs, f->d_hdr, fleet_evolve_cfg(f),
+                                           f->rank_prefix, f->logtab, f->Np_max, prop, f->side);
+    if (rc) return rc;
+    rc = launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
+                                 f->logtab, f->Np_max, warps, ctas, prop, f->stream, false);
+    if (rc) return rc;
+    GPGA_CUDA(cudaEventRecord(f->join, f->side));
+    GPGA_CUDA(cudaStreamWaitEvent(f->stream, f->join, 0));
+    return GPGA_OK;
 }
 
 // Autotuner: warps per CTA (individuals per CTA) and grid shape of the fused
