@@ -62,7 +62,12 @@ __host__ __device__ inline size_t delta_bytes(int Np)
     const size_t need = b > (size_t)Np ? b : (size_t)Np;
     return (need + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t gather_slice_bytes(int Np) { return (size_t)Np * 8 + delta_bytes(Np); }
+// slice of a warp: the delta region only where the per-cluster form runs
+// (N >= DELTA_MIN_N; its full path keeps the listed clusters' labels there)
+__host__ __device__ inline size_t gather_slice_bytes(int Np, bool delta)
+{
+    return (size_t)Np * 8 + (delta ? delta_bytes(Np) : 0);
+}
 
 constexpr uint16_t NO_SLOT = 0xffffu;
 
@@ -243,12 +248,12 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
                     const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
                     sl.cnt()[w0 + q] = (uint32_t)run | ((uint32_t)(run + x0) << 16);
                     if (x0 >= 2) {
-                        sl.lablist()[li] = (uint16_t)(2 * (w0 + q));
+                        if (!PROD) sl.lablist()[li] = (uint16_t)(2 * (w0 + q));
                         sl.list()[li++] = (run << 16) | x0;
                     }
                     run += x0;
                     if (x1 >= 2) {
-                        sl.lablist()[li] = (uint16_t)(2 * (w0 + q) + 1);
+                        if (!PROD) sl.lablist()[li] = (uint16_t)(2 * (w0 + q) + 1);
                         sl.list()[li++] = (run << 16) | x1;
                     }
                     run += x1;
@@ -856,7 +861,8 @@ __global__ void __launch_bounds__(256, 4)
     }
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
+    const GatherSlice sl =
+        gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np, uses_delta(N)), Np);
     const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *ktab = kfix_of(logtab);
     const int diag = *diag_flag;
@@ -1023,7 +1029,7 @@ __global__ void __launch_bounds__(128, 7)
     plan.g = g;
     const uint16_t *cur = (g & 1) ? pop1 : pop0;
     uint16_t *nxt = (g & 1) ? next1 : next0;
-    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np), Np);
+    const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np, delta), Np);
     generation_slot<true>(cur, nxt, cfg.N, cfg.ldp, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix,
                           *diag_flag, logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr,
                           use_pre ? &pre : nullptr);
@@ -1049,7 +1055,7 @@ __device__ __forceinline__ void fleet_items(const FleetRun *__restrict__ runs,
     griddep_wait();
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max);
+    unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max, DELTA);
     const int P = base.P;
     const int i0 = DELTA ? 0 : hdr->ndelta, i1 = DELTA ? hdr->ndelta : hdr->nitems;
     for (int item = i0 + blockIdx.x * nw + warp; item < i1; item += gridDim.x * nw) {
@@ -1097,9 +1103,9 @@ __global__ void __launch_bounds__(128, 6)
 // warps per CTA of the single-run gather kernels: 4 (measured at N=500,
 // P=4096: 1024 CTAs of 4 warps spread over the SMs more evenly than 512 of 8,
 // 4% less time per generation), fewer if the slices do not fit
-static int warps_for(int Np)
+static int warps_for(int Np, bool delta)
 {
-    const size_t per = gather_slice_bytes(Np);
+    const size_t per = gather_slice_bytes(Np, delta);
     int nw = 4;
     while (nw > 1 && nw * per > (size_t)200 * 1024) nw >>= 1;
     return nw;
@@ -1113,8 +1119,8 @@ int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, in
                         double *L, int *err, const DevState *st, unsigned long long *pairs,
                         const ScoreTab &tab, cudaStream_t s)
 {
-    const int nw = warps_for(Np);
-    const size_t smem = nw * gather_slice_bytes(Np);
+    const int nw = warps_for(Np, uses_delta(N));
+    const size_t smem = nw * gather_slice_bytes(Np, uses_delta(N));
     const int grid = (P + nw - 1) / nw;
     gather_score_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, P, N,
                                                           Np, Dfix, diag_flag, logtab, L, err,
@@ -1130,8 +1136,9 @@ int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2
                              unsigned long long *pairs, const ScoreTab &tab, bool pdl,
                              cudaStream_t s)
 {
-    const int nw = warps_for(Np);
-    const size_t smem = nw * gather_slice_bytes(Np);
+    const bool delta = tab.dbuf(0) != nullptr;
+    const int nw = warps_for(Np, delta);
+    const size_t smem = nw * gather_slice_bytes(Np, delta);
     const int grid = (cfg.P + nw - 1) / nw;
     GPGA_CUDA(launch_pdl(gather_generation_kernel, dim3(grid), dim3(32 * nw), smem, s, pdl,
                          pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, Dfix,
@@ -1142,14 +1149,14 @@ int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2
 int fleet_max_warps(int Np_max)
 {
     int nw = 16;
-    while (nw > 1 && nw * gather_slice_bytes(Np_max) > (size_t)200 * 1024) nw >>= 1;
+    while (nw > 1 && nw * gather_slice_bytes(Np_max, false) > (size_t)200 * 1024) nw >>= 1;
     return nw;
 }
 
 int fleet_ctas_per_sm(int Np_max, int warps, int *out)
 {
     GPGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        out, fleet_generation_kernel, 32 * warps, warps * gather_slice_bytes(Np_max)));
+        out, fleet_generation_kernel, 32 * warps, warps * gather_slice_bytes(Np_max, false)));
     return GPGA_OK;
 }
 
@@ -1159,7 +1166,7 @@ int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const Evo
 {
     if (warps < 1 || warps > 16 || ctas < 1)
         return set_error(GPGA_ERR_ARG, "fleet generation: %d warps x %d CTAs", warps, ctas);
-    const size_t smem = warps * gather_slice_bytes(Np_max);
+    const size_t smem = warps * gather_slice_bytes(Np_max, false);
     GPGA_CUDA(launch_pdl(fleet_generation_kernel, dim3(ctas), dim3(32 * warps), smem, s, pdl, runs,
                          hdr, cfg, rank_prefix, logtab, Np_max, prop));
     return GPGA_OK;
@@ -1170,7 +1177,7 @@ int launch_fleet_generation_delta(const FleetRun *runs, const FleetHdr *hdr, con
                                   int prop, cudaStream_t s)
 {
     const int warps = 4;
-    const size_t smem = warps * gather_slice_bytes(Np_max);
+    const size_t smem = warps * gather_slice_bytes(Np_max, true);
     int dev = 0, sms = 152, occ = 1;
     GPGA_CUDA(cudaGetDevice(&dev));
     GPGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
