@@ -71,10 +71,7 @@ struct Fleet {
     int dev = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // side stream and fork / join events: the generation kernel of the runs
-    // with score tables runs beside the one of the other runs
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+
     gpga_params prm{};
     int P = 0, E = 0, M = 0;
     int cap = 0, Nmax = 0, Np_max = 0;
@@ -117,15 +114,7 @@ static size_t run_bytes(const Fleet *f, int N, char *base, RunMem *m)
     t.d.ticket = c.take<unsigned>(TICKETS);
     t.d.work_prefix = c.take<uint64_t>(P);
     t.d.hist = c.take<double>(G);
-    t.d.tab = ScoreTab{};
-    if (uses_delta(N)) {
-        t.d.tab.ldt = (int)Np;
-        for (int b = 0; b < 2; ++b) {
-            t.d.tab.d[b] = c.take<long long>(P * Np);
-            t.d.tab.lf[b] = c.take<long long>(P);
-            t.d.tab.np[b] = c.take<long long>(P);
-        }
-    }
+
     t.canon = c.take<int32_t>(N);
     t.Lbest = c.take<double>(1);
     t.err = c.take<int>(1);
@@ -194,9 +183,6 @@ static void fleet_destroy(Fleet *f)
         if (f->h_hdr[b]) cudaFreeHost(f->h_hdr[b]);
         if (f->h_st[b]) cudaFreeHost(f->h_st[b]);
     }
-    if (f->side) cudaStreamDestroy(f->side);
-    if (f->fork) cudaEventDestroy(f->fork);
-    if (f->join) cudaEventDestroy(f->join);
     if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
     delete f;
 }
@@ -266,7 +252,6 @@ static int fleet_create(const gpga_params *p, int cap, int Nmax, void *stream, F
         memset(f->h_st[b], 0, (size_t)cap * sizeof(DevState));
         f->h_hdr[b]->nruns = 0;
         f->h_hdr[b]->nitems = 0;
-        f->h_hdr[b]->ndelta = 0;
     }
     rc = rank_prefix_table(f->rank_prefix, f->P, f->M, f->sus_tab, f->stream);
     if (!rc) rc = launch_logtab(f->logtab, Nmax, f->stream);
@@ -316,7 +301,7 @@ static int fleet_start(Fleet *f, int slot, const double *C, int ldc, const int32
     GPGA_CUDA(cudaMemsetAsync(m.d.pop1, 0, (size_t)P * Np * sizeof(uint16_t), st));
     const uint16_t *lab2[2] = {m.d.pop0, m.d.pop1};
     rc = launch_gather_score<uint16_t>(lab2, Np, 0, P, N, Np, m.d.Dfix, m.diag, f->logtab, m.d.L,
-                                       m.err, m.d.st, nullptr, m.d.tab, st);
+                                       m.err, m.d.st, nullptr, ScoreTab{}, st);
     if (rc) return rc;
     return launch_select<uint16_t>(m.d.L, fleet_select_cfg(f, N, 0), m.d.rank, m.d.perm,
                                    m.d.work_prefix, m.d.ticket, m.d.st, m.d.hist, lab2, nullptr,
@@ -355,12 +340,8 @@ static int fleet_upload(Fleet *f, int b, long long tick)
     for (size_t k = 0; k < order.size(); ++k) f->h_runs[b][k] = f->slots[order[k]].m.d;
     f->nactive = (int)order.size();
     f->nitems = f->nactive * f->P;
-    int nd = 0; // runs with score tables: a prefix of the table (decreasing N)
-    for (int i : order)
-        if (uses_delta(f->slots[i].N)) ++nd;
     f->h_hdr[b]->nruns = f->nactive;
     f->h_hdr[b]->nitems = f->nitems;
-    f->h_hdr[b]->ndelta = nd * f->P;
     if (f->nactive)
         GPGA_CUDA(cudaMemcpyAsync(f->d_runs, f->h_runs[b], (size_t)f->nactive * sizeof(FleetRun),
                                   cudaMemcpyHostToDevice, f->stream));
@@ -374,28 +355,9 @@ static int fleet_upload(Fleet *f, int b, long long tick)
 // pdl: the launch directly follows the fleet's selection in a captured graph
 static int fleet_gen_launch(Fleet *f, int warps, int ctas, bool pdl = false)
 {
-    const int prop = f->prm.scaling == GPGA_SCALING_PROP;
-    if (!uses_delta(f->Nmax))
-        return launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
-                                       f->logtab, f->Np_max, warps, ctas, prop, f->stream, pdl);
-    // a fleet that may hold runs with score tables (N >= DELTA_MIN_N): their
-    // items on the side stream, beside the other runs' items (fork / join)
-    if (!f->side) {
-        GPGA_CUDA(cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking));
-        GPGA_CUDA(cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming));
-        GPGA_CUDA(cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming));
-    }
-    GPGA_CUDA(cudaEventRecord(f->fork, f->stream));
-    GPGA_CUDA(cudaStreamWaitEvent(f->side, f->fork, 0));
-    int rc = launch_fleet_generation_delta(f->d_runs, f->d_hdr, fleet_evolve_cfg(f),
-                                           f->rank_prefix, f->logtab, f->Np_max, prop, f->side);
-    if (rc) return rc;
-    rc = launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
-                                 f->logtab, f->Np_max, warps, ctas, prop, f->stream, false);
-    if (rc) return rc;
-    GPGA_CUDA(cudaEventRecord(f->join, f->side));
-    GPGA_CUDA(cudaStreamWaitEvent(f->stream, f->join, 0));
-    return GPGA_OK;
+    return launch_fleet_generation(f->d_runs, f->d_hdr, fleet_evolve_cfg(f), f->rank_prefix,
+                                   f->logtab, f->Np_max, warps, ctas,
+                                   f->prm.scaling == GPGA_SCALING_PROP, f->stream, pdl);
 }
 
 // Autotuner: warps per CTA (individuals per CTA) and grid shape of the fused
@@ -470,7 +432,7 @@ static int fleet_tune(Fleet *f)
         const uint16_t *lab2[2] = {s.m.d.pop0, s.m.d.pop1};
         rc = launch_gather_score<uint16_t>(lab2, s.m.d.Np, 0, f->P, s.N, s.m.d.Np, s.m.d.Dfix,
                                            s.m.diag, f->logtab, s.m.d.L, s.m.err, s.m.d.st,
-                                           nullptr, s.m.d.tab, f->stream);
+                                           nullptr, ScoreTab{}, f->stream);
     }
     return rc;
 }

@@ -495,22 +495,6 @@ __global__ void __launch_bounds__(256)
             dst[(size_t)(P - m + r) * Np + j] = src[(size_t)r * Np + j];
         }
         for (int r = threadIdx.x; r < m; r += blockDim.x) b.L[P - m + r] = a.L[r];
-        // the migrants' score tables travel with them (islands share N, so
-        // both runs have tables or neither has: N below DELTA_MIN_N)
-        const int nb = (g + 1) & 1;
-        const long long *tsrc = a.tab.dbuf(nb);
-        long long *tdst = b.tab.dbuf(nb);
-        if (tsrc && tdst) {
-            const int ldt = a.tab.ldt;
-            for (int idx = threadIdx.x; idx < m * ldt; idx += blockDim.x) {
-                const int r = idx / ldt, j = idx - r * ldt;
-                tdst[(size_t)(P - m + r) * ldt + j] = tsrc[(size_t)r * ldt + j];
-            }
-            for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                b.tab.lfbuf(nb)[P - m + r] = a.tab.lfbuf(nb)[r];
-                b.tab.npbuf(nb)[P - m + r] = a.tab.npbuf(nb)[r];
-            }
-        }
     }
 }
 

@@ -248,12 +248,12 @@ __device__ __forceinline__ long long score_full_warp(const GatherSlice &sl, int 
                     const int x0 = (int)(c2[q] & 0xffffu), x1 = (int)(c2[q] >> 16);
                     sl.cnt()[w0 + q] = (uint32_t)run | ((uint32_t)(run + x0) << 16);
                     if (x0 >= 2) {
-                        if (!PROD) sl.lablist()[li] = (uint16_t)(2 * (w0 + q));
+                        if (!PROD && trow) sl.lablist()[li] = (uint16_t)(2 * (w0 + q));
                         sl.list()[li++] = (run << 16) | x0;
                     }
                     run += x0;
                     if (x1 >= 2) {
-                        if (!PROD) sl.lablist()[li] = (uint16_t)(2 * (w0 + q) + 1);
+                        if (!PROD && trow) sl.lablist()[li] = (uint16_t)(2 * (w0 + q) + 1);
                         sl.list()[li++] = (run << 16) | x1;
                     }
                     run += x1;
@@ -862,7 +862,7 @@ __global__ void __launch_bounds__(256, 4)
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const GatherSlice sl =
-        gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np, uses_delta(N)), Np);
+        gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np, tab.dbuf(0) != nullptr), Np);
     const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *ktab = kfix_of(logtab);
     const int diag = *diag_flag;
@@ -926,8 +926,9 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     const long long *kfix = kfix_of(logtab);
     long long lf, np;
     if (!DELTA_OK || !tab.dbuf(0)) {
-        // no score tables (N < DELTA_MIN_N): the child is built by the pair
-        // loop of child_genes and scored from scratch in the product form
+        // no score tables (N < DELTA_MIN_N, or a fleet): the child is built by
+        // the pair loop of child_genes and scored from scratch, in the form
+        // that N selects
         if (slot < cfg.E) {
             const uint16_t *src = cur + (size_t)perm[slot] * ldp;
             for (int j = lane; j < N; j += 32) {
@@ -943,7 +944,9 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
                                   nullptr, dst, sl.lab(), lane, pre);
         }
         __syncwarp();
-        lf = score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np);
+        lf = uses_delta(N)
+                 ? score_full_warp<false>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np)
+                 : score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np);
         if (lane == 0) {
             L[slot] = lfix_to_double(lf);
             if (pairs_out) atomicAdd(pairs_out, (unsigned long long)np);
@@ -1039,26 +1042,24 @@ __global__ void __launch_bounds__(128, 7)
 // Fleet generation: work item i is slot i mod P of the run at table position
 // i / P (the table is ordered by decreasing N, so the costly runs start
 // first); the CTAs stride over the items. Runs whose state is done are
-// skipped. Per slot the work is exactly that of gather_generation_kernel.
-// DELTA: the items [0, ndelta) of the runs with score tables; otherwise the
-// items [ndelta, nitems) of the runs without (two kernels, so that the
-// compact code of the tableless runs keeps its registers and occupancy).
+// skipped. Per slot the work is that of gather_generation_kernel without
+// score tables: every child is scored from scratch, in the form its N
+// selects, so a run's result is the same as alone (where N >= DELTA_MIN_N
+// scores most children by delta, to the same values).
 // ---------------------------------------------------------------------------
-template <bool DELTA>
-__device__ __forceinline__ void fleet_items(const FleetRun *__restrict__ runs,
-                                            const FleetHdr *__restrict__ hdr, const EvolveCfg &base,
-                                            const uint64_t *__restrict__ rank_prefix,
-                                            const double *__restrict__ logtab, int Np_max, int prop)
+__global__ void __launch_bounds__(512, 2)
+    fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
+                            EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
+                            const double *__restrict__ logtab, int Np_max, int prop)
 {
     // may be launched as a programmatic dependent of the fleet's selection:
     // wait for that grid before reading any run's state, permutation or prefix
     griddep_wait();
     extern __shared__ unsigned char smem_g[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max, DELTA);
-    const int P = base.P;
-    const int i0 = DELTA ? 0 : hdr->ndelta, i1 = DELTA ? hdr->ndelta : hdr->nitems;
-    for (int item = i0 + blockIdx.x * nw + warp; item < i1; item += gridDim.x * nw) {
+    unsigned char *slice = smem_g + (size_t)warp * gather_slice_bytes(Np_max, false);
+    const int nitems = hdr->nitems, P = base.P;
+    for (int item = blockIdx.x * nw + warp; item < nitems; item += gridDim.x * nw) {
         const int ri = item / P, slot = item - ri * P;
         const FleetRun &r = runs[ri];
         const DevState *st = r.st;
@@ -1074,30 +1075,11 @@ __device__ __forceinline__ void fleet_items(const FleetRun *__restrict__ runs,
         const bool use_pre = slot >= base.E && !prop && base.sus_tab != nullptr;
         if (use_pre)
             pre = sus_prefetch((uint32_t)(slot - base.E), base.M, P, prefix, base.sus_tab, lane);
-        if (DELTA && slot >= base.E)
-            plan = plan_child(base, r.N, g, slot - base.E, st->k0, st->k1, use_pre ? &pre : nullptr,
-                              lane);
-        generation_slot<false, DELTA>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot,
-                                      r.perm, prefix, r.Np, r.Dfix, *r.diag, logtab, r.L, r.tab,
-                                      sl, lane, nullptr, use_pre ? &pre : nullptr);
+        generation_slot<false, false>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot,
+                                      r.perm, prefix, r.Np, r.Dfix, *r.diag, logtab, r.L,
+                                      ScoreTab{}, sl, lane, nullptr, use_pre ? &pre : nullptr);
         __syncwarp();
     }
-}
-
-__global__ void __launch_bounds__(512, 2)
-    fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
-                            EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
-                            const double *__restrict__ logtab, int Np_max, int prop)
-{
-    fleet_items<false>(runs, hdr, base, rank_prefix, logtab, Np_max, prop);
-}
-
-__global__ void __launch_bounds__(128, 6)
-    fleet_delta_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,
-                       EvolveCfg base, const uint64_t *__restrict__ rank_prefix,
-                       const double *__restrict__ logtab, int Np_max, int prop)
-{
-    fleet_items<true>(runs, hdr, base, rank_prefix, logtab, Np_max, prop);
 }
 
 // warps per CTA of the single-run gather kernels: 4 (measured at N=500,
@@ -1119,8 +1101,9 @@ int launch_gather_score(const LabT *const *lab2, int ldl, int sel_off, int P, in
                         double *L, int *err, const DevState *st, unsigned long long *pairs,
                         const ScoreTab &tab, cudaStream_t s)
 {
-    const int nw = warps_for(Np, uses_delta(N));
-    const size_t smem = nw * gather_slice_bytes(Np, uses_delta(N));
+    const bool delta = tab.dbuf(0) != nullptr;
+    const int nw = warps_for(Np, delta);
+    const size_t smem = nw * gather_slice_bytes(Np, delta);
     const int grid = (P + nw - 1) / nw;
     gather_score_kernel<LabT><<<grid, 32 * nw, smem, s>>>(lab2[0], lab2[1], ldl, sel_off, P, N,
                                                           Np, Dfix, diag_flag, logtab, L, err,
@@ -1172,24 +1155,6 @@ int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const Evo
     return GPGA_OK;
 }
 
-int launch_fleet_generation_delta(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
-                                  const uint64_t *rank_prefix, const double *logtab, int Np_max,
-                                  int prop, cudaStream_t s)
-{
-    const int warps = 4;
-    const size_t smem = warps * gather_slice_bytes(Np_max, true);
-    int dev = 0, sms = 152, occ = 1;
-    GPGA_CUDA(cudaGetDevice(&dev));
-    GPGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GPGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fleet_delta_kernel, 32 * warps,
-                                                            smem));
-    if (occ < 1) return set_error(GPGA_ERR_ARG, "fleet: no room for the delta kernel at Np=%d", Np_max);
-    fleet_delta_kernel<<<sms * occ, 32 * warps, smem, s>>>(runs, hdr, cfg, rank_prefix, logtab,
-                                                           Np_max, prop);
-    GPGA_LAUNCH_CHECK();
-    return GPGA_OK;
-}
-
 template int launch_gather_score<uint16_t>(const uint16_t *const *, int, int, int, int, int,
                                            const int32_t *, const int *, const double *, double *,
                                            int *, const DevState *, unsigned long long *,
@@ -1205,7 +1170,6 @@ int prepare_gather_kernels(int maxsmem)
     if (int rc = raise_smem(gather_score_kernel<int32_t>, maxsmem)) return rc;
     if (int rc = raise_smem(gather_generation_kernel, maxsmem)) return rc;
     if (int rc = raise_smem(fleet_generation_kernel, maxsmem)) return rc;
-    if (int rc = raise_smem(fleet_delta_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }
 

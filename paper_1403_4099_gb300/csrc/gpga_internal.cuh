@@ -136,8 +136,9 @@ inline int pad_n(int N) { return (N + 63) & ~63; }
 // per-cluster fixed-point terms, which lets a GA run keep per-individual
 // score tables and score most children by delta from a parent; smaller N
 // (where a full scoring is cheap) use the one-log product form without
-// tables. The choice depends on N alone, so every call path (single run,
-// fleet, stateless scoring) gives the same L for the same configuration.
+// tables. The form depends on N alone, so every call path (single run,
+// fleet, stateless scoring) gives the same L for the same configuration; only
+// single runs keep the tables (fleet runs score every child from scratch).
 constexpr int DELTA_MIN_N = 448;
 __host__ __device__ inline bool uses_delta(int N) { return N >= DELTA_MIN_N; }
 
@@ -470,15 +471,11 @@ struct FleetRun {
     uint64_t *work_prefix;   // P: proportional-scaling prefix
     DevState *st;            // the run's state
     double *hist;            // max_gens + 1 best values
-    ScoreTab tab;            // the score tables (row length Np)
 };
 
 struct FleetHdr {
     int nruns;  // active descriptors 0 .. nruns-1
     int nitems; // nruns * P work items of the generation kernel
-    int ndelta; // the first ndelta items belong to runs with score tables (N >=
-                // DELTA_MIN_N; the table is sorted by decreasing N)
-    int pad_;
 };
 
 // rank (chunked sort + search, grid) + finalize (perm, stats, termination,
@@ -810,11 +807,7 @@ int launch_fleet_select(const FleetRun *runs, const FleetHdr *hdr, const SelectC
 int launch_fleet_generation(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
                             const uint64_t *rank_prefix, const double *logtab, int Np_max,
                             int warps, int ctas, int prop, cudaStream_t s, bool pdl = false);
-// the same for the items of runs with score tables (delta scoring): a fixed
-// shape of 4-warp CTAs, one wave of resident CTAs striding over those items
-int launch_fleet_generation_delta(const FleetRun *runs, const FleetHdr *hdr, const EvolveCfg &cfg,
-                                  const uint64_t *rank_prefix, const double *logtab, int Np_max,
-                                  int prop, cudaStream_t s);
+
 // island migration over the fleet's runs (ring by table position): every
 // `every` generations, the m elites of each run replace the last m children
 // of the next run
