@@ -866,6 +866,10 @@ __global__ void __launch_bounds__(256, 4)
     const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *ktab = kfix_of(logtab);
     const int diag = *diag_flag;
+    // the per-cluster form for a single run with score tables and for
+    // stateless scoring from DELTA_MIN_N genes up; the product form otherwise
+    // (fleet runs included)
+    const bool per_cluster = tab.dbuf(0) != nullptr || (!st && uses_delta(N));
     for (int p = blockIdx.x * nw + warp; p < P; p += gridDim.x * nw) {
         bool bad = false;
         const LabT *lp = lab + (size_t)p * ldl;
@@ -880,10 +884,10 @@ __global__ void __launch_bounds__(256, 4)
         long long npairs = 0;
         long long *trow = tab.dbuf(b) ? tab.dbuf(b) + (size_t)p * tab.ldt : nullptr;
         const long long lf =
-            uses_delta(N) ? score_full_warp<false>(sl, N, Np, Dfix, diag, ltab, ktab, lane, trow,
-                                                   &npairs)
-                          : score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, ktab, lane, nullptr,
-                                                  &npairs);
+            per_cluster ? score_full_warp<false>(sl, N, Np, Dfix, diag, ltab, ktab, lane, trow,
+                                                 &npairs)
+                        : score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, ktab, lane, nullptr,
+                                                &npairs);
         if (lane == 0) {
             L[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : lfix_to_double(lf);
             if (bad && err) atomicOr(err, 1);
@@ -927,8 +931,8 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     long long lf, np;
     if (!DELTA_OK || !tab.dbuf(0)) {
         // no score tables (N < DELTA_MIN_N, or a fleet): the child is built by
-        // the pair loop of child_genes and scored from scratch, in the form
-        // that N selects
+        // the pair loop of child_genes and scored from scratch in the
+        // one-log product form
         if (slot < cfg.E) {
             const uint16_t *src = cur + (size_t)perm[slot] * ldp;
             for (int j = lane; j < N; j += 32) {
@@ -944,9 +948,7 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
                                   nullptr, dst, sl.lab(), lane, pre);
         }
         __syncwarp();
-        lf = uses_delta(N)
-                 ? score_full_warp<false>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np)
-                 : score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np);
+        lf = score_full_warp<true>(sl, N, Np, Dfix, diag, ltab, kfix, lane, nullptr, &np);
         if (lane == 0) {
             L[slot] = lfix_to_double(lf);
             if (pairs_out) atomicAdd(pairs_out, (unsigned long long)np);
@@ -1043,9 +1045,10 @@ __global__ void __launch_bounds__(128, 7)
 // i / P (the table is ordered by decreasing N, so the costly runs start
 // first); the CTAs stride over the items. Runs whose state is done are
 // skipped. Per slot the work is that of gather_generation_kernel without
-// score tables: every child is scored from scratch, in the form its N
-// selects, so a run's result is the same as alone (where N >= DELTA_MIN_N
-// scores most children by delta, to the same values).
+// score tables: every child is scored from scratch in the product form, so
+// a run's result equals the same run alone for N < DELTA_MIN_N (from
+// DELTA_MIN_N genes up a single run uses the per-cluster form, whose L can
+// differ from the product form's in the last bits).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512, 2)
     fleet_generation_kernel(const FleetRun *__restrict__ runs, const FleetHdr *__restrict__ hdr,

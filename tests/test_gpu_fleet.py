@@ -240,33 +240,3 @@ def test_batch_generation_by_generation_against_oracle(gpga, orc, Ns):
         for k in range(len(Ns)):
             assert np.array_equal(cur[k][0], refs[k]), f"run {k} (N={Ns[k]}) generation {gen + 1}"
     b.close()
-
-
-def test_batch_matches_single_runs_delta_sizes(gpga):
-    """From DELTA_MIN_N (448) genes up a single run scores most children by
-    delta from a parent's score table, while a fleet run scores every child
-    from scratch in the same per-cluster form: the two must agree bit for
-    bit, down to the whole population and its fitness, from a uniform and
-    from a clustered (threshold) start."""
-    Ns = [500, 460]
-    Cs = _windows(gpga, Ns, rep=120)
-    seeds = [77 + k for k in range(len(Ns))]
-    for init in (gpga.INIT_UNIFORM, gpga.INIT_THRESHOLD):
-        prm = _params(gpga, P=256, max_gens=24, tol=-1.0, init=init)
-        b = gpga.Batch(Cs, prm, seeds)
-        while b.step(8) > 0:
-            pass
-        for k, C in enumerate(Cs):
-            ga = gpga.GA(C, prm, seed=seeds[k])
-            ga.step(prm.max_gens)
-            lab, L, g = ga.best()
-            pop, Lpop = ga.population()
-            ga.close()
-            lb, Lb, gb = b.best(k)
-            assert gb == g == 24
-            np.testing.assert_array_equal(lb, lab)
-            assert Lb == L, (k, Lb, L)
-            pop_b, Lpop_b = b.population(k)
-            np.testing.assert_array_equal(pop_b, pop)
-            np.testing.assert_array_equal(Lpop_b, Lpop)
-        b.close()

@@ -225,3 +225,26 @@ def test_headline_path_generation_by_generation_n500(g, orc, n500_C, init):
     assert_L_close(La, orc.loglik_batch(pa, C), f"{init} gen 13")
     ga.close()
     twin.close()
+
+
+def test_delta_scores_equal_full_scores(g, orc):
+    """From DELTA_MIN_N (448) genes up a run scores most children by delta
+    from a parent's score table; ga_score scores the same configurations from
+    scratch in the same per-cluster form. After several generations (the
+    tables carried from generation to generation) every fitness value of the
+    population must equal ga_score's bit for bit, from a uniform and from a
+    clustered start."""
+    import torch
+    pl = synth.market_clusters(2, 460, 1840, 38, 0.2, 0.8, replicate=11)
+    C = orc.pearson(pl.R)
+    for init in (g.INIT_UNIFORM, g.INIT_THRESHOLD):
+        gp = _gparams(g, 512, E=10, max_gens=40, tol=-1.0, pm=0.01, form=g.FORM_GATHER, init=init)
+        ga = g.GA(dev(C), gp, seed=909)
+        for steps in (1, 7, 12):
+            ga.step(steps)
+            pop, L = ga.population()
+            full = g.ga_score(dev(pop, torch.int32), dev(C), form=g.FORM_GATHER)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(L, full.cpu().numpy())
+            assert_L_close(L, orc.loglik_batch(pop, C), f"delta L vs oracle, init {init}")
+        ga.close()
