@@ -345,9 +345,8 @@ def run_gpu(args, ranks):
 
     # recovery within the timed step itself (first generation whose best
     # individual has ARI >= 0.99 vs the planted labels)
-    g_rec, ms_step_rec, ari_best, _ = first_recovery(hist, planted.truth)
-    ms_rec = {"within_timed_step": {"generations": G, "generation": g_rec, "ms": ms_step_rec,
-                                    "best_ari": ari_best}}
+    rec = first_recovery(hist, planted.truth)
+    ms_rec = {"within_timed_step": {"generations": G, **rec}}
 
     # end-to-end leg on every rank, aggregated like the device-timed value
     runtime.barrier(ranks)
@@ -496,30 +495,54 @@ RECOVER_CONFIGS = (
 RECOVER_SEEDS = (101, 202, 303)
 
 
+def planted_members(truth):
+    """Mask of the genes that belong to a planted cluster (two or more members);
+    the noise series are planted as singletons and have no cluster to recover."""
+    t = np.asarray(truth)
+    return np.bincount(t, minlength=t.max() + 1)[t] >= 2
+
+
 def first_recovery(h, truth):
-    """(generation, device ms from the start of ga_reset to the end of that
-    generation) of the first best configuration with ARI >= 0.99 (None if
-    none), and the best ARI with its generation."""
+    """Recovery of the planted clusters along a run's records: the generation and
+    device ms (from the start of ga_reset to the end of that generation) of the
+    first best configuration whose ARI over the members of the planted clusters
+    is >= 0.99 (None if none), with the best such ARI and its generation, and
+    the ARI over all N genes (noise series included) at the same points. The
+    noise series are left out of the criterion because the likelihood itself
+    places them in clusters: on the n500 workload each of them raises L by
+    joining one, so the likelihood's optimum is not the planted partition over
+    all N (pinned by the oracle tests)."""
     from paper_1403_4099_gb300 import metrics
     labs = h["labels"]
-    ari = np.empty(len(labs))
-    prev, prev_a = None, 0.0
+    mem = planted_members(truth)
+    ari_m = np.empty(len(labs))
+    ari_all = np.empty(len(labs))
+    prev, prev_m, prev_a = None, 0.0, 0.0
     for g, l in enumerate(labs):
         if prev is None or not np.array_equal(l, prev):  # the best changes rarely
-            prev, prev_a = l, metrics.ari(l, truth)
-        ari[g] = prev_a
-    hit = np.flatnonzero(ari >= 0.99)
+            prev = l
+            prev_m = metrics.ari(l[mem], truth[mem])
+            prev_a = metrics.ari(l, truth)
+        ari_m[g] = prev_m
+        ari_all[g] = prev_a
+    hit = np.flatnonzero(ari_m >= 0.99)
     g0 = int(hit[0]) if hit.size else None
     ms = None if g0 is None else float(h["t_ns"][1 + g0] - h["t_ns"][0]) / 1e6
-    return g0, ms, float(ari.max()), int(ari.argmax())
+    gb = int(ari_m.argmax())
+    return {"generation": g0, "ms": ms, "best_ari_members": float(ari_m[gb]),
+            "best_ari_members_generation": gb,
+            "ari_all_genes_at_recovery": None if g0 is None else float(ari_all[g0]),
+            "best_ari_all_genes": float(ari_all.max()),
+            "best_L_final": float(h["best_L"][-1])}
 
 
 def run_recover(args, ranks, planted, dev, form):
     """Recovery of the planted clusters by the GA itself (Algorithm 1 from the
     uniform initial population): for each workload and seed, device time from
     the start of ga_reset to the first generation whose best individual has
-    ARI >= 0.99 against the planted partition (stall rule off, up to a cap of
-    generations). Also the correlation-threshold initialiser, reported apart:
+    ARI >= 0.99 against the planted partition over the members of the planted
+    clusters (stall rule off, up to a cap of generations); the ARI over all N
+    genes and the planted partition's own L are reported beside it. Also the correlation-threshold initialiser, reported apart:
     it is a single-linkage cut of C and recovers the partition before any GA
     operator runs (generation 0)."""
     import torch
@@ -542,16 +565,18 @@ def run_recover(args, ranks, planted, dev, form):
                 ga.reset(Cw, sd)
                 ga.step(cap)
                 h = ga.history()
-                g0, ms, best, gbest = first_recovery(h, pl.truth)
-                runs.append({"seed": sd, "generation": g0, "ms": ms, "best_ari": best,
-                             "best_ari_generation": gbest,
+                runs.append({"seed": sd, **first_recovery(h, pl.truth),
                              "ms_per_generation": float(h["t_ns"][-1] - h["t_ns"][0]) / 1e6 /
                                                   (len(h["t_ns"]) - 1)})
             ga.close()
+            # the planted partition's own L (gather form on the device), beside
+            # the best L the runs end with
+            tl = torch.from_numpy(pl.truth.astype(np.int32)[None]).to(dev)
+            L_pl = float(gpga.ga_score(tl, Cw, gpga.FORM_GATHER, stream=stream).cpu()[0])
             ok = [r["ms"] for r in runs if r["ms"] is not None]
             out["uniform_init"][name] = {
                 "N": Nw, "P": Pw, "elite": Ew, "generation_cap": cap,
-                "initial_labels": K0 or Nw,
+                "initial_labels": K0 or Nw, "L_planted_partition": L_pl,
                 "recovered": f"{len(ok)}/{len(runs)}",
                 "median_ms": float(np.median(ok)) if ok else None,
                 "runs": runs}
@@ -573,12 +598,12 @@ def run_recover(args, ranks, planted, dev, form):
         ga.step(50)
         h = ga.history()
         ga.close()
-    g0, ms, best, _ = first_recovery(h, planted.truth)
+    rec = first_recovery(h, planted.truth)
     out["single_linkage_initialiser"] = {
         "what": "correlation-threshold initial population (components of C > tau_p, a "
                 "single-linkage cut); recovers before any GA operator runs",
-        "ms": ms, "generation": g0, "best_ari": best, "prelude_ms": corr_ms,
-        "ms_with_prelude": None if ms is None else ms + corr_ms}
+        **rec, "prelude_ms": corr_ms,
+        "ms_with_prelude": None if rec["ms"] is None else rec["ms"] + corr_ms}
     return out
 
 
