@@ -200,8 +200,10 @@ def gather_roofline(launch_ms, pk, pk_kind, pairs_per_gen, sm_mhz=None):
 DTYPE = {
     "gather": ("int64", "pair sums of D = 1 - C as int32 fixed point 2^-30 added in int64 "
                         "(exact); Eq. 8 assembled in integer fixed point (Q62 table log, "
-                        "result in Q40); FP64 column statistics in the Pearson prelude (FP32 "
-                        "Gram); integer GA operators"),
+                        "result in Q40); Pearson prelude: integer column statistics, the "
+                        "centred returns split three ways into BF16 on tcgen05 with FP32 "
+                        "accumulation and exact fixed-point partial sums; integer GA "
+                        "operators"),
     "plain": ("f32", "FP32 pair accumulation of D = 1 - C, fixed-point per-cluster sums, "
                      "integer Eq. 8 assembly; integer GA operators"),
     "tensor": ("bf16", "one-hot x D split BF16 hi + lo on tcgen05, FP32 accumulation in TMEM, "
@@ -678,7 +680,8 @@ def run_batched(args, ranks):
                 "value": B_WINDOWS * ranks.world / max_secs, "unit": "windows/s",
                 "n_gpus": ranks.world, "steps": len(times), "warmup": 1,
                 "ms_per_step": 1e3 * max_secs, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": DTYPE["gather"][0],
+                "dtype_detail": DTYPE["gather"][1], "data": "synthetic",
                 "config": {"workload": "intraday_n400_w390_s30_x256_p1024", "P": B_P,
                            "N_range": [20, B_N], "windows": B_WINDOWS, "form": "gather"},
                 "evals_per_s": total_evals / max_secs,
@@ -768,7 +771,8 @@ def run_serving(args, ranks):
                           "<=300 generations or stall)",
                 "value": total / max_wall, "unit": "windows/s", "n_gpus": ranks.world,
                 "steps": 1, "warmup": 1, "ms_per_step": 1e3 * max_wall,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE["gather"][0], "dtype_detail": DTYPE["gather"][1],
                 "data": "synthetic",
                 "config": {"workload": "serving_poisson", "rate_per_s": rate, "seconds": dur,
                            "requests": int(arr.shape[0]), "P": S_P, "Ns": list(S_NS)},
@@ -871,7 +875,8 @@ def run_paper(args, ranks):
                           "parameters, each run to 400 generations or stall)",
                 "value": total / max_secs, "unit": "windows/s", "n_gpus": ranks.world,
                 "steps": 1, "warmup": 0, "ms_per_step": 1e3 * max_secs,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE["gather"][0], "dtype_detail": DTYPE["gather"][1],
                 "data": "synthetic",
                 "config": {"workload": "paper_stream_n18_w1800_x1760_p1000", "P": 1000,
                            "max_gens": 400, "pm": 0.1, "pc": 0.9, "pkb": 0.9, "elite": 10},
@@ -1050,7 +1055,8 @@ def run_islands(args, ranks):
                 "value": total / max_t, "unit": "evals/s", "n_gpus": ranks.world,
                 "steps": len(res_i), "warmup": 1, "ms_per_step": 1e3 * max_t,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
+                "dtype": DTYPE["gather"][0],
+                "dtype_detail": DTYPE["gather"][1], "data": "synthetic",
                 "config": {"workload": "islands_n100_t2000_k8_p512_g200", "migrate_every": 10,
                            "migrants": 2, "pm": 0.01},
                 "islands": summary(res_i),

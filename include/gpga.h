@@ -384,11 +384,16 @@ GPGA_API int ga_free(gpga_ga *h);
 /* ------------------------------------------------------------------------
  * Batch: many independent GA runs (e.g. one per sliding window of a returns
  * series, each window's C being the input of one run as in Sec. 4.2) advanced
- * together. Each run is exactly the single-run gather form with its own C, N
- * and seed: same parameters as ga_init (p->form must be GPGA_FORM_GATHER;
- * record and profile must be 0), and bit-for-bit the same result as ga_init +
- * ga_step on that run alone. One generation of all runs is two kernel
- * launches, captured in a CUDA graph; the launch shape of the fused
+ * together. Each run is the single-run gather form with its own C, N and
+ * seed: same parameters as ga_init (p->form must be GPGA_FORM_GATHER; record
+ * and profile must be 0). A run of N < 448 genes gives bit-for-bit the result
+ * of ga_init + ga_step on that run alone. From 448 genes up a single run
+ * scores Eq. 8 as a sum of per-cluster fixed-point terms (so that it can score
+ * children by delta from a parent), while a batch run scores every child from
+ * scratch in the one-log product form; the two agree to about 1e-12 in L, so
+ * such a run can take a different path from the single run once two
+ * individuals' order depends on the last bits. One generation of all runs
+ * is two kernel launches, captured in a CUDA graph; the launch shape of the fused
  * generation kernel (warps per CTA, CTAs) is chosen at init by timing the
  * candidates on the runs themselves.
  * ------------------------------------------------------------------------ */
