@@ -109,13 +109,15 @@ GPGA_API const char *gpga_last_error(void);
 
 /*
  * gpga_set_wait_budget -- failure detection; the paper has no counterpart.
- * Every wait of a kernel of this library on an on-chip barrier (the mbarrier
- * hand-offs of the tcgen05 pipeline of GPGA_FORM_TENSOR) gives up once it has
- * spent `cycles` SM clock cycles: the kernel then stops issuing work, waits
+ * Every wait of a kernel of this library on a barrier (the mbarrier hand-offs
+ * of the tcgen05 pipelines of GPGA_FORM_TENSOR and of the Pearson prelude, and
+ * the grid barrier of corr_clean_rmt's tridiagonal reduction) gives up once it
+ * has spent `cycles` SM clock cycles: the kernel then stops issuing work, waits
  * (with the full default bound) for the tensor-core operations it has already
  * issued, releases its tensor memory and returns; the call reports
- * GPGA_ERR_TIMEOUT (ga_score at once; a GA run at ga_step with `done` or at
- * ga_best) and the device context stays usable. cycles = 0 makes every such
+ * GPGA_ERR_TIMEOUT (ga_score, cluster_corr and corr_clean_rmt at once; a GA
+ * run at ga_step with `done` or at ga_best) and the device context stays
+ * usable. cycles = 0 makes every such
  * wait give up at its first check; cycles < 0 restores the default, 2^32
  * cycles (about 2 s at the maximum SM clock). Process-wide; applies to kernels
  * launched after the call, and a GA handle's generation graphs keep the budget
@@ -300,21 +302,31 @@ GPGA_API int corr_remove_market(double *C, int N, int max_iters, double *lambda1
  * (Sec. 4.2: the eigenvalues in the Wishart range are removed in a
  * trace-preserving way) of `batch` correlation matrices in place. C: device,
  * batch x N x N FP64, each symmetric, estimated from T observations.
- * Per matrix: the eigen-decomposition C = sum_k lambda_k v_k v_k^T (parallel
- * cyclic Jacobi in FP64 until every off-diagonal entry is below 1e-14
- * ||A||_F); the noise set is the eigenvalues inside the Marchenko-Pastur range
+ * Per matrix: the eigen-decomposition C = sum_k lambda_k v_k v_k^T in FP64;
+ * the noise set is the eigenvalues inside the Marchenko-Pastur range
  * [(1 - sqrt q)^2, (1 + sqrt q)^2], q = N / T, and they are replaced by their
  * mean m: C' = m I + sum_{k not noise} (lambda_k - m) v_k v_k^T (same trace);
  * then C <- C'_ij / sqrt(C'_ii C'_jj), clamped to [-1, 1], unit diagonal. A
- * matrix with an empty noise set is left unchanged.
+ * matrix with an empty noise set is left unchanged. Two solvers: up to 32
+ * stocks, or 33 to 127 stocks in batches of more than 4, the batch goes
+ * through parallel cyclic Jacobi together (until every off-diagonal entry is
+ * below 1e-14 ||A||_F); otherwise each matrix in turn is reduced to
+ * tridiagonal form (Householder), its eigenvalues found by bisection and the
+ * eigenvectors of the smaller of the kept and noise sets by inverse iteration
+ * (C' then formed as C - sum_{noise} (lambda_k - m) v_k v_k^T when the noise
+ * set is the smaller one).
  * eigvals (device, optional, batch x N): the input's eigenvalues, ascending.
  * n_noise (host, optional, batch): the noise-set sizes. sweeps (host,
- * optional): Jacobi sweeps run (the batch sweeps together).
+ * optional): Jacobi sweeps run (the batch sweeps together); 0 when the
+ * tridiagonal solver ran.
  * Errors: GPGA_ERR_ARG (NULL or host C, batch outside [1, 65535], N outside
- * [2, GPGA_MAX_N], T not positive, a non-finite entry), GPGA_ERR_DEGENERATE
- * (no convergence in 40 sweeps, or a non-positive diagonal after the
- * cleaning). Device scratch of 3 batch n2^2 doubles (n2 = N rounded up to
- * even). Blocks the host until the stream reaches the end of the call.
+ * [2, GPGA_MAX_N], T not positive, a non-finite entry; C is left unchanged),
+ * GPGA_ERR_DEGENERATE (no Jacobi convergence in 40 sweeps, or a non-positive
+ * diagonal after the cleaning), GPGA_ERR_TIMEOUT (a bounded grid barrier of
+ * the tridiagonal reduction gave up, see gpga_set_wait_budget; C is left
+ * unchanged). Device scratch: 3 batch n2^2 doubles (Jacobi, n2 = N rounded up
+ * to even) or about 4.5 N^2 doubles (tridiagonal). Blocks the host until the
+ * stream reaches the end of the call.
  */
 GPGA_API int corr_clean_rmt(double *C, int batch, int N, double T, double *eigvals, int *n_noise,
                            int *sweeps, void *stream);

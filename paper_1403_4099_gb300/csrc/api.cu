@@ -100,6 +100,7 @@ int prepare_device()
     if (!rc) rc = prepare_tc_kernels(maxsmem);
     if (!rc) rc = prepare_gather_kernels(maxsmem);
     if (!rc) rc = prepare_corr_kernels(maxsmem);
+    if (!rc) rc = prepare_rmt_tri_kernels(maxsmem);
     if (rc) return rc;
     ready[dev] = true;
     return GPGA_OK;

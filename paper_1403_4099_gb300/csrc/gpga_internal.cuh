@@ -411,6 +411,10 @@ int market_remove(double *C, int N, int max_iters, double *lambda1, int *iters, 
 // B, optional) the noise-set sizes; sweeps (host, optional) Jacobi sweeps run
 int rmt_clean(double *C, int B, int N, double T, double *eig_sorted, int *n_noise, int *sweeps,
               cudaStream_t s);
+// the same through a tridiagonal reduction, one matrix at a time (rmt_tri.cu)
+int rmt_clean_tri(double *C, int B, int N, double T, double *eig_sorted, int *n_noise,
+                  cudaStream_t s);
+int prepare_rmt_tri_kernels(int maxsmem);
 
 
 // ---------------------------------------------------------------------------

@@ -362,9 +362,28 @@ __global__ void rmt_normalise_kernel(const double *__restrict__ Cp, int N, int n
     }
 }
 
+int rmt_normalise(const double *Cp, int B, int N, int n2, const int *ncount, double *C, int *err,
+                  cudaStream_t s)
+{
+    int blocks = (int)(((size_t)N * N + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    rmt_normalise_kernel<<<dim3(blocks, B), 256, 0, s>>>(Cp, N, n2, ncount, C, err);
+    GPGA_LAUNCH_CHECK();
+    return GPGA_OK;
+}
+
+// the Jacobi rounds of a sweep cost a launch each once a matrix spans more
+// than one 32 x 32 tile; from there a few matrices go through the tridiagonal
+// reduction of rmt_tri.cu (one matrix at a time), large batches stay here
+static bool use_tridiagonal(int B, int N) { return N > 2 * JT && (N >= 128 || B <= 4); }
+
 int rmt_clean(double *C, int B, int N, double T, double *eig_sorted, int *n_noise, int *sweeps,
               cudaStream_t s)
 {
+    if (use_tridiagonal(B, N)) {
+        if (sweeps) *sweeps = 0;
+        return rmt_clean_tri(C, B, N, T, eig_sorted, n_noise, s);
+    }
     const int n2 = (N + 1) & ~1, h = n2 >> 1, tiles = (h + JT - 1) / JT;
     const size_t stride = (size_t)n2 * n2;
     const size_t mat = (size_t)B * stride * sizeof(double);

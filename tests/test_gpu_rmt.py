@@ -150,3 +150,97 @@ def test_clean_rejects_bad_input(g):
         g.corr_clean_rmt(dev(bad), 100)
     with pytest.raises(TypeError):
         g.corr_clean_rmt(torch.eye(8, dtype=torch.float64), 100)  # host memory
+
+
+# ---------------------------------------------------------------------------
+# The tridiagonal solver (Householder reduction, bisection, inverse iteration),
+# which cleans one matrix at a time from 33 stocks up (and every batch from
+# 128 stocks up): the cases above with N > 32 already run it; these add its
+# own edge cases.
+# ---------------------------------------------------------------------------
+def test_tri_known_spectrum(g, orc):
+    """A random orthogonal basis with a prescribed spectrum (no eigenvalue near
+    a range edge): the eigenvalues come back to 1e-12 and C' matches."""
+    N, T = 80, 400
+    rng = np.random.default_rng(23)
+    Q, R = np.linalg.qr(rng.standard_normal((N, N)))
+    Q = Q * np.sign(np.diag(R))
+    lo, hi = orc.wishart_range(N, T)
+    lam = np.concatenate([np.linspace(0.05, lo - 0.05, 10), np.linspace(lo + 0.05, hi - 0.05, 60),
+                          np.linspace(hi + 0.1, 9.0, 10)])
+    C = (Q * lam) @ Q.T
+    C = 0.5 * (C + C.T)
+    got, n_ref = _check(g, orc, C, T)
+    assert n_ref == 60
+
+
+def test_tri_exact_multiplicity_in_the_expanded_set(g, orc):
+    """One block of 10 stocks at correlation 0.9 among 110 independent ones:
+    the kept set is 0.1 nine times over (exactly) and 9.1; the noise set is 1
+    110 times, equal to its mean, so C' = C. Inverse iteration must span the
+    nine-fold eigenspace (distinct starts, Gram-Schmidt in the group)."""
+    N, T = 120, 1200
+    C = np.eye(N)
+    C[:10, :10] = 0.9
+    np.fill_diagonal(C, 1.0)
+    Cd = dev(C)
+    ev, nn, sweeps = g.corr_clean_rmt(Cd, T)
+    assert nn == [110] and sweeps == 0
+    assert np.max(np.abs(ev.cpu().numpy()[0] - np.sort(np.linalg.eigvalsh(C)))) < 1e-12
+    ref, _, _ = orc.clean_rmt(C, T)
+    assert np.max(np.abs(Cd.cpu().numpy() - ref)) < C_TOL
+    assert np.max(np.abs(Cd.cpu().numpy() - C)) < C_TOL
+
+
+def test_tri_identity_and_empty_range(g, orc):
+    N = 100
+    Cd = dev(np.eye(N))
+    _, nn, sweeps = g.corr_clean_rmt(Cd, 1000)
+    assert nn == [N] and sweeps == 0
+    assert np.array_equal(Cd.cpu().numpy(), np.eye(N))
+    C = 0.5 * np.ones((N, N)) + 0.5 * np.eye(N)
+    Cd = dev(C)
+    _, nn, _ = g.corr_clean_rmt(Cd, 5000)  # range [0.7, 1.3]: 0.5 and 50.5 outside
+    assert nn == [0]
+    assert np.array_equal(Cd.cpu().numpy(), C)  # untouched
+
+
+def test_tri_small_batch_matches_oracle_one_by_one(g, orc):
+    """Three matrices of 150 stocks in one call (the tridiagonal solver takes
+    them in turn)."""
+    Cs = []
+    for k in range(3):
+        pl = synth.planted_returns(np.random.default_rng(300 + k), 600, [40, 30, 20], [0.6, 0.4, 0.3],
+                                   n_noise=60, beta=0.25)
+        Cs.append(orc.pearson(pl.R))
+    nn = _batch_check(g, orc, Cs, 600)
+    assert min(nn) > 0
+
+
+def test_tri_rejects_non_finite_and_leaves_c(g):
+    bad = np.eye(64)
+    bad[5, 9] = bad[9, 5] = np.inf
+    Cd = dev(bad)
+    with pytest.raises(g.GpgaError) as e:
+        g.corr_clean_rmt(Cd, 500)
+    assert e.value.code == g.ERR_ARG
+    assert np.array_equal(Cd.cpu().numpy(), bad)
+
+
+def test_tri_timeout_then_recovers(g, orc):
+    """A wait budget of 0 cycles makes the reduction's first grid barrier give
+    up at once (nothing hangs): GPGA_ERR_TIMEOUT and C unchanged; with the
+    default budget the same call then matches the oracle."""
+    pl = synth.n100()
+    C = orc.pearson(pl.R)
+    T = pl.R.shape[0]
+    Cd = dev(C)
+    g.set_wait_budget(0)
+    try:
+        with pytest.raises(g.GpgaError) as e:
+            g.corr_clean_rmt(Cd, T)
+    finally:
+        g.set_wait_budget(-1)
+    assert e.value.code == g.ERR_TIMEOUT
+    assert np.array_equal(Cd.cpu().numpy(), C)
+    _check(g, orc, C, T)
