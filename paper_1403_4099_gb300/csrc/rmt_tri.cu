@@ -130,8 +130,10 @@ __device__ void householder(const double *x, int n, double *u, double *red, doub
     } else {
         const double mu = sqrt(x0 * x0 + sig2);
         const double bt = x0 >= 0.0 ? -mu : mu;
-        const double inv = 1.0 / (x0 - bt);
-        *tau = (bt - x0) / bt;
+        const double dn = x0 - bt;             // |dn| >= |bt| > 0
+        const double q = 1.0 / (bt * dn);      // one division for both reciprocals
+        const double inv = bt * q;             // 1 / (x0 - beta)
+        *tau = -dn * (dn * q);                 // (beta - x0) / beta
         *beta = bt;
         for (int j = threadIdx.x; j < n; j += blockDim.x) u[j] = j == 0 ? 1.0 : x[j] * inv;
     }
@@ -772,37 +774,35 @@ __global__ void __launch_bounds__(BACK_THREADS)
 }
 
 // Step 6b. Cp = base + sum_s w_s v_s v_s^T, base = C (noise set expanded) or
-// m I (kept set), 32 x 32 tiles of the upper triangle written to both
-// triangles; nothing to do with an empty noise set
+// m I (kept set), 32 x 32 tiles of the upper triangle (w_s folded into the
+// staged j operand: one FMA per term); entries with i <= j are written to
+// both triangles, so C' is exactly symmetric. Nothing to do with an empty
+// noise set.
 __global__ void __launch_bounds__(256)
     tri_rebuild_kernel(const double *__restrict__ V, int N, const int *__restrict__ info,
                        const double *__restrict__ w, const double *__restrict__ mean,
                        const double *__restrict__ C, double *__restrict__ Cp)
 {
     __shared__ double si[TRI_TILE][TRI_TILE + 1], sj[TRI_TILE][TRI_TILE + 1];
-    __shared__ double sw[TRI_TILE];
-    if (info[3] == 0 || blockIdx.x < blockIdx.y) return; // upper tiles, mirrored
+    if (info[3] == 0 || blockIdx.x < blockIdx.y) return;
     const int K = info[0];
     const bool noise_form = info[2] != 0;
     const int i0 = blockIdx.y * TRI_TILE, j0 = blockIdx.x * TRI_TILE;
-    const bool diag_tile = blockIdx.x == blockIdx.y;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int s0 = 0; s0 < K; s0 += TRI_TILE) {
         for (int r = ty; r < TRI_TILE; r += 8) {
             const int s = s0 + r;
-            si[r][tx] = (s < K && i0 + tx < N) ? V[(size_t)s * N + i0 + tx] : 0.0;
-            sj[r][tx] = (s < K && j0 + tx < N) ? V[(size_t)s * N + j0 + tx] : 0.0;
+            const bool in = s < K;
+            si[r][tx] = (in && i0 + tx < N) ? V[(size_t)s * N + i0 + tx] : 0.0;
+            sj[r][tx] = (in && j0 + tx < N) ? w[s] * V[(size_t)s * N + j0 + tx] : 0.0;
         }
-        if (threadIdx.x < TRI_TILE) sw[threadIdx.x] = s0 + threadIdx.x < K ? w[s0 + threadIdx.x] : 0.0;
         __syncthreads();
-        // w_s (v_si v_sj): the product of the two entries first, so that
-        // entries (i, j) and (j, i) round alike and C' is exactly symmetric
 #pragma unroll 4
         for (int c = 0; c < TRI_TILE; ++c) {
-            const double bj = sj[c][tx], wc = sw[c];
+            const double bj = sj[c][tx];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += wc * (si[c][ty + 8 * q] * bj);
+            for (int q = 0; q < 4; ++q) acc[q] += si[c][ty + 8 * q] * bj;
         }
         __syncthreads();
     }
@@ -810,13 +810,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = i0 + ty + 8 * q, j = j0 + tx;
-        if (i < N && j < N) {
+        if (i < N && j < N && i <= j) {
             const double base = noise_form ? C[(size_t)i * N + j] : (i == j ? m : 0.0);
-            Cp[(size_t)i * N + j] = base + acc[q];
-            if (!diag_tile) {
-                const double bt = noise_form ? C[(size_t)j * N + i] : 0.0;
-                Cp[(size_t)j * N + i] = bt + acc[q];
-            }
+            const double v = base + acc[q];
+            Cp[(size_t)i * N + j] = v;
+            Cp[(size_t)j * N + i] = v;
         }
     }
 }
