@@ -910,8 +910,14 @@ __global__ void __launch_bounds__(256, 4)
 // draws for generation g (slot >= E). REG_OK: table rows may pass through
 // registers (the single-run kernel; the fleet kernel streams them, which
 // keeps its item loop within its registers).
+// PATH (fixed per instantiation, so that a kernel holds only the code its runs
+// use): GEN_PRODUCT, no score tables, every child scored from scratch in the
+// product form; GEN_DELTA_REG / GEN_DELTA_STREAM, score tables, children
+// scored by delta, the table row through registers (Np <= 512) or streamed.
 // ---------------------------------------------------------------------------
-template <bool REG_OK, bool DELTA_OK = true>
+enum GenPath : int { GEN_PRODUCT = 0, GEN_DELTA_REG = 1, GEN_DELTA_STREAM = 2 };
+
+template <bool REG_OK, int PATH>
 __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *nxt, int N, int ldp,
                                                 const EvolveCfg &cfg, const ChildPlan &plan,
                                                 uint32_t k0, uint32_t k1, int slot,
@@ -929,7 +935,7 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     const long long *ltab = reinterpret_cast<const long long *>(logtab);
     const long long *kfix = kfix_of(logtab);
     long long lf, np;
-    if (!DELTA_OK || !tab.dbuf(0)) {
+    if (PATH == GEN_PRODUCT) {
         // no score tables (N < DELTA_MIN_N, or a fleet): the child is built by
         // the pair loop of child_genes and scored from scratch in the
         // one-log product form
@@ -975,7 +981,7 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
         const long long lfa = tab.lfbuf(b)[ia], npa = tab.npbuf(b)[ia];
         const long long *ta = tab.dbuf(b) + (size_t)ia * tab.ldt;
         if (nx <= DELTA_X) {
-            if (REG_OK && Np <= 512)
+            if (REG_OK && PATH == GEN_DELTA_REG)
                 score_delta_warp<true>(sl, N, Np, nx, ta, lfa, npa, tc, Dfix, diag, ltab, kfix,
                                        lane, &lf, &np);
             else
@@ -993,6 +999,7 @@ __device__ __forceinline__ void generation_slot(const uint16_t *cur, uint16_t *n
     }
 }
 
+template <int PATH>
 __global__ void __launch_bounds__(128, 7)
     gather_generation_kernel(const uint16_t *pop0, const uint16_t *pop1, uint16_t *next0,
                              uint16_t *next1, EvolveCfg cfg, const int32_t *__restrict__ perm,
@@ -1017,7 +1024,7 @@ __global__ void __launch_bounds__(128, 7)
     SusPre pre;
     const bool use_pre = cfg.sus_tab != nullptr && slot >= cfg.E;
     if (use_pre) pre = sus_prefetch((uint32_t)(slot - cfg.E), cfg.M, cfg.P, prefix, cfg.sus_tab, lane);
-    const bool delta = tab.dbuf(0) != nullptr;
+    constexpr bool delta = PATH != GEN_PRODUCT;
     const int g_hint = *reinterpret_cast<volatile const int *>(&st->gnext);
     ChildPlan plan;
     plan.g = g_hint;
@@ -1035,7 +1042,7 @@ __global__ void __launch_bounds__(128, 7)
     const uint16_t *cur = (g & 1) ? pop1 : pop0;
     uint16_t *nxt = (g & 1) ? next1 : next0;
     const GatherSlice sl = gather_slice(smem_g + (size_t)warp * gather_slice_bytes(Np, delta), Np);
-    generation_slot<true>(cur, nxt, cfg.N, cfg.ldp, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix,
+    generation_slot<true, PATH>(cur, nxt, cfg.N, cfg.ldp, cfg, plan, k0, k1, slot, perm, prefix, Np, Dfix,
                           *diag_flag, logtab, L, tab, sl, lane, pairs ? pairs + g + 1 : nullptr,
                           use_pre ? &pre : nullptr);
 }
@@ -1078,7 +1085,7 @@ __global__ void __launch_bounds__(512, 2)
         const bool use_pre = slot >= base.E && !prop && base.sus_tab != nullptr;
         if (use_pre)
             pre = sus_prefetch((uint32_t)(slot - base.E), base.M, P, prefix, base.sus_tab, lane);
-        generation_slot<false, false>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot,
+        generation_slot<false, GEN_PRODUCT>(cur, nxt, r.N, r.Np, base, plan, st->k0, st->k1, slot,
                                       r.perm, prefix, r.Np, r.Dfix, *r.diag, logtab, r.L,
                                       ScoreTab{}, sl, lane, nullptr, use_pre ? &pre : nullptr);
         __syncwarp();
@@ -1126,9 +1133,19 @@ int launch_gather_generation(const uint16_t *const *pop2, uint16_t *const *next2
     const int nw = warps_for(Np, delta);
     const size_t smem = nw * gather_slice_bytes(Np, delta);
     const int grid = (cfg.P + nw - 1) / nw;
-    GPGA_CUDA(launch_pdl(gather_generation_kernel, dim3(grid), dim3(32 * nw), smem, s, pdl,
-                         pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np, Dfix,
-                         diag_flag, logtab, L, st, pairs, tab));
+    const int path = !delta ? GEN_PRODUCT : (Np <= 512 ? GEN_DELTA_REG : GEN_DELTA_STREAM);
+    if (path == GEN_PRODUCT)
+        GPGA_CUDA(launch_pdl(gather_generation_kernel<GEN_PRODUCT>, dim3(grid), dim3(32 * nw), smem,
+                             s, pdl, pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix, Np,
+                             Dfix, diag_flag, logtab, L, st, pairs, tab));
+    else if (path == GEN_DELTA_REG)
+        GPGA_CUDA(launch_pdl(gather_generation_kernel<GEN_DELTA_REG>, dim3(grid), dim3(32 * nw),
+                             smem, s, pdl, pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix,
+                             Np, Dfix, diag_flag, logtab, L, st, pairs, tab));
+    else
+        GPGA_CUDA(launch_pdl(gather_generation_kernel<GEN_DELTA_STREAM>, dim3(grid), dim3(32 * nw),
+                             smem, s, pdl, pop2[0], pop2[1], next2[0], next2[1], cfg, perm, prefix,
+                             Np, Dfix, diag_flag, logtab, L, st, pairs, tab));
     return GPGA_OK;
 }
 
@@ -1171,7 +1188,9 @@ int prepare_gather_kernels(int maxsmem)
 {
     if (int rc = raise_smem(gather_score_kernel<uint16_t>, maxsmem)) return rc;
     if (int rc = raise_smem(gather_score_kernel<int32_t>, maxsmem)) return rc;
-    if (int rc = raise_smem(gather_generation_kernel, maxsmem)) return rc;
+    if (int rc = raise_smem(gather_generation_kernel<GEN_PRODUCT>, maxsmem)) return rc;
+    if (int rc = raise_smem(gather_generation_kernel<GEN_DELTA_REG>, maxsmem)) return rc;
+    if (int rc = raise_smem(gather_generation_kernel<GEN_DELTA_STREAM>, maxsmem)) return rc;
     if (int rc = raise_smem(fleet_generation_kernel, maxsmem)) return rc;
     return GPGA_OK;
 }
