@@ -516,9 +516,9 @@ int launch_fleet_migrate(const FleetRun *runs, const FleetHdr *hdr, int P, int e
 // (key descending, index ascending; NaN as -inf). The slices' counts add up
 // to the exact rank, so perm[rank_i] = i is written at once: no atomics, no
 // ticket, no CTA waits for another. The CTA that holds rank 0 does the
-// generation's bookkeeping (best, the mean from the fixed-point sum of all
-// fitness values, which every CTA forms from its shared copy, the record of
-// the best configuration and the device clock, the termination test).
+// generation's bookkeeping (best, the record of the best configuration and the
+// device clock, the termination test); CTA 0 writes the mean, from the
+// fixed-point sum of all fitness values.
 // Stateful use: g = st->gen + gen_off (read only by the CTA that holds rank 0,
 // which is also the only writer of the state).
 // ---------------------------------------------------------------------------
@@ -561,7 +561,9 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
     const int P = cfg.P, Pp = (P + 2 * SEL_WARPS - 1) & ~(2 * SEL_WARPS - 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
     // keys (a padding key 0 is below every real key, so it is never fitter),
-    // four loads in flight per thread; the fixed-point sum for the mean
+    // four loads in flight per thread; CTA 0 alone forms the fixed-point sum
+    // for the mean
+    const bool mean_cta = st && blockIdx.x == 0;
     long long fsum = 0;
     for (int j0 = tid; j0 < Pp; j0 += 4 * nt) {
         unsigned long long u[4];
@@ -574,10 +576,10 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
         for (int q = 0; q < 4; ++q) {
             const int j = j0 + q * nt;
             if (j < Pp) s_key[j] = j < P ? order_key_bits(u[q]) : 0ull;
-            if (st && j < P) fsum += fix30_bits(u[q]);
+            if (mean_cta && j < P) fsum += fix30_bits(u[q]);
         }
     }
-    if (st) {
+    if (mean_cta) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
         if (lane == 0) s_sum[warp] = fsum;
@@ -611,6 +613,12 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
     // the next generation kernel (a programmatic dependent) may be scheduled
     // now; it waits for this grid to complete before it reads anything written here
     griddep_launch();
+    if (mean_cta && tid == 0) {
+        long long lsum = 0;
+#pragma unroll
+        for (int w = 0; w < SEL_WARPS; ++w) lsum += s_sum[w];
+        st->mean = (double)lsum * 9.313225746154785e-10 / (double)P;
+    }
     const int bidx = s_best;
     if (!st || bidx < 0) return;
     const int g = st->gen + cfg.gen_off;
@@ -619,9 +627,6 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
         for (int j = tid; j < cfg.N; j += blockDim.x) ring[(size_t)g * cfg.N + j] = src[j];
     }
     if (tid == 0) {
-        long long lsum = 0;
-#pragma unroll
-        for (int w = 0; w < SEL_WARPS; ++w) lsum += s_sum[w];
         double best = L[bidx];
         if (isnan(best)) best = -INFINITY;
         st->gen = g;
@@ -637,7 +642,6 @@ __global__ void __launch_bounds__(32 * SEL_WARPS)
             ts[1 + g] = t;
         }
         st->done = done;
-        st->mean = (double)lsum * 9.313225746154785e-10 / (double)P;
     }
 }
 
