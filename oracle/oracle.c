@@ -303,6 +303,9 @@ int orc_loglik_batch(const int32_t *labels, int P, int N, int ld, const double *
     int err = ORC_OK;
 #ifdef _OPENMP
     int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+    /* a small batch runs on one thread: a team's start-up and barrier cost
+     * more than its work there, and far more when the host is oversubscribed */
+    if ((long long)P * N < 32768) nt = 1;
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
 #endif
     for (int p = 0; p < P; ++p) {

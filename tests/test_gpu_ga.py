@@ -62,6 +62,41 @@ def test_evolve_bit_exact(g, orc, case):
     assert np.array_equal(nxt.cpu().numpy(), onxt)
 
 
+@pytest.mark.parametrize("P", [2, 33, 1000, 4096, 16384])
+@pytest.mark.parametrize("dist", ["equal", "narrow", "outliers", "signed_zero_nan"])
+def test_rank_order_adversarial_fitness(g, orc, P, dist):
+    """The device's rank order (key descending, index ascending, NaN as -inf)
+    equals the oracle's for fitness vectors that crowd the keys together or
+    spread them apart: all equal, a spread of 1e-9 around 75, a few huge
+    outliers, and signed zeros with NaN and infinities, from the smallest
+    population to the largest accepted."""
+    import torch
+    rng = np.random.default_rng(P * 7 + len(dist))
+    if dist == "equal":
+        L = np.full(P, 3.25)
+    elif dist == "narrow":
+        L = 75.0 + rng.random(P) * 1e-9
+        L[rng.integers(0, P, P // 4 + 1)] = 75.0
+    elif dist == "outliers":
+        L = rng.standard_normal(P)
+        L[rng.integers(0, P, 2)] = 1e300
+        L[rng.integers(0, P, 2)] = -1e300
+    else:
+        L = np.round(rng.standard_normal(P), 1)
+        L[rng.integers(0, P, P // 8 + 1)] = 0.0
+        L[rng.integers(0, P, P // 8 + 1)] = -0.0
+        L[rng.integers(0, P, 3)] = np.nan
+        L[rng.integers(0, P, 2)] = -np.inf
+        L[rng.integers(0, P, 2)] = np.inf
+    N = 8
+    pop = rng.integers(0, N, (P, N)).astype(np.int32)
+    E = min(2, P - 1)
+    gp = _gparams(g, P, E)
+    _, perm, _ = g.ga_evolve(dev(pop, torch.int32), dev(L), gp, 99, 4)
+    torch.cuda.synchronize()
+    assert np.array_equal(perm.cpu().numpy(), orc.ga_rank(L))
+
+
 def test_uniform_init_bit_exact(g, orc):
     import torch
     p = synth.n100()
