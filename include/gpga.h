@@ -368,10 +368,10 @@ GPGA_API int gpga_log_selftest(const double *x, int n, double *y_table, double *
  * until the process exits; the call makes no cudaMalloc, cudaFree or other
  * allocating call. Set-up: the first call on a device looks up that array's
  * device address (cudaGetSymbolAddress) once, with that device current, and
- * keeps it for the process; a cudaDeviceReset invalidates it, so do not call
- * this entry point on a device after resetting that device in the same
- * process. The call waits for its stream at the end, so no call of it can be
- * captured into a CUDA graph. The caller passes inputs and
+ * keeps it for the process; make that first call before any stream capture.
+ * A cudaDeviceReset invalidates the address, so do not call this entry point
+ * on a device after resetting that device in the same process. The caller
+ * passes inputs and
  * outputs exactly as for ga_score: labels (device, P x N int32 in [0, N),
  * leading dimension ld >= N), C (device, N x N FP64), L (device, P FP64,
  * written).
