@@ -4,7 +4,7 @@ individual within |dL| <= 1e-4 + 1e-6 |L| and max |dC| <= 1e-6 (asserted).
 With PARITY_TABLE_OUT=<path> in the environment the figures are also written
 there as a markdown table, e.g.
 
-    PARITY_TABLE_OUT=gpurun_out/parity_errors_by_form.md \\
+    PARITY_TABLE_OUT=/tmp/parity_errors_by_form.md \\
         python -m pytest tests/test_gpu_parity_table.py -m gpu -q
 
 The expected values come from oracle/ only."""
@@ -62,7 +62,7 @@ def test_parity_table(orc):
     if out:
         with open(out, "w") as f:
             f.write("# Likelihood and correlation errors against the FP64 oracle\n\n")
-            f.write("Command: `PARITY_TABLE_OUT=gpurun_out/parity_errors_by_form.md python -m "
+            f.write(f"Command: `PARITY_TABLE_OUT={out} python -m "
                     "pytest tests/test_gpu_parity_table.py -m gpu -q` (1 GB300). Same seeded "
                     "inputs on both sides; the oracle's C is the input of every GPU score. Bar "
                     "per individual: |dL| <= 1e-4 + 1e-6 |L|.\n\n")
