@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recover", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="leave out the batched workload's summary from the headline line")
+                    help="leave out the batched and serving summaries from the headline line")
     ap.add_argument("--workload", default="planted",
                     choices=["planted", "batched", "serving", "paper", "preprocess", "islands"],
                     help="planted: the N=500 headline; batched: 256 sliding intraday windows "
@@ -366,17 +366,22 @@ def run_gpu(args, ranks):
         if out["recover"]:
             ms_rec.update(out["recover"])
 
-    # the batched workload (256 sliding windows in one fleet), one timed job,
-    # carried in the headline line so that one run records it too
+    # the batched workload (256 sliding windows in one fleet, one timed job) and
+    # the serving stream (Poisson arrivals for --serve-seconds), carried in the
+    # headline line so that one run records them too
     secondary = None
     if ranks.rank == 0 and ranks.world == 1 and not args.no_secondary:
-        try:
-            bl = run_batched(argparse.Namespace(**{**vars(args), "steps": 10}), ranks, emit=False)
-            secondary = {"batched": {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step",
-                                                        "evals_per_s", "generations", "config",
-                                                        "ari_single_regime_windows")}}
-        except Exception as exc:  # reported, never hides the headline
-            secondary = {"batched": {"error": repr(exc)[:300]}}
+        secondary = {}
+        keep = {"batched": ("metric", "value", "unit", "ms_per_step", "evals_per_s",
+                            "generations", "config", "ari_single_regime_windows"),
+                "serving": ("metric", "value", "unit", "config", "latency_ms", "evals_per_s",
+                            "generations_mean", "active_runs")}
+        for name, fn in (("batched", run_batched), ("serving", run_serving)):
+            try:
+                sl = fn(argparse.Namespace(**{**vars(args), "steps": 10}), ranks, emit=False)
+                secondary[name] = {k: sl[k] for k in keep[name]}
+            except Exception as exc:  # reported, never hides the headline
+                secondary[name] = {"error": repr(exc)[:300]}
 
     cpu = None
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
@@ -736,7 +741,9 @@ def run_batched(args, ranks, emit=True):
 S_NS, S_P, S_POOL = (30, 100, 300, 1000), 2048, 8
 
 
-def run_serving(args, ranks):
+def run_serving(args, ranks, emit=True):
+    """Config 5: a Poisson stream of correlation windows. Prints its JSON line
+    (emit) or returns it (as a secondary object of the headline line)."""
     import torch
 
     from paper_1403_4099_gb300 import gpga, runtime, synth
@@ -820,8 +827,11 @@ def run_serving(args, ranks):
                 "gpu_generation_graphs_s": st["gpu_ms"] / 1e3,
                 "individual_generations_per_gpu_s": (st["item_gens"] / (st["gpu_ms"] / 1e3)
                                                      if st["gpu_ms"] > 0 else None)}
+        if not emit:
+            return line
         print(json.dumps(line), flush=True)
     runtime.barrier(ranks)
+    return None
 
 
 # ---------------------------------------------------------------------------

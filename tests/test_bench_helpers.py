@@ -48,3 +48,26 @@ def test_traffic_files_parse(bench, kernel, sources):
     got = bench.profiled_traffic(kernel, bench.source_hash(*sources))
     assert got is None or got > 0
     assert bench.profiled_traffic(kernel, "0" * 16) is None  # other sources: unknown
+
+
+def test_first_recovery_reads_the_records(bench):
+    """Recovery along a run's records: the first generation whose best
+    configuration matches the planted clusters over their members (noise series
+    left out), its device time, and the final configuration's merged and split
+    planted clusters."""
+    import numpy as np
+    truth = np.array([0, 0, 0, 1, 1, 1, 2, 2, 3, 4])  # clusters 0-2, noise 3 and 4
+    merged = np.array([5, 5, 5, 5, 5, 5, 7, 7, 1, 5])  # 0 and 1 together
+    split = np.array([5, 5, 6, 3, 3, 3, 7, 7, 5, 5])   # 0 in two pieces
+    exact = np.array([9, 9, 9, 2, 2, 2, 4, 4, 9, 2])   # noise placed anywhere
+    h = {"labels": [merged, split, exact, exact], "t_ns": np.array([0, 10, 20, 35, 50]),
+         "best_L": np.array([1.0, 2.0, 3.0, 3.0])}
+    r = bench.first_recovery(h, truth)
+    assert r["generation"] == 2 and r["ms"] == 35e-6
+    assert r["best_ari_members"] == 1.0 and r["best_ari_members_generation"] == 2
+    assert r["final_planted_clusters_merged"] == 0 and r["final_planted_clusters_split"] == 0
+    r = bench.first_recovery({**h, "labels": [exact, merged]}, truth)
+    assert r["final_planted_clusters_merged"] == 2 and r["final_planted_clusters_split"] == 0
+    r = bench.first_recovery({**h, "labels": [split]}, truth)
+    assert r["generation"] is None and r["ms"] is None
+    assert r["final_planted_clusters_merged"] == 0 and r["final_planted_clusters_split"] == 1
