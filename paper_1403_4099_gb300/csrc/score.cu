@@ -9,6 +9,8 @@
 // Accumulating 1 - C_ij directly keeps n_s^2 - c_s free of cancellation.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "gpga_internal.cuh"
 
 namespace gpga {
@@ -409,13 +411,25 @@ template int launch_assemble<int32_t>(const int32_t *const *, int, int, const fl
 
 // ---------------------------------------------------------------------------
 // Final re-score of one configuration in FP64 straight from C (Eq. 5, 6, 8),
-// plus its canonical relabelling (first occurrence -> 0, 1, 2, ...). One CTA.
-// Canonical ids from the first gene of each label (atomicMin) and a block scan;
-// row sums are sequential in j; cluster sums run over members in ascending i
-// (one thread per cluster); the terms, in canonical order, are summed with
-// compensation as 32 contiguous runs whose (sum, error) pairs are combined by
-// a two-sum butterfly (error of the total about one ulp).
+// plus its canonical relabelling (first occurrence -> 0, 1, 2, ...), on a
+// thread-block cluster of RESCORE_CTAS CTAs (one CTA when the cluster cannot
+// be placed). Every CTA forms the canonical ids (first gene of each label by
+// atomicMin, a block scan) and the member list of every cluster in ascending
+// gene order (a counting sort, stable through warp match masks). The rows of
+// C are then dealt out over the cluster in chunks of 32 list positions, so a
+// warp's lanes take rows of the same cluster: a thread sums C_ij and 1 - C_ij
+// over its row's members j in ascending order with Neumaier compensation.
+// An FP64 instruction holds the FP64 pipe whatever the number of active lanes,
+// so the loops run over members only and keep the lanes busy. After a cluster
+// barrier CTA 0 reads the other CTAs' row sums from their shared memory (the
+// others wait at a second barrier until it has), sums each cluster's rows in
+// ascending order (one thread per cluster), takes the Eq. 8 terms and adds
+// them in canonical order as 32 compensated runs combined by a two-sum
+// butterfly. Every sum is in the same order as a sequential one over the
+// members, within about one ulp of the exact value.
 // ---------------------------------------------------------------------------
+constexpr int RESCORE_CTAS = 8;
+
 __device__ __forceinline__ void neu_add(double &s, double &c, double x)
 {
     const double t = s + x;
@@ -435,21 +449,30 @@ __device__ __forceinline__ void two_sum_add(double &s, double &c, double x)
     s = t;
 }
 
+// CTA of the cluster that owns list position p: positions go out in chunks
+// of 32, chunk q to warp q mod (ncta nw) counted CTA-fastest
+__device__ __forceinline__ int rescore_owner(int p, int ncta) { return (p >> 5) % ncta; }
+
 __global__ void __launch_bounds__(1024)
     rescore_kernel(const uint16_t *pop0, const uint16_t *pop1, int ldp,
                    const DevState *__restrict__ st, const double *__restrict__ C, int N,
                    int32_t *__restrict__ canon, double *__restrict__ L_out)
 {
+    namespace cg = cooperative_groups;
+    const cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), ncta = (int)cluster.num_blocks();
     const uint16_t *lab = ((st->gen & 1) ? pop1 : pop0) + (size_t)st->best_idx * ldp;
     extern __shared__ double sm_d[];
-    double *rc = sm_d;           // N row sums of C over same-cluster columns
+    double *rc = sm_d;           // N row sums of C over same-cluster columns (by gene)
     double *rd = sm_d + N;       // N row sums of (1 - C)
     double *term = sm_d + 2 * N; // per canonical cluster: its Eq. 8 term (0 for singletons)
-    int *li = reinterpret_cast<int *>(sm_d + 3 * N); // labels
-    int *first = li + N;         // label -> first gene carrying it (N if none)
-    int *pos = first + N;        // gene -> canonical id of a first occurrence (scan)
+    int *li = reinterpret_cast<int *>(sm_d + 3 * N); // labels, then fill counters
+    int *first = li + N;         // label -> first gene carrying it, then cluster sizes
+    int *gid = first + N;        // gene -> canonical id (scan of first occurrences)
+    int *start = gid + N;        // canonical id -> its first list position
+    int *mem = start + N;        // the member list: genes by cluster, ascending in each
     __shared__ int s_part[32];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int i = tid; i < N; i += nt) {
         li[i] = lab[i];
         first[i] = N;
@@ -472,7 +495,7 @@ __global__ void __launch_bounds__(1024)
     if (lane == 31) s_part[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        int w = lane < (nt >> 5) ? s_part[lane] : 0;
+        int w = lane < nw ? s_part[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, w, o);
@@ -483,39 +506,124 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     int run = v - cnt + (wid ? s_part[wid - 1] : 0);
     for (int i = lo; i < hi; ++i) {
-        pos[i] = run;
+        gid[i] = run; // provisional: valid at first occurrences
         if (first[li[i]] == i) ++run;
     }
-    const int K = s_part[(nt >> 5) - 1];
+    const int K = s_part[nw - 1];
     __syncthreads();
-    // row sums over the gene's cluster, sequential in j
-    for (int i = tid; i < N; i += nt) {
+    int g_own[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = tid + u * nt;
+        g_own[u] = i < N ? gid[first[li[i]]] : 0;
+    }
+    __syncthreads();
+    // canonical id of every gene; cluster sizes (over first[]), fill counters
+    // (over li[])
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = tid + u * nt;
+        if (i < N) gid[i] = g_own[u];
+    }
+    for (int k = tid; k < N; k += nt) {
+        first[k] = 0;
+        li[k] = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) atomicAdd(&first[gid[i]], 1);
+    __syncthreads();
+    // list starts: exclusive scan of the sizes over the K clusters
+    {
+        const int kc = (K + nt - 1) / nt;
+        const int k0 = min(K, tid * kc), k1 = min(K, k0 + kc);
+        int sz = 0;
+        for (int k = k0; k < k1; ++k) sz += first[k];
+        int x = sz;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        __syncthreads(); // s_part is reused
+        if (lane == 31) s_part[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < nw ? s_part[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            s_part[lane] = w;
+        }
+        __syncthreads();
+        int at = x - sz + (wid ? s_part[wid - 1] : 0);
+        for (int k = k0; k < k1; ++k) {
+            start[k] = at;
+            at += first[k];
+        }
+    }
+    __syncthreads();
+    // member lists, ascending gene order inside each cluster: warp 0 walks the
+    // genes 32 at a time; lanes with the same id are ordered by lane
+    if (wid == 0) {
+        const unsigned lt = (1u << lane) - 1u;
+        for (int b = 0; b < N; b += 32) {
+            const int i = b + lane;
+            const int k = i < N ? gid[i] : -1 - lane; // a distinct key per idle lane
+            const unsigned same = __match_any_sync(0xffffffffu, k);
+            if (i < N) {
+                const int r = __popc(same & lt);
+                mem[start[k] + li[k] + r] = i;
+            }
+            __syncwarp();
+            if (i < N && (same & lt) == 0) li[k] += __popc(same);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // row sums of the list positions this CTA owns; singletons need none
+    const int lanes_all = ncta * nt;
+    for (int p0 = (wid * ncta + rank) * 32; p0 < N; p0 += lanes_all) {
+        const int p = p0 + lane;
+        if (p >= N) continue;
+        const int i = mem[p], k = gid[i], n = first[k];
+        if (n < 2) continue;
+        const double *row = C + (size_t)i * N;
+        const int q0 = start[k];
         double sc = 0.0, cc = 0.0, sd = 0.0, cd = 0.0;
-        const int si = li[i];
-        for (int j = first[si]; j < N; ++j) {
-            if (li[j] != si) continue;
-            const double x = C[(size_t)i * N + j];
+        for (int q = q0; q < q0 + n; ++q) {
+            const double x = __ldg(row + mem[q]);
             neu_add(sc, cc, x);
             neu_add(sd, cd, 1.0 - x);
         }
         rc[i] = sc + cc;
         rd[i] = sd + cd;
     }
-    __syncthreads();
-    // one thread per cluster: member sums in ascending index, then its term
-    for (int i = tid; i < N; i += nt) {
-        const int s = li[i];
-        if (first[s] != i) continue; // i opens cluster s
-        int n = 0;
-        double c = 0.0, cc = 0.0, d = 0.0, dc = 0.0;
-        for (int j = i; j < N; ++j) {
-            if (li[j] != s) continue;
-            ++n;
-            neu_add(c, cc, rc[j]);
-            neu_add(d, dc, rd[j]);
+    cluster.sync(); // every row sum is in its CTA's shared memory
+    if (rank == 0 && ncta > 1) {
+        for (int p = tid; p < N; p += nt) {
+            const int owner = rescore_owner(p, ncta);
+            const int i = mem[p];
+            if (owner != 0 && first[gid[i]] >= 2) {
+                rc[i] = *cluster.map_shared_rank(rc + i, owner);
+                rd[i] = *cluster.map_shared_rank(rd + i, owner);
+            }
         }
+    }
+    cluster.sync(); // CTA 0 has read the others' shared memory: they may exit
+    if (rank != 0) return;
+    // one thread per cluster: its members' row sums in ascending index, then its term
+    for (int k = tid; k < K; k += nt) {
+        const int n = first[k];
         double t = 0.0;
         if (n >= 2) {
+            double c = 0.0, cc = 0.0, d = 0.0, dc = 0.0;
+            for (int q = start[k]; q < start[k] + n; ++q) {
+                const int j = mem[q];
+                neu_add(c, cc, rc[j]);
+                neu_add(d, dc, rd[j]);
+            }
             const double dn = (double)n;
             double cs = c + cc, ds = d + dc;
             const double eps = 9.094947017729282e-13;
@@ -523,7 +631,7 @@ __global__ void __launch_bounds__(1024)
             if (!(ds >= dn * (dn - 1.0) * eps)) ds = dn * (dn - 1.0) * eps;
             t = 0.5 * (log(dn / cs) + (dn - 1.0) * log((dn * dn - dn) / ds));
         }
-        term[pos[i]] = t;
+        term[k] = t;
     }
     __syncthreads();
     // terms in canonical order: lane l of warp 0 sums a contiguous run with
@@ -548,15 +656,34 @@ __global__ void __launch_bounds__(1024)
         }
         if (lane == 0) *L_out = s + c;
     }
-    for (int i = tid; i < N; i += nt) canon[i] = pos[first[li[i]]];
+    for (int i = tid; i < N; i += nt) canon[i] = gid[i];
+}
+
+// cluster size the re-score launches with (RESCORE_CTAS, or 1 when a cluster
+// of that size with this shared memory cannot be placed); set at preparation
+static int g_rescore_ctas = 1;
+
+static size_t rescore_smem(int N)
+{
+    return (size_t)N * (3 * sizeof(double) + 5 * sizeof(int));
 }
 
 int launch_rescore_fp64(const uint16_t *pop0, const uint16_t *pop1, int ldp, const DevState *st,
                         const double *C, int N, int32_t *canon_out, double *L_out, cudaStream_t s)
 {
-    const size_t smem = (size_t)N * (3 * sizeof(double) + 3 * sizeof(int));
-    rescore_kernel<<<1, 1024, smem, s>>>(pop0, pop1, ldp, st, C, N, canon_out, L_out);
-    GPGA_LAUNCH_CHECK();
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(g_rescore_ctas);
+    c.blockDim = dim3(1024);
+    c.dynamicSmemBytes = rescore_smem(N);
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = g_rescore_ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    GPGA_CUDA(cudaLaunchKernelEx(&c, rescore_kernel, pop0, pop1, ldp, st, C, N, canon_out, L_out));
     return GPGA_OK;
 }
 
@@ -595,6 +722,23 @@ int prepare_score_kernels(int maxsmem)
     if (int rc = raise_smem(assemble_kernel<uint16_t>, maxsmem)) return rc;
     if (int rc = raise_smem(assemble_kernel<int32_t>, maxsmem)) return rc;
     if (int rc = raise_smem(rescore_kernel, maxsmem)) return rc;
+    // the re-score's cluster: RESCORE_CTAS CTAs if that many can be placed with
+    // the shared memory of the largest N, else a single CTA does all the rows
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(RESCORE_CTAS);
+    c.blockDim = dim3(1024);
+    c.dynamicSmemBytes = rescore_smem(GPGA_MAX_N);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = RESCORE_CTAS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    int nclusters = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, rescore_kernel, &c);
+    if (e != cudaSuccess) (void)cudaGetLastError(); // not placeable: one CTA
+    g_rescore_ctas = (e == cudaSuccess && nclusters >= 1) ? RESCORE_CTAS : 1;
     return GPGA_OK;
 }
 
