@@ -11,7 +11,8 @@
 //   edge (from_k, v_k) of weight w_k; label(v_0) = v_0 and
 //   label(v_k) = w_k > tau ? label(from_k) : v_k.
 // Prim's rule: the next vertex has the largest key (ties to the lower index);
-// a key improves only on a strictly larger C. All comparisons are exact FP64.
+// a key improves only on a strictly larger C. The comparisons are those of
+// FP64 values, made exactly on order-preserving integer images.
 #include <math.h>
 
 #include "gpga_internal.cuh"
@@ -20,20 +21,46 @@ namespace gpga {
 
 static constexpr uint32_t STREAM_TAU = 4u;
 
+// Order-preserving integer image of an FP64 value, so that Prim's
+// comparisons run on the integer pipe (an FP64 instruction holds the FP64 pipe
+// for tens of cycles whatever its active lanes): for non-NaN a and b,
+// a > b iff prim_key(a) > prim_key(b) and a == b iff the keys are equal
+// (-0 and +0 share a key). NaN takes the key of -inf. Every key is above 0.
+__device__ __forceinline__ unsigned long long prim_key(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    if (mag > 0x7ff0000000000000ull) b = 0xfff0000000000000ull; // NaN -> -inf
+    else if (mag == 0ull) b = 0ull;                            // -0 -> +0
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// larger key first, ties to the lower vertex
+__device__ __forceinline__ void prim_max(unsigned long long &bk, int &bi, unsigned long long k, int i)
+{
+    if (k > bk || (k == bk && i < bi)) {
+        bk = k;
+        bi = i;
+    }
+}
+
 __global__ void __launch_bounds__(1024)
     mst_kernel(const double *__restrict__ C, int N, int32_t *__restrict__ order,
                int32_t *__restrict__ from, double *__restrict__ w_out)
 {
-    extern __shared__ double sm[];
-    double *key = sm;                                        // N
-    int *src = reinterpret_cast<int *>(key + N);             // N
-    int *in = src + N;                                       // N
-    __shared__ double s_bk[32];
+    extern __shared__ unsigned long long sm_key[];
+    unsigned long long *key = sm_key;                  // N: image of the best edge weight
+    double *val = reinterpret_cast<double *>(key + N); // N: that weight
+    int *src = reinterpret_cast<int *>(val + N);       // N
+    int *in = src + N;                                 // N
+    __shared__ unsigned long long s_bk[32];
     __shared__ int s_bi[32];
     __shared__ int s_pick;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, nw = nt >> 5;
     for (int j = tid; j < N; j += nt) {
-        key[j] = C[j]; // row 0
+        const double c = C[j]; // row 0
+        key[j] = prim_key(c);
+        val[j] = c;
         src[j] = 0;
         in[j] = j == 0;
     }
@@ -45,48 +72,31 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     for (int step = 1; step < N; ++step) {
         // argmax of key over vertices not in the tree, ties to the lower index
-        double bk = -INFINITY;
+        // (key 0 is below every real key, so a vertex is always found)
+        unsigned long long bk = 0ull;
         int bi = 0x7fffffff;
-        for (int j = tid; j < N; j += nt) {
-            if (in[j]) continue;
-            const double k = key[j];
-            if (k > bk || (k == bk && j < bi)) {
-                bk = k;
-                bi = j;
-            }
-        }
+        for (int j = tid; j < N; j += nt)
+            if (!in[j]) prim_max(bk, bi, key[j], j);
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ok > bk || (ok == bk && oi < bi)) {
-                bk = ok;
-                bi = oi;
-            }
-        }
-        if ((tid & 31) == 0) {
+        for (int o = 16; o; o >>= 1)
+            prim_max(bk, bi, __shfl_xor_sync(0xffffffffu, bk, o), __shfl_xor_sync(0xffffffffu, bi, o));
+        if (lane == 0) {
             s_bk[tid >> 5] = bk;
             s_bi[tid >> 5] = bi;
         }
         __syncthreads();
         if (tid < 32) {
-            const int nw = nt >> 5;
-            bk = tid < nw ? s_bk[tid] : -INFINITY;
+            bk = tid < nw ? s_bk[tid] : 0ull;
             bi = tid < nw ? s_bi[tid] : 0x7fffffff;
 #pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ok > bk || (ok == bk && oi < bi)) {
-                    bk = ok;
-                    bi = oi;
-                }
-            }
+            for (int o = 16; o; o >>= 1)
+                prim_max(bk, bi, __shfl_xor_sync(0xffffffffu, bk, o),
+                         __shfl_xor_sync(0xffffffffu, bi, o));
             if (tid == 0) {
                 s_pick = bi;
                 order[step] = bi;
                 from[step] = src[bi];
-                w_out[step] = key[bi];
+                w_out[step] = val[bi];
                 in[bi] = 1;
             }
         }
@@ -96,8 +106,10 @@ __global__ void __launch_bounds__(1024)
         for (int j = tid; j < N; j += nt) {
             if (in[j]) continue;
             const double c = row[j];
-            if (c > key[j]) {
-                key[j] = c;
+            const unsigned long long ck = prim_key(c);
+            if (ck > key[j]) {
+                key[j] = ck;
+                val[j] = c;
                 src[j] = v;
             }
         }
@@ -108,7 +120,7 @@ __global__ void __launch_bounds__(1024)
 int launch_mst(const double *C, int N, int32_t *order, int32_t *from, double *w,
                cudaStream_t s)
 {
-    const size_t smem = (size_t)N * (sizeof(double) + 2 * sizeof(int));
+    const size_t smem = (size_t)N * (sizeof(unsigned long long) + sizeof(double) + 2 * sizeof(int));
     mst_kernel<<<1, 1024, smem, s>>>(C, N, order, from, w);
     GPGA_LAUNCH_CHECK();
     return GPGA_OK;
