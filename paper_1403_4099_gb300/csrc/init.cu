@@ -297,10 +297,24 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// better Prim candidate: smaller key, ties to the lower gene index
+// Integer image of a tree distance for the minimum search: for finite a, b,
+// a < b iff dist_img(a) < dist_img(b) and a == b iff the images are equal;
+// +inf (the search's starting value) and NaN share the largest image, so a
+// member is always picked and any finite distance is preferred to them.
+__device__ __forceinline__ unsigned long long dist_img(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool nan = (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+    const bool pinf = b == 0x7ff0000000000000ull;
+    return (nan || pinf) ? ~0ull : prim_key(x);
+}
+
+// better Prim candidate: smaller key, ties to the lower gene index (compared
+// on the integer pipe)
 __device__ __forceinline__ bool prim_better(double k, int g, double bk, int bg)
 {
-    return k < bk || (k == bk && g < bg);
+    const unsigned long long ik = dist_img(k), ib = dist_img(bk);
+    return ik < ib || (ik == ib && g < bg);
 }
 
 __global__ void __launch_bounds__(256)
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(256)
             }
             if (!in) {
                 const double d = corr_dist(C, N, bg, g);
-                if (d < key) {
+                if (dist_img(d) < dist_img(key)) {
                     key = d;
                     src = bg;
                 }
@@ -430,7 +444,7 @@ __global__ void __launch_bounds__(256)
         for (int t = tid; t < n; t += blockDim.x) {
             if (intree[t]) continue;
             const double d = corr_dist(C, N, vg, mem[t]);
-            if (d < key[t]) {
+            if (dist_img(d) < dist_img(key[t])) {
                 key[t] = d;
                 src[t] = vg;
             }
